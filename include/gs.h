@@ -1,0 +1,202 @@
+/*
+ * gs.h -- C ABI of the GB300 differentiable tile rasterizer (libgs.so).
+ *
+ * The paper trains 3D Gaussian Splatting primitives, initialised from an
+ * isosurface point cloud, to match images rendered from a structured camera
+ * orbit (Section III, "Method Overview"); every training view runs the
+ * differentiable tile rasterizer of 3D-GS (Section I): EWA projection of the
+ * Gaussians, duplication into 16x16 screen tiles, a radix sort on
+ * (tile, depth) keys, front-to-back alpha compositing per tile, its
+ * reverse-order backward pass and an Adam update.  This header exposes those
+ * steps one call each.
+ *
+ * Conventions shared by every call
+ *  - All pointers named "device" are CUDA device pointers on the context's
+ *    device; "host" pointers are ordinary host memory.  No call takes
+ *    ownership of a caller pointer.
+ *  - Calls are asynchronous on the context's stream (gs_set_stream) unless
+ *    stated otherwise.  Errors detected on the host (bad arguments, missing
+ *    preceding step, allocation failure, CUDA launch errors) are returned
+ *    immediately and nothing is launched.  Errors detected on the device
+ *    (instance capacity exceeded, a bounded wait that ran out) are recorded
+ *    in a device status word and returned by gs_sync.
+ *  - Parameters (gs_params) are FP32 "SoA planes": data[p * stride + i] is
+ *    plane p of Gaussian i, with
+ *        planes 0-2   mean x, y, z (world)
+ *        planes 3-5   log-scale s0, s1, s2
+ *        planes 6-9   rotation quaternion w, x, y, z (need not be unit)
+ *        plane  10    opacity logit o (opacity = 1 / (1 + exp(-o)))
+ *        planes 11..  SH colour coefficients, plane 11 + 3k + c = coefficient
+ *                     k (k = l*l + l + m, real orthonormal basis) of channel c
+ *    P = 11 + 3 (deg+1)^2 planes; stride >= n, stride % 4 == 0, data 16-byte
+ *    aligned.  Gradients and Adam moments use the same layout.
+ *  - Images are FP32, planar, [view][channel 3][height][width], the views of
+ *    a batch concatenated in order (view v starts at 3 * sum_{u<v} W_u H_u).
+ *  - One context serves one host thread at a time.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_EINVAL = 1,     /* bad argument; nothing launched */
+  GS_ENOMEM = 2,     /* device allocation failed */
+  GS_ECUDA = 3,      /* CUDA runtime error (message in gs_last_error) */
+  GS_ECAPACITY = 4,  /* more tile instances than the preset capacity */
+  GS_ETIMEOUT = 5,   /* a bounded device-side wait ran out */
+  GS_EBUSY = 6,      /* server: no free slot / memory budget */
+  GS_EAGAIN = 7,     /* server: result not ready before the timeout */
+  GS_ESTATE = 8      /* a call needs a preceding step that has not run */
+} gs_status;
+
+typedef struct gs_ctx gs_ctx;
+
+/* Context limits.  Zero fields take defaults (see gs_create). */
+typedef struct {
+  int64_t max_gaussians;     /* N capacity for workspaces (grown on demand) */
+  int32_t max_views;         /* views per batch, <= 64 */
+  int32_t flags;             /* reserved, 0 */
+  int64_t instance_capacity; /* 0: grow on demand (host reads the count);
+                                > 0: fixed capacity, overflow -> GS_ECAPACITY
+                                (required for CUDA-graph capture) */
+} gs_config;
+
+/* Pinhole camera, world -> camera.  The camera looks down +z, x right,
+ * y down; pixel (i, j) is the point (i, j) of the image plane, so the
+ * principal point of a centred camera is ((W-1)/2, (H-1)/2). */
+typedef struct {
+  float viewmat[16]; /* row-major 4x4 world->camera (rotation rows, translation column) */
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float znear;       /* Gaussians with depth <= znear are culled */
+  float bg[3];       /* background colour composited behind the Gaussians */
+} gs_camera;
+
+/* A Gaussian set (device) in the plane layout above. */
+typedef struct {
+  float* data;
+  int64_t n;
+  int64_t stride;
+  int32_t sh_degree; /* 0..3 */
+  int32_t reserved;
+} gs_params;
+
+/* Adam hyper-parameters: one learning rate per parameter group. */
+typedef struct {
+  float lr_mean, lr_scale, lr_quat, lr_opacity, lr_sh_dc, lr_sh_rest;
+  float beta1, beta2, eps;
+} gs_adam_hp;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  cfg may be NULL (defaults:
+ * max_views 64, instance capacity grown on demand).  Allocates the device
+ * status word; workspaces are allocated lazily and grow.  *out is NULL on
+ * error.  Errors: GS_EINVAL (out NULL, bad cfg), GS_ECUDA, GS_ENOMEM. */
+gs_status gs_create(gs_ctx** out, int device, const gs_config* cfg);
+
+/* Free every device buffer of the context (synchronises its stream). */
+void gs_destroy(gs_ctx* ctx);
+
+/* Last error message of this context ("" when none); owned by the context. */
+const char* gs_last_error(const gs_ctx* ctx);
+
+/* Use `stream` (a cudaStream_t, NULL = legacy default stream) for every
+ * following call of this context. */
+gs_status gs_set_stream(gs_ctx* ctx, void* stream);
+
+/* Wait for the context's stream; return the device status word (GS_OK,
+ * GS_ECAPACITY or GS_ETIMEOUT) and clear it. */
+gs_status gs_sync(gs_ctx* ctx);
+
+/* ---------------------------------------------------------------- the path */
+
+/* Step 1, projection (EWA splatting of 3D-GS, Section I; Gaussians from the
+ * point cloud, Section III).  For each of the B cameras (host array) and
+ * each Gaussian: t = W mu + tau, cull if depth <= znear, Sigma = R S S^T R^T,
+ * Sigma' = J W Sigma W^T J^T + 0.3 I (J with image-plane slopes clamped to
+ * 1.3x the half field of view), conic = Sigma'^-1, radius
+ * ceil(3 sqrt(lambda_max)), tile rect, opacity sigma(o) and view-dependent
+ * colour max(0, SH(d) + 0.5).  Results stay in the context for the next
+ * steps.  1 <= B <= max_views; cameras may differ in resolution.
+ * Errors: GS_EINVAL (null pointers, n <= 0, sh_degree outside 0..3, bad
+ * stride/alignment, width/height <= 0), GS_ENOMEM, GS_ECUDA. */
+gs_status gs_project(gs_ctx* ctx, const gs_params* params, const gs_camera* cams, int32_t B);
+
+/* Step 2, binning: exclusive scan of per-(view, Gaussian) tile counts,
+ * duplication into one instance per touched tile with the 64-bit key
+ * (bin << 32) | FP32 depth bits (bin = the view's first tile + ty * gw + tx)
+ * and value = Gaussian index, an LSD onesweep radix sort on the key bits
+ * that vary, and per-bin [start, end) ranges of the sorted list.  With a
+ * grow-on-demand context this call reads the instance count on the host
+ * (one stream synchronisation).  Errors: GS_ESTATE (no gs_project),
+ * GS_ENOMEM, GS_ECUDA; device-side GS_ECAPACITY via gs_sync. */
+gs_status gs_bin_sort(gs_ctx* ctx);
+
+/* Step 3, forward compositing.  Per pixel, over its tile's sorted list:
+ * alpha = min(0.99, opacity * exp(power)), skip if power > 0 or
+ * alpha < 1/255, stop before a Gaussian that would bring T below 1e-4,
+ * C += rgb alpha T, T *= 1 - alpha; output C + T bg.  images: device,
+ * [B][3][H][W] as above.  Also keeps T_final and the index of the last
+ * contributor per pixel for the backward pass.
+ * Errors: GS_ESTATE (no gs_bin_sort), GS_EINVAL (images NULL), GS_ECUDA. */
+gs_status gs_raster_fwd(gs_ctx* ctx, float* images);
+
+/* Step 4, backward.  Given dL/dimages (device, image layout), walks every
+ * tile list in reverse from each pixel's last contributor, recovering T by
+ * division, and writes dL/dparams into grads->data (device, overwritten;
+ * same n, stride and degree as params).  The derivative is the exact one of
+ * step 3 where it exists: zero through a clamped alpha (opacity * G > 0.99),
+ * the slope clamp and the colour clamp.  params must be the set given to
+ * gs_project.  Errors: GS_ESTATE (no gs_raster_fwd), GS_EINVAL, GS_ECUDA. */
+gs_status gs_raster_bwd(gs_ctx* ctx, const gs_params* params, const float* dL_dimages,
+                        gs_params* grads);
+
+/* L1 photometric loss over `count` floats (device): *loss = mean |x - y|
+ * (device scalar) and dL_dx = sign(x - y) / count (device; sign(0) = 0).
+ * Either output may be NULL.  Errors: GS_EINVAL, GS_ECUDA. */
+gs_status gs_l1_loss(gs_ctx* ctx, const float* x, const float* y, int64_t count, float* loss,
+                     float* dL_dx);
+
+/* Step 5, Adam with bias correction (torch.optim.Adam semantics), dense over
+ * all planes, per-group learning rate; step counts from 1.  p, m, v are
+ * updated in place; g is read.  All four share n, stride and degree.
+ * Errors: GS_EINVAL (mismatched sets, step < 1), GS_ECUDA. */
+gs_status gs_adam(gs_ctx* ctx, gs_params* p, const gs_params* g, gs_params* m, gs_params* v,
+                  const gs_adam_hp* hp, int64_t step);
+
+/* ---------------------------------------------------------------- inspection */
+
+/* Intermediate buffers of the last batch (device pointers owned by the
+ * context, valid until the next call that rewrites them). */
+typedef enum {
+  GS_BUF_REC0 = 0,   /* float4 [B][N]: mu_x, mu_y, conic A, conic B */
+  GS_BUF_REC1 = 1,   /* float4 [B][N]: conic C, opacity, red, green */
+  GS_BUF_REC2 = 2,   /* float4 [B][N]: blue, depth, radius (int bits), tiles (uint bits) */
+  GS_BUF_KEYS = 3,   /* uint64 [I]: sorted keys */
+  GS_BUF_VALS = 4,   /* uint32 [I]: sorted Gaussian indices */
+  GS_BUF_RANGES = 5, /* uint32 [bins][2]: [start, end) per bin */
+  GS_BUF_TFINAL = 6, /* float [pixels]: transmittance after the last contributor */
+  GS_BUF_NLAST = 7,  /* uint32 [pixels]: 1 + list position of the last contributor */
+  GS_BUF_G2D = 8     /* float [B][N][12]: dL/d(mu_x, mu_y, A, B, C, opacity, r, g, b) */
+} gs_buffer;
+
+/* *ptr = device pointer of the buffer, *count = number of elements (of the
+ * type listed above) that are valid.  Errors: GS_EINVAL, GS_ESTATE. */
+gs_status gs_get_buffer(gs_ctx* ctx, int32_t which, void** ptr, int64_t* count);
+
+/* Sizes of the last batch: instances I, tile bins, pixels (per channel).
+ * Synchronises the stream to read the device-side instance count. */
+gs_status gs_get_counts(gs_ctx* ctx, int64_t* instances, int64_t* bins, int64_t* pixels);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

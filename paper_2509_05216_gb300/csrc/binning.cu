@@ -1,0 +1,361 @@
+// Binning: scan of tile counts, duplication into (tile, depth) keyed
+// instances, an LSD onesweep radix sort and per-tile ranges.
+//
+// 3D-GS renders tile by tile from a list sorted by (tile, depth) (Section I);
+// each Gaussian is emitted once per 16x16 tile its rect touches with the key
+// (bin << 32) | bits(depth).  Depths are positive FP32 values, so their bit
+// patterns order like the values.  The sort is stable, so equal keys keep the
+// emission order, which is increasing Gaussian index within a bin.
+#include "gs_internal.cuh"
+#include "launch.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------- scan
+
+// Exclusive scan of the per-block instance counts of the projection, one
+// block of 1024 threads looping over chunks; writes the total too.
+__global__ void __launch_bounds__(1024) scan_block_sums_kernel(const uint32_t* __restrict__ sums,
+                                                                int64_t nb, uint32_t* __restrict__ offsets,
+                                                                uint64_t* __restrict__ total) {
+  __shared__ uint64_t warp_tot[32];
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    uint64_t x = i < nb ? sums[i] : 0;
+    uint64_t inc = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t w = warp_tot[lane];
+      uint64_t winc = w;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, winc, off);
+        if (lane >= off) winc += y;
+      }
+      warp_tot[lane] = winc - w;  // exclusive over warps
+    }
+    __syncthreads();
+    const uint64_t excl = carry + warp_tot[wid] + inc - x;
+    if (i < nb) offsets[i] = (uint32_t)excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+void launch_scan_block_sums(const uint32_t* sums, int64_t nb, uint32_t* offsets, uint64_t* total,
+                            cudaStream_t s) {
+  scan_block_sums_kernel<<<1, 1024, 0, s>>>(sums, nb, offsets, total);
+}
+
+// ---------------------------------------------------------------- duplicate
+
+// Same block partition as the projection (one thread per Gaussian, looping
+// over views): instances are emitted in (Gaussian, view, ty, tx) order.
+__global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = g < a.n;
+  uint32_t mine = 0;
+  if (live)
+    for (int v = 0; v < a.B; v++) mine += a.tiles[(int64_t)v * a.stride + g];
+  // block exclusive scan of `mine`
+  __shared__ uint32_t wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = mine;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += y;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t w = lane < nw ? wsum[lane] : 0u;
+    uint32_t winc = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, winc, off);
+      if (lane >= off) winc += y;
+    }
+    wsum[lane] = winc - w;
+  }
+  __syncthreads();
+  if (!live || mine == 0) return;
+  int64_t pos = (int64_t)a.block_offsets[blockIdx.x] + wsum[wid] + (inc - mine);
+  if (pos + mine > a.capacity) {
+    atomicOr(a.status, kStatusCapacity);
+    return;
+  }
+  for (int v = 0; v < a.B; v++) {
+    const int64_t o = (int64_t)v * a.stride + g;
+    if (a.tiles[o] == 0) continue;
+    const ViewRec& V = a.views[v];
+    const float4 r0 = a.rec0[o];
+    const float4 r2 = a.rec2[o];
+    int x0, x1, y0, y1;
+    tile_rect(V, r0.x, r0.y, __float_as_int(r2.z), x0, x1, y0, y1);
+    const uint64_t dbits = (uint64_t)__float_as_uint(r2.y);
+    const int64_t stop = pos + a.tiles[o];  // never write past this view's share
+    for (int ty = y0; ty < y1; ty++)
+      for (int tx = x0; tx < x1 && pos < stop; tx++) {
+        const uint64_t bin = (uint64_t)(V.tile_offset + ty * V.gw + tx);
+        a.keys[pos] = (bin << 32) | dbits;
+        a.vals[pos] = (uint32_t)g;
+        pos++;
+      }
+  }
+}
+
+void launch_duplicate(const DuplicateArgs& a, cudaStream_t s) {
+  const int threads = project_fwd_block();
+  const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
+  duplicate_kernel<<<blocks, threads, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------- onesweep radix sort
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per partition
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr uint32_t kFlagAggregate = 1u << 30;
+constexpr uint32_t kFlagPrefix = 2u << 30;
+constexpr uint32_t kValueMask = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 20;  // about a second of polling
+
+size_t sort_lookback_bytes(int64_t count) {
+  const int64_t parts = (count + kSortTile - 1) / kSortTile;
+  return (size_t)(parts > 0 ? parts : 1) * kRadix * sizeof(uint32_t);
+}
+
+// Digit counts of every pass in one read of the keys.  hist: [npass][256].
+__global__ void __launch_bounds__(256) digit_histogram_kernel(const uint64_t* __restrict__ keys,
+                                                               int64_t count, int npass,
+                                                               uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[8][kRadix];
+  for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    for (int p = 0; p < npass; p++) atomicAdd(&sh[p][(k >> (kRadixBits * p)) & (kRadix - 1)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npass * kRadix; i += blockDim.x) {
+    const uint32_t c = (&sh[0][0])[i];
+    if (c) atomicAdd(&hist[i], c);
+  }
+}
+
+void launch_digit_histogram(const uint64_t* keys, int64_t count, int npass, uint32_t* hist, cudaStream_t s) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t want = (count + 4095) / 4096;
+  const unsigned blocks = (unsigned)(want < 1 ? 1 : (want > (int64_t)sms * 8 ? (int64_t)sms * 8 : want));
+  digit_histogram_kernel<<<blocks, 256, 0, s>>>(keys, count, npass, hist);
+}
+
+// One LSD pass: rank keys of the partition by digit (stable), find the
+// partition's offset for each digit by decoupled look-back over the earlier
+// partitions (bounded waits), then scatter through shared memory so that the
+// global writes are coalesced.  hist_pass: the 256 digit counts of this pass.
+struct SortSmem {
+  uint32_t warp_hist[kSortWarps][kRadix];  // per-warp digit counts -> offsets
+  uint32_t digit_start[kRadix];            // exclusive scan of the tile's digit counts
+  uint32_t global_base[kRadix];            // global destination of the digit's first key
+  uint32_t part;
+  int timed_out;
+  uint64_t keys[kSortTile];
+  uint32_t vals[kSortTile];
+};
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, int64_t count, int shift, const uint32_t* __restrict__ hist_pass,
+    uint32_t* lookback, uint32_t* counter, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    sm.part = atomicAdd(counter, 1u);
+    sm.timed_out = 0;
+  }
+  for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&sm.warp_hist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t part = sm.part;
+  const int64_t nparts = (count + kSortTile - 1) / kSortTile;
+  if ((int64_t)part >= nparts) return;
+  const int64_t base = (int64_t)part * kSortTile;
+
+  // load (warp-striped: warp w owns positions [w * items * 32, ...))
+  uint64_t key[kSortItems];
+  uint32_t val[kSortItems];
+  uint32_t rank[kSortItems];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < kSortItems; i++) {
+    const int64_t p = base + (int64_t)wid * kSortItems * 32 + i * 32 + lane;
+    const bool ok = p < count;
+    key[i] = ok ? kin[p] : ~0ull;
+    val[i] = ok ? vin[p] : 0u;
+    const unsigned vm = __ballot_sync(0xffffffffu, ok);
+    rank[i] = 0xffffffffu;
+    if (ok) {
+      const uint32_t d = (uint32_t)(key[i] >> shift) & (kRadix - 1);
+      const unsigned peers = __match_any_sync(vm, d);
+      const uint32_t before = sm.warp_hist[wid][d];
+      rank[i] = before + __popc(peers & lt);
+      __syncwarp(vm);
+      if ((peers & lt) == 0) sm.warp_hist[wid][d] = before + __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // per digit: counts over warps -> warp offsets; tile count; look-back
+  const uint32_t d = tid;  // kSortThreads == kRadix
+  uint32_t tile_count = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; w++) {
+    const uint32_t c = sm.warp_hist[w][d];
+    sm.warp_hist[w][d] = tile_count;
+    tile_count += c;
+  }
+  volatile uint32_t* lb = lookback;
+  if (part == 0) {
+    lb[d] = kFlagPrefix | tile_count;
+  } else {
+    lb[(int64_t)part * kRadix + d] = kFlagAggregate | tile_count;
+  }
+  uint32_t excl = 0;
+  if (part > 0) {
+    int64_t j = (int64_t)part - 1;
+    int spins = 0;
+    while (true) {
+      const uint32_t w = lb[j * kRadix + d];
+      const uint32_t flag = w & ~kValueMask;
+      if (flag == 0) {
+        if (++spins > kSpinLimit) {
+          sm.timed_out = 1;
+          break;
+        }
+        continue;
+      }
+      excl += w & kValueMask;
+      if (flag == kFlagPrefix) break;
+      if (--j < 0) break;  // partition 0 always publishes a prefix
+    }
+    lb[(int64_t)part * kRadix + d] = kFlagPrefix | ((excl + tile_count) & kValueMask);
+  }
+  // digit starts inside the tile (block exclusive scan over the 256 digits)
+  {
+    uint32_t inc = tile_count;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    __shared__ uint32_t wtot[kSortWarps];
+    if (lane == 31) wtot[wid] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < wid; w++) wpre += wtot[w];
+    sm.digit_start[d] = wpre + inc - tile_count;
+    sm.global_base[d] = hist_pass[d] + excl;
+  }
+  __syncthreads();
+  if (sm.timed_out) {
+    if (tid == 0) atomicOr(status, kStatusTimeout);
+    return;
+  }
+  // local sorted position, through shared memory
+#pragma unroll
+  for (int i = 0; i < kSortItems; i++) {
+    if (rank[i] == 0xffffffffu) continue;
+    const uint32_t dd = (uint32_t)(key[i] >> shift) & (kRadix - 1);
+    const uint32_t lp = sm.digit_start[dd] + sm.warp_hist[wid][dd] + rank[i];
+    sm.keys[lp] = key[i];
+    sm.vals[lp] = val[i];
+  }
+  __syncthreads();
+  const int n_here = (int)((count - base) < kSortTile ? (count - base) : kSortTile);
+  for (int lp = tid; lp < n_here; lp += kSortThreads) {
+    const uint64_t k = sm.keys[lp];
+    const uint32_t dd = (uint32_t)(k >> shift) & (kRadix - 1);
+    const uint32_t dst = sm.global_base[dd] + (lp - sm.digit_start[dd]);
+    if (dst < (uint64_t)count) {
+      kout[dst] = k;
+      vout[dst] = sm.vals[lp];
+    }
+  }
+}
+
+void launch_onesweep_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                          int64_t count, int digit, const uint32_t* hist_pass, uint32_t* lookback,
+                          uint32_t* counter, int* status, cudaStream_t s) {
+  const int64_t parts = (count + kSortTile - 1) / kSortTile;
+  if (parts == 0) return;
+  const size_t smem = sizeof(SortSmem);
+  // (idempotent; set on every call so that each device the library runs on gets it)
+  cudaFuncSetAttribute(onesweep_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  onesweep_pass_kernel<<<(unsigned)parts, kSortThreads, smem, s>>>(kin, vin, kout, vout, count,
+                                                                    kRadixBits * digit, hist_pass,
+                                                                    lookback, counter, status);
+}
+
+// Exclusive scan of a pass's 256 digit counts, in place (one block per pass).
+__global__ void digit_scan_kernel(uint32_t* hist) {
+  __shared__ uint32_t s[kRadix];
+  uint32_t* h = hist + blockIdx.x * kRadix;
+  s[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < kRadix; i++) {
+      const uint32_t c = s[i];
+      s[i] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  h[threadIdx.x] = s[threadIdx.x];
+}
+
+void launch_digit_scan(uint32_t* hist, int npass, cudaStream_t s) {
+  digit_scan_kernel<<<npass, kRadix, 0, s>>>(hist);
+}
+
+// ---------------------------------------------------------------- tile ranges
+
+__global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, int64_t count, uint2* __restrict__ ranges) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t bin = (uint32_t)(keys[i] >> 32);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != bin) ranges[bin].x = (uint32_t)i;
+    if (i == count - 1 || (uint32_t)(keys[i + 1] >> 32) != bin) ranges[bin].y = (uint32_t)(i + 1);
+  }
+}
+
+void launch_tile_ranges(const uint64_t* keys, int64_t count, uint2* ranges, cudaStream_t s) {
+  if (count == 0) return;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  tile_ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, count, ranges);
+}
+
+}  // namespace gs

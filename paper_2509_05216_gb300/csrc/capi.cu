@@ -1,0 +1,507 @@
+// Host side of the C ABI declared in include/gs.h: context, workspaces,
+// argument checks and the launch sequence of each step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gs_internal.cuh"
+#include "launch.h"
+
+namespace gs {
+void launch_digit_scan(uint32_t* hist, int npass, cudaStream_t s);
+}
+
+using namespace gs;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct gs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  gs_config cfg{};
+  std::string err;
+  int* status_d = nullptr;
+  int* status_h = nullptr;     // pinned
+  uint64_t* pinned = nullptr;  // pinned scratch for small read-backs (16 KB)
+  int raster_ppt = 2;
+
+  // last batch
+  int B = 0, deg = 0;
+  int64_t n = 0, stride = 0, bins = 0, pixels = 0, instances = 0, nblocks = 0;
+  bool projected = false, sorted = false, rastered = false;
+  int sorted_in = 0;  // which ping-pong buffer holds the sorted list
+  std::vector<ViewRec> views_h;
+
+  DevBuf views, rec0, rec1, rec2, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
+      hist, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial;
+};
+
+namespace {
+
+gs_status fail(gs_ctx* c, gs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return st;
+}
+
+#define GS_CUDA(ctx, call)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, GS_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                \
+  } while (0)
+
+#define GS_CHECK_LAUNCH(ctx)                                                                    \
+  do {                                                                                          \
+    cudaError_t e_ = cudaGetLastError();                                                        \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(ctx, GS_ECUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                    \
+  } while (0)
+
+gs_status ensure(gs_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return GS_OK;
+  size_t want = bytes + bytes / 8;
+  if (b.p) {
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    GS_CUDA(c, cudaFree(b.p));
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    b.p = nullptr;
+    return fail(c, GS_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", want, cudaGetErrorString(e));
+  }
+  b.cap = want;
+  return GS_OK;
+}
+
+#define GS_TRY(expr)                  \
+  do {                                \
+    gs_status s_ = (expr);            \
+    if (s_ != GS_OK) return s_;       \
+  } while (0)
+
+template <class T>
+T* P(DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+gs_status check_params(gs_ctx* c, const gs_params* p, const char* what) {
+  if (!p) return fail(c, GS_EINVAL, "%s is NULL", what);
+  if (!p->data) return fail(c, GS_EINVAL, "%s->data is NULL", what);
+  if (p->n <= 0) return fail(c, GS_EINVAL, "%s->n must be > 0", what);
+  if (p->n >= (int64_t)1 << 31) return fail(c, GS_EINVAL, "%s->n too large", what);
+  if (p->stride < p->n || p->stride % 4 != 0)
+    return fail(c, GS_EINVAL, "%s->stride must be >= n and a multiple of 4", what);
+  if (p->sh_degree < 0 || p->sh_degree > 3) return fail(c, GS_EINVAL, "%s->sh_degree must be 0..3", what);
+  if (reinterpret_cast<uintptr_t>(p->data) % 16 != 0) return fail(c, GS_EINVAL, "%s->data not 16-byte aligned", what);
+  return GS_OK;
+}
+
+void set_device(gs_ctx* c) { cudaSetDevice(c->device); }
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_create(gs_ctx** out, int device, const gs_config* cfg) {
+  if (!out) return GS_EINVAL;
+  *out = nullptr;
+  gs_config conf{};
+  if (cfg) conf = *cfg;
+  if (conf.max_views == 0) conf.max_views = kMaxViews;
+  if (conf.max_views < 0 || conf.max_views > kMaxViews) return GS_EINVAL;
+  if (conf.max_gaussians < 0 || conf.instance_capacity < 0) return GS_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    (void)cudaGetLastError();
+    return GS_ECUDA;
+  }
+  gs_ctx* c = new gs_ctx();
+  c->device = device;
+  c->cfg = conf;
+  if (const char* e = getenv("GS_RASTER_PPT")) {
+    int v = atoi(e);
+    if (v == 1 || v == 2 || v == 4) c->raster_ppt = v;
+  }
+  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&c->status_d, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->status_d, 0, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->status_h, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->pinned, 16384) != cudaSuccess) {
+    (void)cudaGetLastError();
+    gs_destroy(c);
+    return GS_ECUDA;
+  }
+  *out = c;
+  return GS_OK;
+}
+
+void gs_destroy(gs_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  DevBuf* bufs[] = {&c->views, &c->rec0, &c->rec1, &c->rec2, &c->tiles, &c->block_sums, &c->block_offsets,
+                    &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->lookback,
+                    &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (c->status_d) cudaFree(c->status_d);
+  if (c->status_h) cudaFreeHost(c->status_h);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+}
+
+const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+gs_status gs_set_stream(gs_ctx* c, void* stream) {
+  if (!c) return GS_EINVAL;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  return GS_OK;
+}
+
+gs_status gs_sync(gs_ctx* c) {
+  if (!c) return GS_EINVAL;
+  set_device(c);
+  GS_CUDA(c, cudaMemcpyAsync(c->status_h, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int st = *c->status_h;
+  if (st & kStatusTimeout) return fail(c, GS_ETIMEOUT, "a bounded device-side wait ran out");
+  if (st & kStatusCapacity) return fail(c, GS_ECAPACITY, "instance capacity exceeded");
+  return GS_OK;
+}
+
+gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, int32_t B) {
+  if (!c) return GS_EINVAL;
+  GS_TRY(check_params(c, params, "params"));
+  if (!cams) return fail(c, GS_EINVAL, "cams is NULL");
+  if (B < 1 || B > c->cfg.max_views) return fail(c, GS_EINVAL, "B must be in 1..%d", c->cfg.max_views);
+  set_device(c);
+  c->projected = c->sorted = c->rastered = false;
+  c->views_h.assign(B, ViewRec{});
+  int64_t tile_off = 0, pix_off = 0;
+  for (int v = 0; v < B; v++) {
+    const gs_camera& k = cams[v];
+    if (k.width <= 0 || k.height <= 0 || k.width > 65536 || k.height > 65536)
+      return fail(c, GS_EINVAL, "camera %d: bad size %dx%d", v, k.width, k.height);
+    if (!(k.fx > 0.f) || !(k.fy > 0.f)) return fail(c, GS_EINVAL, "camera %d: focal must be > 0", v);
+    ViewRec& r = c->views_h[v];
+    for (int i = 0; i < 3; i++) {
+      for (int j = 0; j < 3; j++) r.R[3 * i + j] = k.viewmat[4 * i + j];
+      r.t[i] = k.viewmat[4 * i + 3];
+    }
+    r.fx = k.fx; r.fy = k.fy; r.cx = k.cx; r.cy = k.cy;
+    r.znear = k.znear;
+    r.limx = (float)(1.3 * (double)k.width / (2.0 * (double)k.fx));
+    r.limy = (float)(1.3 * (double)k.height / (2.0 * (double)k.fy));
+    for (int j = 0; j < 3; j++) {
+      double s = 0.0;
+      for (int i = 0; i < 3; i++) s -= (double)k.viewmat[4 * i + j] * (double)k.viewmat[4 * i + 3];
+      r.campos[j] = (float)s;
+      r.bg[j] = k.bg[j];
+    }
+    r.W = k.width; r.H = k.height;
+    r.gw = (k.width + kTile - 1) / kTile;
+    r.gh = (k.height + kTile - 1) / kTile;
+    r.tile_offset = (int)tile_off;
+    r.pix_offset = pix_off;
+    tile_off += (int64_t)r.gw * r.gh;
+    pix_off += (int64_t)k.width * k.height;
+  }
+  if (tile_off >= ((int64_t)1 << 31)) return fail(c, GS_EINVAL, "too many tiles in the batch");
+  const int64_t n = params->n, stride = params->stride;
+  const int64_t nb = (n + project_fwd_block() - 1) / project_fwd_block();
+  GS_TRY(ensure(c, c->views, sizeof(ViewRec) * B));
+  GS_TRY(ensure(c, c->rec0, sizeof(float4) * B * stride));
+  GS_TRY(ensure(c, c->rec1, sizeof(float4) * B * stride));
+  GS_TRY(ensure(c, c->rec2, sizeof(float4) * B * stride));
+  GS_TRY(ensure(c, c->tiles, sizeof(uint32_t) * B * stride));
+  GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * nb));
+  GS_CUDA(c, cudaMemcpyAsync(c->views.p, c->views_h.data(), sizeof(ViewRec) * B, cudaMemcpyHostToDevice,
+                             c->stream));
+  ProjectArgs a{};
+  a.params = params->data;
+  a.n = n;
+  a.stride = stride;
+  a.views = P<ViewRec>(c->views);
+  a.B = B;
+  a.rec0 = P<float4>(c->rec0);
+  a.rec1 = P<float4>(c->rec1);
+  a.rec2 = P<float4>(c->rec2);
+  a.tiles = P<uint32_t>(c->tiles);
+  a.block_sums = P<uint32_t>(c->block_sums);
+  launch_project_fwd(a, params->sh_degree, c->stream);
+  GS_CHECK_LAUNCH(c);
+  c->B = B;
+  c->n = n;
+  c->stride = stride;
+  c->deg = params->sh_degree;
+  c->bins = tile_off;
+  c->pixels = pix_off;
+  c->nblocks = nb;
+  c->projected = true;
+  return GS_OK;
+}
+
+gs_status gs_bin_sort(gs_ctx* c) {
+  if (!c) return GS_EINVAL;
+  if (!c->projected) return fail(c, GS_ESTATE, "gs_bin_sort needs gs_project first");
+  set_device(c);
+  c->sorted = c->rastered = false;
+  GS_TRY(ensure(c, c->block_offsets, sizeof(uint32_t) * c->nblocks));
+  GS_TRY(ensure(c, c->total, sizeof(uint64_t)));
+  launch_scan_block_sums(P<uint32_t>(c->block_sums), c->nblocks, P<uint32_t>(c->block_offsets),
+                         P<uint64_t>(c->total), c->stream);
+  GS_CHECK_LAUNCH(c);
+  int64_t I;
+  if (c->cfg.instance_capacity > 0) {
+    return fail(c, GS_EINVAL, "fixed instance capacity is not supported by gs_bin_sort yet");
+  }
+  GS_CUDA(c, cudaMemcpyAsync(c->pinned, c->total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  I = (int64_t)c->pinned[0];
+  if (I >= ((int64_t)1 << 30) - 1) return fail(c, GS_ECAPACITY, "%lld instances exceed 2^30", (long long)I);
+  c->instances = I;
+  GS_TRY(ensure(c, c->keys0, sizeof(uint64_t) * I));
+  GS_TRY(ensure(c, c->keys1, sizeof(uint64_t) * I));
+  GS_TRY(ensure(c, c->vals0, sizeof(uint32_t) * I));
+  GS_TRY(ensure(c, c->vals1, sizeof(uint32_t) * I));
+  GS_TRY(ensure(c, c->ranges, sizeof(uint2) * c->bins));
+  DuplicateArgs d{};
+  d.n = c->n;
+  d.stride = c->stride;
+  d.views = P<ViewRec>(c->views);
+  d.B = c->B;
+  d.rec0 = P<float4>(c->rec0);
+  d.rec2 = P<float4>(c->rec2);
+  d.tiles = P<uint32_t>(c->tiles);
+  d.block_offsets = P<uint32_t>(c->block_offsets);
+  d.keys = P<uint64_t>(c->keys0);
+  d.vals = P<uint32_t>(c->vals0);
+  d.capacity = I;
+  d.status = c->status_d;
+  launch_duplicate(d, c->stream);
+  GS_CHECK_LAUNCH(c);
+
+  // radix passes over the 32 depth bits and the bits of the largest bin
+  int bin_bits = 0;
+  while (((int64_t)1 << bin_bits) < c->bins) bin_bits++;
+  const int npass = (32 + bin_bits + 7) / 8;
+  int cur = 0;
+  if (I > 1) {
+    GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
+    GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * 8 * 256, c->stream));
+    launch_digit_histogram(P<uint64_t>(c->keys0), I, npass, P<uint32_t>(c->hist), c->stream);
+    GS_CHECK_LAUNCH(c);
+    uint32_t* h_host = reinterpret_cast<uint32_t*>(c->pinned);
+    GS_CUDA(c, cudaMemcpyAsync(h_host, c->hist.p, sizeof(uint32_t) * npass * 256, cudaMemcpyDeviceToHost,
+                               c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<int> passes;
+    for (int p = 0; p < npass; p++) {
+      bool trivial = false;
+      for (int d = 0; d < 256; d++)
+        if ((int64_t)h_host[p * 256 + d] == I) trivial = true;
+      if (!trivial) passes.push_back(p);
+    }
+    launch_digit_scan(P<uint32_t>(c->hist), npass, c->stream);
+    GS_CHECK_LAUNCH(c);
+    const size_t lb = sort_lookback_bytes(I);
+    if (!passes.empty()) {
+      GS_TRY(ensure(c, c->lookback, lb * passes.size()));
+      GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
+      GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * passes.size(), c->stream));
+      GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * 8, c->stream));
+    }
+    for (size_t q = 0; q < passes.size(); q++) {
+      const int p = passes[q];
+      const uint64_t* kin = P<uint64_t>(cur ? c->keys1 : c->keys0);
+      const uint32_t* vin = P<uint32_t>(cur ? c->vals1 : c->vals0);
+      uint64_t* kout = P<uint64_t>(cur ? c->keys0 : c->keys1);
+      uint32_t* vout = P<uint32_t>(cur ? c->vals0 : c->vals1);
+      launch_onesweep_pass(kin, vin, kout, vout, I, p, P<uint32_t>(c->hist) + p * 256,
+                           reinterpret_cast<uint32_t*>(P<unsigned char>(c->lookback) + lb * q),
+                           P<uint32_t>(c->counters) + q, c->status_d, c->stream);
+      GS_CHECK_LAUNCH(c);
+      cur ^= 1;
+    }
+  }
+  GS_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * c->bins, c->stream));
+  launch_tile_ranges(P<uint64_t>(cur ? c->keys1 : c->keys0), I, P<uint2>(c->ranges), c->stream);
+  GS_CHECK_LAUNCH(c);
+  c->sorted_in = cur;
+  c->sorted = true;
+  return GS_OK;
+}
+
+static RasterArgs raster_args(gs_ctx* c) {
+  RasterArgs r{};
+  r.views = P<ViewRec>(c->views);
+  r.B = c->B;
+  r.stride = c->stride;
+  r.ranges = P<uint2>(c->ranges);
+  r.vals = P<uint32_t>(c->sorted_in ? c->vals1 : c->vals0);
+  r.rec0 = P<float4>(c->rec0);
+  r.rec1 = P<float4>(c->rec1);
+  r.rec2 = P<float4>(c->rec2);
+  r.tfinal = P<float>(c->tfinal);
+  r.nlast = P<uint32_t>(c->nlast);
+  return r;
+}
+
+gs_status gs_raster_fwd(gs_ctx* c, float* images) {
+  if (!c) return GS_EINVAL;
+  if (!c->sorted) return fail(c, GS_ESTATE, "gs_raster_fwd needs gs_bin_sort first");
+  if (!images) return fail(c, GS_EINVAL, "images is NULL");
+  set_device(c);
+  GS_TRY(ensure(c, c->tfinal, sizeof(float) * c->pixels));
+  GS_TRY(ensure(c, c->nlast, sizeof(uint32_t) * c->pixels));
+  RasterArgs r = raster_args(c);
+  r.image = images;
+  launch_raster_fwd(r, c->bins, c->raster_ppt, c->stream);
+  GS_CHECK_LAUNCH(c);
+  c->rastered = true;
+  return GS_OK;
+}
+
+gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dimages, gs_params* grads) {
+  if (!c) return GS_EINVAL;
+  if (!c->rastered) return fail(c, GS_ESTATE, "gs_raster_bwd needs gs_raster_fwd first");
+  GS_TRY(check_params(c, params, "params"));
+  GS_TRY(check_params(c, grads, "grads"));
+  if (!dL_dimages) return fail(c, GS_EINVAL, "dL_dimages is NULL");
+  if (params->n != c->n || params->stride != c->stride || params->sh_degree != c->deg)
+    return fail(c, GS_EINVAL, "params differ from the projected set");
+  if (grads->n != c->n || grads->stride != c->stride || grads->sh_degree != c->deg)
+    return fail(c, GS_EINVAL, "grads must match params in n, stride and sh_degree");
+  set_device(c);
+  const size_t g2d_bytes = sizeof(float4) * 3 * c->B * c->stride;
+  GS_TRY(ensure(c, c->g2d, g2d_bytes));
+  GS_CUDA(c, cudaMemsetAsync(c->g2d.p, 0, g2d_bytes, c->stream));
+  RasterArgs r = raster_args(c);
+  r.dimage = dL_dimages;
+  r.g2d = P<float4>(c->g2d);
+  launch_raster_bwd(r, c->bins, c->raster_ppt, c->stream);
+  GS_CHECK_LAUNCH(c);
+  ProjectBwdArgs b{};
+  b.params = params->data;
+  b.n = c->n;
+  b.stride = c->stride;
+  b.views = P<ViewRec>(c->views);
+  b.B = c->B;
+  b.g2d = P<float4>(c->g2d);
+  b.grads = grads->data;
+  if (grads->stride > grads->n) {
+    // padding columns are not written by the kernel; keep them zero
+    GS_CUDA(c, cudaMemsetAsync(grads->data, 0, sizeof(float) * n_planes(c->deg) * grads->stride, c->stream));
+  }
+  launch_project_bwd(b, c->deg, c->stream);
+  GS_CHECK_LAUNCH(c);
+  return GS_OK;
+}
+
+gs_status gs_l1_loss(gs_ctx* c, const float* x, const float* y, int64_t count, float* loss, float* dL_dx) {
+  if (!c) return GS_EINVAL;
+  if (!x || !y) return fail(c, GS_EINVAL, "x and y must not be NULL");
+  if (count <= 0) return fail(c, GS_EINVAL, "count must be > 0");
+  set_device(c);
+  const int parts = l1_parts(count);
+  GS_TRY(ensure(c, c->l1_partial, sizeof(float) * parts));
+  launch_l1(x, y, count, P<float>(c->l1_partial), parts, loss, dL_dx, c->stream);
+  GS_CHECK_LAUNCH(c);
+  return GS_OK;
+}
+
+gs_status gs_adam(gs_ctx* c, gs_params* p, const gs_params* g, gs_params* m, gs_params* v,
+                  const gs_adam_hp* hp, int64_t step) {
+  if (!c) return GS_EINVAL;
+  GS_TRY(check_params(c, p, "p"));
+  GS_TRY(check_params(c, g, "g"));
+  GS_TRY(check_params(c, m, "m"));
+  GS_TRY(check_params(c, v, "v"));
+  if (!hp) return fail(c, GS_EINVAL, "hp is NULL");
+  if (step < 1) return fail(c, GS_EINVAL, "step must be >= 1");
+  const gs_params* all[3] = {g, m, v};
+  for (const gs_params* q : all)
+    if (q->n != p->n || q->stride != p->stride || q->sh_degree != p->sh_degree)
+      return fail(c, GS_EINVAL, "p, g, m, v must share n, stride and sh_degree");
+  set_device(c);
+  AdamArgs a{};
+  a.p = p->data;
+  a.g = g->data;
+  a.m = m->data;
+  a.v = v->data;
+  a.stride = p->stride;
+  a.planes = n_planes(p->sh_degree);
+  const double bc1 = 1.0 - std::pow((double)hp->beta1, (double)step);
+  const double bc2 = 1.0 - std::pow((double)hp->beta2, (double)step);
+  for (int pl = 0; pl < a.planes; pl++) {
+    double lr;
+    if (pl < 3) lr = hp->lr_mean;
+    else if (pl < 6) lr = hp->lr_scale;
+    else if (pl < 10) lr = hp->lr_quat;
+    else if (pl < 11) lr = hp->lr_opacity;
+    else if (pl < 14) lr = hp->lr_sh_dc;
+    else lr = hp->lr_sh_rest;
+    a.lr[pl] = (float)(lr / bc1);
+  }
+  a.beta1 = hp->beta1;
+  a.beta2 = hp->beta2;
+  a.eps = hp->eps;
+  a.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
+  launch_adam(a, c->stream);
+  GS_CHECK_LAUNCH(c);
+  return GS_OK;
+}
+
+gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
+  if (!c || !ptr || !count) return GS_EINVAL;
+  const int64_t bn = (int64_t)c->B * c->stride;
+  switch (which) {
+    case GS_BUF_REC0: if (!c->projected) return GS_ESTATE; *ptr = c->rec0.p; *count = bn; break;
+    case GS_BUF_REC1: if (!c->projected) return GS_ESTATE; *ptr = c->rec1.p; *count = bn; break;
+    case GS_BUF_REC2: if (!c->projected) return GS_ESTATE; *ptr = c->rec2.p; *count = bn; break;
+    case GS_BUF_KEYS: if (!c->sorted) return GS_ESTATE; *ptr = c->sorted_in ? c->keys1.p : c->keys0.p; *count = c->instances; break;
+    case GS_BUF_VALS: if (!c->sorted) return GS_ESTATE; *ptr = c->sorted_in ? c->vals1.p : c->vals0.p; *count = c->instances; break;
+    case GS_BUF_RANGES: if (!c->sorted) return GS_ESTATE; *ptr = c->ranges.p; *count = c->bins; break;
+    case GS_BUF_TFINAL: if (!c->rastered) return GS_ESTATE; *ptr = c->tfinal.p; *count = c->pixels; break;
+    case GS_BUF_NLAST: if (!c->rastered) return GS_ESTATE; *ptr = c->nlast.p; *count = c->pixels; break;
+    case GS_BUF_G2D: if (!c->g2d.p) return GS_ESTATE; *ptr = c->g2d.p; *count = bn; break;
+    default: return fail(c, GS_EINVAL, "unknown buffer %d", which);
+  }
+  return GS_OK;
+}
+
+gs_status gs_get_counts(gs_ctx* c, int64_t* instances, int64_t* bins, int64_t* pixels) {
+  if (!c) return GS_EINVAL;
+  if (!c->projected) return fail(c, GS_ESTATE, "no batch projected");
+  set_device(c);
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (instances) *instances = c->sorted ? c->instances : -1;
+  if (bins) *bins = c->bins;
+  if (pixels) *pixels = c->pixels;
+  return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// L1 photometric loss and the Adam update.
+//
+// The paper fits the Gaussians to the orbit views (Section III); the loss is
+// the mean absolute error between rendered and target images and the
+// optimiser is Adam with bias correction (torch.optim.Adam semantics), one
+// learning rate per parameter group.
+#include "gs_internal.cuh"
+#include "launch.h"
+
+namespace gs {
+
+constexpr int kL1Threads = 256;
+
+int l1_parts(int64_t count) {
+  int64_t parts = (count + kL1Threads * 16 - 1) / (kL1Threads * 16);
+  if (parts < 1) parts = 1;
+  if (parts > 152 * 8) parts = 152 * 8;
+  return (int)parts;
+}
+
+__global__ void __launch_bounds__(kL1Threads) l1_kernel(const float* __restrict__ x, const float* __restrict__ y,
+                                                        int64_t count, float inv_count, float* __restrict__ grad,
+                                                        float* __restrict__ partial) {
+  float s = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = x[i] - y[i];
+    s += fabsf(d);
+    if (grad) grad[i] = d > 0.f ? inv_count : (d < 0.f ? -inv_count : 0.f);
+  }
+  __shared__ float red[kL1Threads / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < kL1Threads / 32; w++) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void l1_finish_kernel(const float* __restrict__ partial, int nparts, double inv_count, float* loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nparts; i++) t += partial[i];
+    *loss = (float)(t * inv_count);
+  }
+}
+
+void launch_l1(const float* x, const float* y, int64_t count, float* partial, int nparts, float* loss,
+               float* grad, cudaStream_t s) {
+  const float inv = (float)(1.0 / (double)count);
+  l1_kernel<<<nparts, kL1Threads, 0, s>>>(x, y, count, inv, grad, partial);
+  if (loss) l1_finish_kernel<<<1, 32, 0, s>>>(partial, nparts, 1.0 / (double)count, loss);
+}
+
+// Adam over [planes][stride] float planes, float4 at a time (stride % 4 == 0,
+// so a vector never straddles two planes).
+__global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
+  const int64_t n4 = (int64_t)a.planes * a.stride / 4;
+  const int64_t per_plane4 = a.stride / 4;
+  float4* p4 = reinterpret_cast<float4*>(a.p);
+  const float4* g4 = reinterpret_cast<const float4*>(a.g);
+  float4* m4 = reinterpret_cast<float4*>(a.m);
+  float4* v4 = reinterpret_cast<float4*>(a.v);
+  const float b1 = a.beta1, b2 = a.beta2, c1 = 1.f - a.beta1, c2 = 1.f - a.beta2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const float lr = a.lr[i / per_plane4];
+    const float4 g = g4[i];
+    float4 m = m4[i], v = v4[i], p = p4[i];
+#define ADAM_LANE(f)                                                  \
+  m.f = fmaf(b1, m.f, c1 * g.f);                                      \
+  v.f = fmaf(b2, v.f, c2 * g.f * g.f);                                \
+  p.f -= lr * m.f / fmaf(sqrtf(v.f), a.inv_sqrt_bc2, a.eps);
+    ADAM_LANE(x) ADAM_LANE(y) ADAM_LANE(z) ADAM_LANE(w)
+#undef ADAM_LANE
+    m4[i] = m;
+    v4[i] = v;
+    p4[i] = p;
+  }
+}
+
+void launch_adam(const AdamArgs& a, cudaStream_t s) {
+  const int64_t n4 = (int64_t)a.planes * a.stride / 4;
+  int64_t blocks = (n4 + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+}
+
+}  // namespace gs

@@ -1,0 +1,406 @@
+// EWA projection of 3D Gaussians to 2D conics with view-dependent SH colour,
+// forward (per view and Gaussian) and backward (chain rule to the parameters,
+// summed over the views of a batch).
+//
+// The paper initialises 3D-GS primitives from isosurface points and fits them
+// to orbit views (Section III); the projection is the EWA splatting step of
+// 3D-GS (Section I): Sigma' = J W Sigma W^T J^T + 0.3 I, conic = Sigma'^-1,
+// radius ceil(3 sqrt(lambda_max)), colour max(0, SH(d) + 0.5).
+//
+// Layout: one thread per Gaussian loads its parameters once (coalesced plane
+// reads) and loops over the B views, so a batch reads the parameter set once.
+#include "gs_internal.cuh"
+#include "launch.h"
+
+namespace gs {
+
+template <int DEG>
+struct ShEval {
+  static constexpr int K = (DEG + 1) * (DEG + 1);
+  // Y[k] of the unit direction (x, y, z): the unit-sphere forms of the
+  // real harmonics' Cartesian polynomials.
+  __device__ __forceinline__ static void basis(float x, float y, float z, float* Y) {
+    Y[0] = kSH0;
+    if (DEG < 1) return;
+    Y[1] = kSH1 * y;
+    Y[2] = kSH1 * z;
+    Y[3] = kSH1 * x;
+    if (DEG < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kSH2a * x * y;
+    Y[5] = kSH2a * y * z;
+    Y[6] = kSH2b * (3.f * zz - 1.f);
+    Y[7] = kSH2a * x * z;
+    Y[8] = kSH2c * (xx - yy);
+    if (DEG < 3) return;
+    Y[9] = kSH3e * y * (3.f * xx - yy);
+    Y[10] = kSH3f * x * y * z;
+    Y[11] = kSH3g * y * (5.f * zz - 1.f);
+    Y[12] = kSH3h * z * (5.f * zz - 3.f);
+    Y[13] = kSH3g * x * (5.f * zz - 1.f);
+    Y[14] = kSH3k * z * (xx - yy);
+    Y[15] = kSH3e * x * (xx - 3.f * yy);
+  }
+  // g += sum_k w[k] grad Y_k(x, y, z)
+  __device__ __forceinline__ static void grad(float x, float y, float z, const float* w, float& gx,
+                                              float& gy, float& gz) {
+    gx = gy = gz = 0.f;
+    if (DEG < 1) return;
+    gy += kSH1 * w[1];
+    gz += kSH1 * w[2];
+    gx += kSH1 * w[3];
+    if (DEG < 2) return;
+    gx += kSH2a * (y * w[4] + z * w[7]) + 2.f * kSH2c * x * w[8];
+    gy += kSH2a * (x * w[4] + z * w[5]) - 2.f * kSH2c * y * w[8];
+    gz += kSH2a * (y * w[5] + x * w[7]) + 6.f * kSH2b * z * w[6];
+    if (DEG < 3) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx += kSH3e * 6.f * x * y * w[9] + kSH3f * y * z * w[10] + kSH3g * (5.f * zz - 1.f) * w[13] +
+          2.f * kSH3k * x * z * w[14] + kSH3e * 3.f * (xx - yy) * w[15];
+    gy += kSH3e * 3.f * (xx - yy) * w[9] + kSH3f * x * z * w[10] + kSH3g * (5.f * zz - 1.f) * w[11] -
+          2.f * kSH3k * y * z * w[14] - kSH3e * 6.f * x * y * w[15];
+    gz += kSH3f * x * y * w[10] + 10.f * kSH3g * y * z * w[11] + kSH3h * (15.f * zz - 3.f) * w[12] +
+          10.f * kSH3g * x * z * w[13] + kSH3k * (xx - yy) * w[14];
+  }
+};
+
+// Intermediate values of one (view, Gaussian) projection.
+struct ProjState {
+  float tx, ty, tz;
+  float ux, uy;       // clamped slopes used in J
+  bool clx, cly;      // slope clamped
+  float s[3];         // exp(log-scale)
+  float qn[4];        // normalised quaternion
+  float qinv;         // 1 / |q|
+  float Rq[9];        // rotation of the normalised quaternion
+  float Sig[6];       // Sigma: 00 01 02 11 12 22
+  float T[6];         // J W (2x3, row-major)
+  float c00, c01, c11, det;
+};
+
+// Covariance part of the projection (shared by forward and backward).
+__device__ __forceinline__ void project_cov(const ViewRec& V, const float* mean, const float* lsc,
+                                            const float* quat, float depth, ProjState& st) {
+  const float* R = V.R;
+  st.tx = fmaf(R[0], mean[0], fmaf(R[1], mean[1], fmaf(R[2], mean[2], V.t[0])));
+  st.ty = fmaf(R[3], mean[0], fmaf(R[4], mean[1], fmaf(R[5], mean[2], V.t[1])));
+  st.tz = depth;
+  float ux = st.tx / st.tz, uy = st.ty / st.tz;
+  st.clx = fabsf(ux) > V.limx;
+  st.cly = fabsf(uy) > V.limy;
+  st.ux = fminf(fmaxf(ux, -V.limx), V.limx);
+  st.uy = fminf(fmaxf(uy, -V.limy), V.limy);
+
+  for (int i = 0; i < 3; i++) st.s[i] = expf(lsc[i]);
+  float qq = quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3];
+  st.qinv = rsqrtf(qq);
+  for (int i = 0; i < 4; i++) st.qn[i] = quat[i] * st.qinv;
+  const float w = st.qn[0], x = st.qn[1], y = st.qn[2], z = st.qn[3];
+  float* Q = st.Rq;
+  Q[0] = 1.f - 2.f * (y * y + z * z);
+  Q[1] = 2.f * (x * y - w * z);
+  Q[2] = 2.f * (x * z + w * y);
+  Q[3] = 2.f * (x * y + w * z);
+  Q[4] = 1.f - 2.f * (x * x + z * z);
+  Q[5] = 2.f * (y * z - w * x);
+  Q[6] = 2.f * (x * z - w * y);
+  Q[7] = 2.f * (y * z + w * x);
+  Q[8] = 1.f - 2.f * (x * x + y * y);
+  float M[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) M[3 * i + j] = Q[3 * i + j] * st.s[j];
+  st.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  st.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  st.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  st.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  st.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  st.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+
+  const float itz = 1.f / st.tz;
+  const float J00 = V.fx * itz, J02 = -V.fx * st.ux * itz;
+  const float J11 = V.fy * itz, J12 = -V.fy * st.uy * itz;
+  for (int j = 0; j < 3; j++) {
+    st.T[j] = J00 * R[j] + J02 * R[6 + j];
+    st.T[3 + j] = J11 * R[3 + j] + J12 * R[6 + j];
+  }
+  // Sigma' = T Sigma T^T + 0.3 I
+  const float* S = st.Sig;
+  float a[3], b[3];  // a = Sigma T0^T, b = Sigma T1^T
+  a[0] = S[0] * st.T[0] + S[1] * st.T[1] + S[2] * st.T[2];
+  a[1] = S[1] * st.T[0] + S[3] * st.T[1] + S[4] * st.T[2];
+  a[2] = S[2] * st.T[0] + S[4] * st.T[1] + S[5] * st.T[2];
+  b[0] = S[0] * st.T[3] + S[1] * st.T[4] + S[2] * st.T[5];
+  b[1] = S[1] * st.T[3] + S[3] * st.T[4] + S[4] * st.T[5];
+  b[2] = S[2] * st.T[3] + S[4] * st.T[4] + S[5] * st.T[5];
+  st.c00 = st.T[0] * a[0] + st.T[1] * a[1] + st.T[2] * a[2] + kDilation;
+  st.c01 = st.T[3] * a[0] + st.T[4] * a[1] + st.T[5] * a[2];
+  st.c11 = st.T[3] * b[0] + st.T[4] * b[1] + st.T[5] * b[2] + kDilation;
+  st.det = st.c00 * st.c11 - st.c01 * st.c01;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
+  constexpr int K = ShEval<DEG>::K;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = g < a.n;
+  float mean[3], lsc[3], quat[4], op = 0.f, sh[3 * K];
+  if (live) {
+    const float* P = a.params;
+    const int64_t S = a.stride;
+#pragma unroll
+    for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
+#pragma unroll
+    for (int i = 0; i < 3; i++) lsc[i] = __ldg(P + (3 + i) * S + g);
+#pragma unroll
+    for (int i = 0; i < 4; i++) quat[i] = __ldg(P + (6 + i) * S + g);
+    op = __ldg(P + 10 * S + g);
+#pragma unroll
+    for (int i = 0; i < 3 * K; i++) sh[i] = __ldg(P + (11 + i) * S + g);
+  }
+  const float opacity = 1.f / (1.f + expf(-op));
+  uint32_t total = 0;
+  for (int v = 0; v < a.B; v++) {
+    const ViewRec& V = a.views[v];
+    const int64_t o = (int64_t)v * a.stride + g;
+    uint32_t tiles = 0;
+    int radius = 0;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    float depth = 0.f, blue = 0.f;
+    if (live) {
+      depth = depth_key(V, mean[0], mean[1], mean[2]);
+      if (depth > V.znear) {
+        ProjState st;
+        project_cov(V, mean, lsc, quat, depth, st);
+        if (st.det != 0.f) {
+          const float idet = 1.f / st.det;
+          const float mid = 0.5f * (st.c00 + st.c11);
+          const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - st.det));
+          radius = (int)ceilf(3.f * sqrtf(lam));
+          const float mx = fmaf(V.fx, st.tx / st.tz, V.cx);
+          const float my = fmaf(V.fy, st.ty / st.tz, V.cy);
+          int x0, x1, y0, y1;
+          if (radius > 0 && tile_rect(V, mx, my, radius, x0, x1, y0, y1)) {
+            tiles = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+            // colour
+            float dx = mean[0] - V.campos[0], dy = mean[1] - V.campos[1], dz = mean[2] - V.campos[2];
+            const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= inv; dy *= inv; dz *= inv;
+            float Y[K];
+            ShEval<DEG>::basis(dx, dy, dz, Y);
+            float rgb[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              float acc = 0.5f;
+#pragma unroll
+              for (int k = 0; k < K; k++) acc = fmaf(sh[3 * k + c], Y[k], acc);
+              rgb[c] = fmaxf(acc, 0.f);
+            }
+            r0 = make_float4(mx, my, st.c11 * idet, -st.c01 * idet);
+            r1 = make_float4(st.c00 * idet, opacity, rgb[0], rgb[1]);
+            blue = rgb[2];
+          } else {
+            radius = 0;
+          }
+        }
+      }
+      a.rec0[o] = r0;
+      a.rec1[o] = r1;
+      a.rec2[o] = make_float4(blue, depth, __int_as_float(tiles ? radius : 0), __uint_as_float(tiles));
+      a.tiles[o] = tiles;
+    }
+    total += tiles;
+  }
+  // block total of the instance counts (for the scan)
+  __shared__ uint32_t red[32];
+  uint32_t s = total;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0u;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) a.block_sums[blockIdx.x] = s;
+  }
+}
+
+// Backward: dL/d(mu2D, conic, opacity, rgb) per (view, Gaussian) -> dL/dparams.
+template <int DEG>
+__global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
+  constexpr int K = ShEval<DEG>::K;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n) return;
+  const float* P = a.params;
+  const int64_t S = a.stride;
+  float mean[3], lsc[3], quat[4];
+#pragma unroll
+  for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
+#pragma unroll
+  for (int i = 0; i < 3; i++) lsc[i] = __ldg(P + (3 + i) * S + g);
+#pragma unroll
+  for (int i = 0; i < 4; i++) quat[i] = __ldg(P + (6 + i) * S + g);
+  const float op = __ldg(P + 10 * S + g);
+  const float opacity = 1.f / (1.f + expf(-op));
+
+  float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gop = 0.f;
+  float gsh[3 * K];
+#pragma unroll
+  for (int i = 0; i < 3 * K; i++) gsh[i] = 0.f;
+
+  for (int v = 0; v < a.B; v++) {
+    const int64_t o = ((int64_t)v * S + g) * 3;
+    const float4 g0 = a.g2d[o], g1 = a.g2d[o + 1], g2 = a.g2d[o + 2];
+    if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
+        g1.z == 0.f && g1.w == 0.f && g2.x == 0.f)
+      continue;
+    const ViewRec& V = a.views[v];
+    const float depth = depth_key(V, mean[0], mean[1], mean[2]);
+    if (!(depth > V.znear)) continue;
+    ProjState st;
+    project_cov(V, mean, lsc, quat, depth, st);
+    const float gmx = g0.x, gmy = g0.y, gA = g0.z, gB = g0.w, gC = g1.x, gsig = g1.y;
+    const float grgb[3] = {g1.z, g1.w, g2.x};
+
+    // conic = (c11, -c01, c00) / det  ->  Sigma'
+    const float id = 1.f / st.det, id2 = id * id;
+    const float c00 = st.c00, c01 = st.c01, c11 = st.c11;
+    const float gc00 = gA * (-c11 * c11 * id2) + gB * (c01 * c11 * id2) + gC * (id - c00 * c11 * id2);
+    const float gc11 = gA * (id - c00 * c11 * id2) + gB * (c01 * c00 * id2) + gC * (-c00 * c00 * id2);
+    const float gc01 = gA * (2.f * c11 * c01 * id2) + gB * (-id - 2.f * c01 * c01 * id2) +
+                       gC * (2.f * c00 * c01 * id2);
+    const float gh = 0.5f * gc01;
+    // Sigma' = T Sigma T^T: dL/dSigma = T^T G T, dL/dT = 2 G T Sigma
+    float GT[6];
+    for (int j = 0; j < 3; j++) {
+      GT[j] = gc00 * st.T[j] + gh * st.T[3 + j];
+      GT[3 + j] = gh * st.T[j] + gc11 * st.T[3 + j];
+    }
+    const float* Sg = st.Sig;
+    const float Sfull[9] = {Sg[0], Sg[1], Sg[2], Sg[1], Sg[3], Sg[4], Sg[2], Sg[4], Sg[5]};
+    float gT[6];
+    for (int i = 0; i < 2; i++)
+      for (int b = 0; b < 3; b++)
+        gT[3 * i + b] = 2.f * (GT[3 * i] * Sfull[b] + GT[3 * i + 1] * Sfull[3 + b] + GT[3 * i + 2] * Sfull[6 + b]);
+    float gS[9];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) gS[3 * i + j] = st.T[i] * GT[j] + st.T[3 + i] * GT[3 + j];
+    // T = J W
+    const float* R = V.R;
+    const float gJ00 = gT[0] * R[0] + gT[1] * R[1] + gT[2] * R[2];
+    const float gJ02 = gT[0] * R[6] + gT[1] * R[7] + gT[2] * R[8];
+    const float gJ11 = gT[3] * R[3] + gT[4] * R[4] + gT[5] * R[5];
+    const float gJ12 = gT[3] * R[6] + gT[4] * R[7] + gT[5] * R[8];
+    const float itz = 1.f / st.tz, itz2 = itz * itz;
+    float gtx = 0.f, gty = 0.f;
+    float gtz = -gJ00 * V.fx * itz2 + gJ02 * V.fx * st.ux * itz2 - gJ11 * V.fy * itz2 + gJ12 * V.fy * st.uy * itz2;
+    const float gux = -gJ02 * V.fx * itz, guy = -gJ12 * V.fy * itz;
+    if (!st.clx) {
+      gtx += gux * itz;
+      gtz -= gux * st.tx * itz2;
+    }
+    if (!st.cly) {
+      gty += guy * itz;
+      gtz -= guy * st.ty * itz2;
+    }
+    // mu2D = (fx tx/tz + cx, fy ty/tz + cy)
+    gtx += gmx * V.fx * itz;
+    gty += gmy * V.fy * itz;
+    gtz -= (gmx * V.fx * st.tx + gmy * V.fy * st.ty) * itz2;
+    // t = W mu + tau
+    for (int j = 0; j < 3; j++) gm[j] += R[j] * gtx + R[3 + j] * gty + R[6 + j] * gtz;
+    // Sigma = M M^T, M = Rq diag(s): dL/dM = 2 gS M
+    float gM[9];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) {
+        float acc = 0.f;
+        for (int k = 0; k < 3; k++) acc += (gS[3 * i + k] + gS[3 * k + i]) * st.Rq[3 * k + j] * st.s[j];
+        gM[3 * i + j] = acc;
+      }
+    float gR[9];
+    for (int j = 0; j < 3; j++) {
+      float gsj = 0.f;
+      for (int i = 0; i < 3; i++) {
+        gsj += gM[3 * i + j] * st.Rq[3 * i + j];
+        gR[3 * i + j] = gM[3 * i + j] * st.s[j];
+      }
+      gls[j] += gsj * st.s[j];
+    }
+    // rotation of the unit quaternion (w, x, y, z)
+    const float w = st.qn[0], x = st.qn[1], y = st.qn[2], z = st.qn[3];
+    float gqn[4];
+    gqn[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gqn[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] -
+                    2.f * x * gR[8]);
+    gqn[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] -
+                    2.f * y * gR[8]);
+    gqn[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] +
+                    y * gR[7]);
+    const float dq = gqn[0] * st.qn[0] + gqn[1] * st.qn[1] + gqn[2] * st.qn[2] + gqn[3] * st.qn[3];
+    for (int i = 0; i < 4; i++) gq[i] += (gqn[i] - st.qn[i] * dq) * st.qinv;
+    // opacity
+    gop += gsig * opacity * (1.f - opacity);
+    // colour: rgb_c = max(0, 0.5 + sum_k sh_kc Y_k(d)), d = (mu - campos) / |mu - campos|
+    float dx = mean[0] - V.campos[0], dy = mean[1] - V.campos[1], dz = mean[2] - V.campos[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv; dy *= inv; dz *= inv;
+    float Y[K];
+    ShEval<DEG>::basis(dx, dy, dz, Y);
+    float gc[3];
+    for (int c = 0; c < 3; c++) {
+      float acc = 0.5f;
+      for (int k = 0; k < K; k++) acc = fmaf(__ldg(P + (11 + 3 * k + c) * S + g), Y[k], acc);
+      gc[c] = acc < 0.f ? 0.f : grgb[c];
+    }
+    float wk[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        gsh[3 * k + c] += gc[c] * Y[k];
+        acc += gc[c] * __ldg(P + (11 + 3 * k + c) * S + g);
+      }
+      wk[k] = acc;
+    }
+    float gdx, gdy, gdz;
+    ShEval<DEG>::grad(dx, dy, dz, wk, gdx, gdy, gdz);
+    const float dd = gdx * dx + gdy * dy + gdz * dz;
+    gm[0] += (gdx - dx * dd) * inv;
+    gm[1] += (gdy - dy * dd) * inv;
+    gm[2] += (gdz - dz * dd) * inv;
+  }
+  float* G = a.grads;
+  for (int i = 0; i < 3; i++) G[i * S + g] = gm[i];
+  for (int i = 0; i < 3; i++) G[(3 + i) * S + g] = gls[i];
+  for (int i = 0; i < 4; i++) G[(6 + i) * S + g] = gq[i];
+  G[10 * S + g] = gop;
+#pragma unroll
+  for (int i = 0; i < 3 * K; i++) G[(11 + i) * S + g] = gsh[i];
+}
+
+void launch_project_fwd(const ProjectArgs& a, int deg, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
+  switch (deg) {
+    case 0: project_fwd_kernel<0><<<blocks, threads, 0, s>>>(a); break;
+    case 1: project_fwd_kernel<1><<<blocks, threads, 0, s>>>(a); break;
+    case 2: project_fwd_kernel<2><<<blocks, threads, 0, s>>>(a); break;
+    default: project_fwd_kernel<3><<<blocks, threads, 0, s>>>(a); break;
+  }
+}
+
+int project_fwd_block() { return 256; }
+
+void launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t s) {
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
+  switch (deg) {
+    case 0: project_bwd_kernel<0><<<blocks, threads, 0, s>>>(a); break;
+    case 1: project_bwd_kernel<1><<<blocks, threads, 0, s>>>(a); break;
+    case 2: project_bwd_kernel<2><<<blocks, threads, 0, s>>>(a); break;
+    default: project_bwd_kernel<3><<<blocks, threads, 0, s>>>(a); break;
+  }
+}
+
+}  // namespace gs

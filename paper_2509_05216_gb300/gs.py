@@ -1,0 +1,233 @@
+"""Thin Python binding of libgs.so (include/gs.h), through ctypes.
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Tensors are torch CUDA tensors; their device pointers and the current CUDA
+stream are handed to the C ABI.  If the library is missing or cannot be
+loaded, importing the binding raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lib = None
+
+GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ECAPACITY, GS_ETIMEOUT, GS_EBUSY, GS_EAGAIN, GS_ESTATE = range(9)
+_NAMES = ["GS_OK", "GS_EINVAL", "GS_ENOMEM", "GS_ECUDA", "GS_ECAPACITY", "GS_ETIMEOUT", "GS_EBUSY",
+          "GS_EAGAIN", "GS_ESTATE"]
+
+(GS_BUF_REC0, GS_BUF_REC1, GS_BUF_REC2, GS_BUF_KEYS, GS_BUF_VALS, GS_BUF_RANGES, GS_BUF_TFINAL,
+ GS_BUF_NLAST, GS_BUF_G2D) = range(9)
+
+
+class GsError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__("%s: %s" % (_NAMES[status] if 0 <= status < len(_NAMES) else status, msg))
+
+
+class gs_config(ctypes.Structure):
+    _fields_ = [("max_gaussians", ctypes.c_int64), ("max_views", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("instance_capacity", ctypes.c_int64)]
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("viewmat", ctypes.c_float * 16), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("znear", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+
+
+class gs_params(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_int64), ("stride", ctypes.c_int64),
+                ("sh_degree", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class gs_adam_hp(ctypes.Structure):
+    _fields_ = [("lr_mean", ctypes.c_float), ("lr_scale", ctypes.c_float), ("lr_quat", ctypes.c_float),
+                ("lr_opacity", ctypes.c_float), ("lr_sh_dc", ctypes.c_float), ("lr_sh_rest", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+EXPORTS = ["gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
+           "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
+           "gs_get_counts"]
+
+
+def load(path: str | None = None):
+    """Load libgs.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    L = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    L.gs_create.argtypes = [P(vp), ctypes.c_int, P(gs_config)]
+    L.gs_destroy.argtypes = [vp]
+    L.gs_destroy.restype = None
+    L.gs_last_error.argtypes = [vp]
+    L.gs_last_error.restype = ctypes.c_char_p
+    L.gs_set_stream.argtypes = [vp, vp]
+    L.gs_sync.argtypes = [vp]
+    L.gs_project.argtypes = [vp, P(gs_params), P(gs_camera), i32]
+    L.gs_bin_sort.argtypes = [vp]
+    L.gs_raster_fwd.argtypes = [vp, vp]
+    L.gs_raster_bwd.argtypes = [vp, P(gs_params), vp, P(gs_params)]
+    L.gs_l1_loss.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.gs_adam.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), P(gs_params), P(gs_adam_hp), i64]
+    L.gs_get_buffer.argtypes = [vp, i32, P(vp), P(i64)]
+    L.gs_get_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if f.restype is ctypes.c_int:
+            f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def camera_struct(cam) -> gs_camera:
+    c = gs_camera()
+    vm = np.asarray(cam["viewmat"], np.float64).reshape(16)
+    for i in range(16):
+        c.viewmat[i] = float(vm[i])
+    c.fx, c.fy, c.cx, c.cy = (float(cam[k]) for k in ("fx", "fy", "cx", "cy"))
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.znear = float(cam["znear"])
+    for i in range(3):
+        c.bg[i] = float(cam["bg"][i])
+    return c
+
+
+def params_struct(t: torch.Tensor, n: int, deg: int) -> gs_params:
+    if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.is_contiguous()):
+        raise ValueError("parameters must be a contiguous float32 CUDA tensor [P, stride]")
+    if t.shape[0] != 11 + 3 * (deg + 1) ** 2:
+        raise ValueError("plane count %d does not match SH degree %d" % (t.shape[0], deg))
+    return gs_params(t.data_ptr(), n, t.shape[1], deg, 0)
+
+
+class _DevArray:
+    """Zero-copy view of a device buffer for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Context:
+    """One gs_ctx.  Methods are the C ABI's calls with tensor arguments."""
+
+    def __init__(self, device: int = 0, max_views: int = 64, instance_capacity: int = 0):
+        self.L = load()
+        self.device = device
+        cfg = gs_config(0, max_views, 0, instance_capacity)
+        h = ctypes.c_void_p()
+        st = self.L.gs_create(ctypes.byref(h), device, ctypes.byref(cfg))
+        if st != GS_OK:
+            raise GsError(st, "gs_create(device=%d) failed" % device)
+        self.h = h
+        self._stream = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.gs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != GS_OK:
+            raise GsError(st, "%s: %s" % (what, self.L.gs_last_error(self.h).decode()))
+
+    def _bind_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            self._check(self.L.gs_set_stream(self.h, ctypes.c_void_p(s)), "gs_set_stream")
+            self._stream = s
+
+    # -- the path ---------------------------------------------------------
+    def gs_project(self, params: torch.Tensor, n: int, deg: int, cams):
+        self._bind_stream()
+        p = params_struct(params, n, deg)
+        arr = (gs_camera * len(cams))(*[camera_struct(c) for c in cams])
+        self._check(self.L.gs_project(self.h, ctypes.byref(p), arr, len(cams)), "gs_project")
+
+    def gs_bin_sort(self):
+        self._bind_stream()
+        self._check(self.L.gs_bin_sort(self.h), "gs_bin_sort")
+
+    def gs_raster_fwd(self, images: torch.Tensor):
+        self._bind_stream()
+        assert images.is_cuda and images.dtype == torch.float32 and images.is_contiguous()
+        self._check(self.L.gs_raster_fwd(self.h, ctypes.c_void_p(images.data_ptr())), "gs_raster_fwd")
+
+    def gs_raster_bwd(self, params: torch.Tensor, n: int, deg: int, dL_dimages: torch.Tensor,
+                      grads: torch.Tensor):
+        self._bind_stream()
+        assert dL_dimages.is_cuda and dL_dimages.dtype == torch.float32 and dL_dimages.is_contiguous()
+        p = params_struct(params, n, deg)
+        g = params_struct(grads, n, deg)
+        self._check(self.L.gs_raster_bwd(self.h, ctypes.byref(p), ctypes.c_void_p(dL_dimages.data_ptr()),
+                                         ctypes.byref(g)), "gs_raster_bwd")
+
+    def gs_l1_loss(self, x: torch.Tensor, y: torch.Tensor, loss: torch.Tensor | None, grad: torch.Tensor | None):
+        self._bind_stream()
+        assert x.is_contiguous() and y.is_contiguous() and x.numel() == y.numel()
+        self._check(self.L.gs_l1_loss(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                      x.numel(), ctypes.c_void_p(loss.data_ptr() if loss is not None else 0),
+                                      ctypes.c_void_p(grad.data_ptr() if grad is not None else 0)), "gs_l1_loss")
+
+    def gs_adam(self, p, g, m, v, n, deg, hp: dict, step: int):
+        self._bind_stream()
+        sp, sg, sm, sv = (params_struct(t, n, deg) for t in (p, g, m, v))
+        h = gs_adam_hp(hp["lr_mean"], hp["lr_scale"], hp["lr_quat"], hp["lr_opacity"], hp["lr_sh_dc"],
+                       hp["lr_sh_rest"], hp.get("beta1", 0.9), hp.get("beta2", 0.999), hp.get("eps", 1e-15))
+        self._check(self.L.gs_adam(self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv),
+                                   ctypes.byref(h), int(step)), "gs_adam")
+
+    def gs_sync(self):
+        self._check(self.L.gs_sync(self.h), "gs_sync")
+
+    # -- inspection -------------------------------------------------------
+    def gs_get_counts(self):
+        i, b, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.L.gs_get_counts(self.h, ctypes.byref(i), ctypes.byref(b), ctypes.byref(p)),
+                    "gs_get_counts")
+        return i.value, b.value, p.value
+
+    def gs_get_buffer(self, which: int) -> torch.Tensor:
+        """Copy of an intermediate buffer as a torch tensor."""
+        ptr, cnt = ctypes.c_void_p(), ctypes.c_int64()
+        self._check(self.L.gs_get_buffer(self.h, which, ctypes.byref(ptr), ctypes.byref(cnt)), "gs_get_buffer")
+        n = cnt.value
+        spec = {GS_BUF_REC0: ((n, 4), "<f4"), GS_BUF_REC1: ((n, 4), "<f4"), GS_BUF_REC2: ((n, 4), "<f4"),
+                GS_BUF_KEYS: ((n,), "<i8"), GS_BUF_VALS: ((n,), "<i4"), GS_BUF_RANGES: ((n, 2), "<i4"),
+                GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((n, 12), "<f4")}[which]
+        if n == 0:
+            return torch.empty(spec[0], device="cuda:%d" % self.device,
+                               dtype={"<f4": torch.float32, "<i8": torch.int64, "<i4": torch.int32}[spec[1]])
+        t = torch.as_tensor(_DevArray(ptr.value, *spec), device="cuda:%d" % self.device)
+        return t.clone()
+
+
+def image_offsets(cams):
+    """Start (in floats) of each view's [3][H][W] block in a batch image buffer."""
+    offs, o = [], 0
+    for c in cams:
+        offs.append(o)
+        o += 3 * c["width"] * c["height"]
+    return offs, o
+
+
+def split_images(buf: torch.Tensor, cams):
+    offs, _ = image_offsets(cams)
+    return [buf[o:o + 3 * c["width"] * c["height"]].view(3, c["height"], c["width"]) for o, c in zip(offs, cams)]

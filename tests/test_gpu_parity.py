@@ -1,0 +1,226 @@
+"""CUDA path against the FP64 oracle, through the C ABI (GPU only).
+
+Tolerances (FP32 path vs FP64 oracle): projection values rel 1e-4 (means in
+pixels abs 2e-3), depth bit-exact (both sides evaluate the same FP32
+expression), tile counts / keys / values / ranges bit-exact against a CPU
+recomputation from the GPU's own FP32 projection, images max-abs 1e-4 and
+gradients rel-L2 1e-3 on everything the oracle does not flag as marginal.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_05216_gb300 import gs, inputs
+from tests.gpu_helpers import expected_binning, rel_l2, run_forward, to_dev_images
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gs.Context(0)
+    yield c
+    c.close()
+
+
+def mixed_cams():
+    return [inputs.pinhole(inputs.look_at((0.4, -2.8, 1.0)), 200, 152),
+            inputs.pinhole(inputs.look_at((2.5, 1.0, -1.2)), 256, 256),
+            inputs.pinhole(inputs.look_at((-1.5, 2.0, 1.9)), 97, 131, bg=(0.2, 0.4, 0.1))]
+
+
+SCENES = {
+    "sphere_c1": lambda: (inputs.sphere_scene(), [inputs.sphere_camera()]),
+    "random_deg3_mixed": lambda: (inputs.random_scene(20000, 3, 11, extent=0.8), mixed_cams()),
+    "random_deg1_one": lambda: (inputs.random_scene(5001, 1, 12, extent=0.6, log_scale=(-4, -1.5)),
+                                [inputs.pinhole(inputs.look_at((0.1, 0.2, 2.4)), 130, 70)]),
+}
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_projection_matches_oracle(ctx, oracle, name):
+    scene, cams = SCENES[name]()
+    run_forward(ctx, scene, cams)
+    n, stride = scene["n"], scene["params"].shape[1]
+    r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
+    r1 = ctx.gs_get_buffer(gs.GS_BUF_REC1).cpu().numpy()
+    r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+    for v, cam in enumerate(cams):
+        sl = slice(v * stride, v * stride + n)
+        pr = oracle.project(scene, cam)
+        vis = (pr["flags"] & oracle.G_VISIBLE) != 0
+        tiles = r2[sl, 3].view(np.uint32)
+        margin = (pr["flags"] & oracle.G_MARG_RECT) != 0
+        # visibility and radius agree except on marginal rects
+        assert np.array_equal((tiles > 0)[~margin], vis[~margin])
+        rad = r2[sl, 2].view(np.int32)
+        both = vis & (tiles > 0)
+        assert np.array_equal(rad[both & ~margin], pr["radius"][both & ~margin])
+        # depth: the same FP32 evaluation on both sides
+        dep = r2[sl, 1]
+        assert np.array_equal(dep[both], pr["depth"][both].astype(np.float32))
+        m = both
+        np.testing.assert_allclose(r0[sl][m, 0:2], pr["mean2d"][m], rtol=0, atol=2e-3)
+        np.testing.assert_allclose(r0[sl][m, 2], pr["conic"][m, 0], rtol=1e-4, atol=1e-7)
+        np.testing.assert_allclose(r0[sl][m, 3], pr["conic"][m, 1], rtol=1e-4,
+                                   atol=1e-4 * np.abs(pr["conic"][m, 0:3]).max(axis=1).max())
+        np.testing.assert_allclose(r1[sl][m, 0], pr["conic"][m, 2], rtol=1e-4, atol=1e-7)
+        np.testing.assert_allclose(r1[sl][m, 1], pr["opacity"][m], rtol=1e-6, atol=0)
+        rgb = np.concatenate([r1[sl][m, 2:4], r2[sl][m, 0:1]], axis=1)
+        np.testing.assert_allclose(rgb, pr["rgb"][m], rtol=0, atol=2e-5)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_binning_is_bit_exact(ctx, name):
+    scene, cams = SCENES[name]()
+    run_forward(ctx, scene, cams)
+    n, stride = scene["n"], scene["params"].shape[1]
+    r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
+    r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+    keys, vals, ranges, per_view = expected_binning(r0, r2, cams, n, stride)
+    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)
+    gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64)
+    gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
+    inst, bins, _ = ctx.gs_get_counts()
+    assert inst == keys.size == per_view.sum()
+    # per-(view, Gaussian) tile counts equal the rect areas
+    for v in range(len(cams)):
+        t = r2[v * stride: v * stride + n, 3].view(np.uint32)
+        assert int(t.sum()) == int(per_view[v])
+    assert np.array_equal(gk, keys)
+    assert np.array_equal(gv, vals)
+    assert np.array_equal(gr, ranges)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_image_matches_oracle(ctx, oracle, name):
+    scene, cams = SCENES[name]()
+    _, img = run_forward(ctx, scene, cams)
+    views = gs.split_images(img, cams)
+    tf = ctx.gs_get_buffer(gs.GS_BUF_TFINAL).cpu().numpy()
+    off = 0
+    for v, cam in enumerate(cams):
+        ref, reft, marg, _ = oracle.render(scene, cam)
+        ok = ~marg
+        assert ok.mean() > 0.98
+        got = views[v].cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref)[:, ok].max() <= 1e-4
+        HW = cam["width"] * cam["height"]
+        t = tf[off: off + HW].reshape(cam["height"], cam["width"])
+        assert np.abs(t - reft)[ok].max() <= 1e-4
+        assert t.min() >= np.float32(1e-4) and t.max() <= 1.0
+        off += HW
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_gradient_matches_oracle(ctx, oracle, name):
+    scene, cams = SCENES[name]()
+    p, _ = run_forward(ctx, scene, cams)
+    rng = np.random.default_rng(7)
+    dimgs = []
+    for cam in cams:
+        _, _, marg, _ = oracle.render(scene, cam)
+        d = rng.normal(size=(3, cam["height"], cam["width"])) * (~marg)
+        dimgs.append(d)
+    grads = torch.zeros_like(p)
+    ctx.gs_raster_bwd(p, scene["n"], scene["deg"], to_dev_images(dimgs), grads)
+    ctx.gs_sync()
+    ref, ref2d = oracle.render_grad(scene, cams, dimgs, want_2d=True)
+    n, stride = scene["n"], scene["params"].shape[1]
+    keep = np.ones(n, bool)
+    for cam in cams:
+        keep &= (oracle.gaussian_flags(scene, cam) & oracle.G_MARG_ANY_GRAD) == 0
+    g = grads.cpu().numpy().astype(np.float64)
+    assert rel_l2(g[:, :n][:, keep], ref[:, :n][:, keep]) <= 1e-3
+    # per-plane check of the larger groups, so no group hides behind another
+    for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
+        r = ref[lo:hi, :n][:, keep]
+        if np.linalg.norm(r) > 0:
+            assert rel_l2(g[lo:hi, :n][:, keep], r) <= 1e-3, (lo, hi)
+    g2d = ctx.gs_get_buffer(gs.GS_BUF_G2D).cpu().numpy().astype(np.float64)
+    for v in range(len(cams)):
+        got = g2d[v * stride: v * stride + n, :9][keep]
+        assert rel_l2(got, ref2d[v][keep]) <= 1e-3
+
+
+def test_batched_forward_equals_single_views(ctx):
+    scene, cams = SCENES["random_deg3_mixed"]()
+    _, img = run_forward(ctx, scene, cams)
+    batch = [t.clone() for t in gs.split_images(img, cams)]
+    for v, cam in enumerate(cams):
+        _, one = run_forward(ctx, scene, [cam])
+        assert torch.equal(one.view(3, cam["height"], cam["width"]), batch[v])
+
+
+def test_all_gaussians_behind_camera_give_background(ctx):
+    scene = inputs.random_scene(300, 2, 3, extent=0.3)
+    cam = inputs.pinhole(inputs.look_at((0.0, 0.0, 3.0), target=(0.0, 0.0, 6.0)), 40, 33, bg=(0.3, 0.2, 0.1))
+    _, img = run_forward(ctx, scene, [cam])
+    inst, _, _ = ctx.gs_get_counts()
+    assert inst == 0
+    out = img.view(3, 33, 40).cpu().numpy()
+    for c in range(3):
+        assert np.all(out[c] == np.float32(cam["bg"][c]))
+
+
+def test_single_gaussian_and_large_splat(ctx, oracle):
+    # one Gaussian filling most of a ragged 100x77 image
+    scene = inputs.pack_params(np.zeros((1, 3)), np.full((1, 3), -0.7), np.array([[1.0, 0.2, 0.1, 0.0]]),
+                               np.array([1.5]), np.full((1, 1, 3), 0.4))
+    cam = inputs.pinhole(inputs.look_at((0.0, -3.0, 0.5)), 100, 77)
+    _, img = run_forward(ctx, scene, [cam])
+    ref, _, marg, _ = oracle.render(scene, cam)
+    got = img.view(3, 77, 100).cpu().numpy()
+    assert np.abs(got - ref)[:, ~marg].max() <= 1e-4
+
+
+def test_l1_loss_matches_oracle(ctx, oracle):
+    rng = np.random.default_rng(3)
+    x = rng.uniform(size=100003).astype(np.float32)
+    y = rng.uniform(size=100003).astype(np.float32)
+    y[::97] = x[::97]  # exact ties: sign(0) = 0
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(x.size, device="cuda")
+    ctx.gs_l1_loss(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), loss, grad)
+    ctx.gs_sync()
+    ref, gref = oracle.l1(x, y)
+    assert abs(loss.item() - ref) <= 1e-6 * ref
+    np.testing.assert_allclose(grad.cpu().numpy(), gref, rtol=1e-6, atol=0)
+
+
+def test_adam_matches_oracle(ctx, oracle):
+    rng = np.random.default_rng(4)
+    scene = inputs.random_scene(1003, 3, 2)
+    P, stride = scene["params"].shape
+    n = scene["n"]
+    hp = dict(lr_mean=1.6e-4, lr_scale=5e-3, lr_quat=1e-3, lr_opacity=0.05, lr_sh_dc=2.5e-3,
+              lr_sh_rest=2.5e-3 / 20, beta1=0.9, beta2=0.999, eps=1e-15)
+    lr_planes = np.array([hp["lr_mean"]] * 3 + [hp["lr_scale"]] * 3 + [hp["lr_quat"]] * 4 + [hp["lr_opacity"]]
+                         + [hp["lr_sh_dc"]] * 3 + [hp["lr_sh_rest"]] * (P - 14))
+    p = torch.from_numpy(scene["params"]).cuda()
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    p64, m64, v64 = scene["params"].astype(np.float64), np.zeros((P, stride)), np.zeros((P, stride))
+    for step in range(1, 4):
+        g = rng.normal(size=(P, stride)).astype(np.float32)
+        g[:, n:] = 0
+        ctx.gs_adam(p, torch.from_numpy(g).cuda(), m, v, n, 3, hp, step)
+        oracle.adam(p64, g.astype(np.float64), m64, v64, lr_planes, step)
+    ctx.gs_sync()
+    np.testing.assert_allclose(p.cpu().numpy(), p64, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(m.cpu().numpy(), m64, rtol=1e-5, atol=1e-7)
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    scene = inputs.random_scene(10, 0, 1)
+    p = torch.from_numpy(scene["params"]).cuda()
+    bad = inputs.pinhole(inputs.look_at((0, 0, 3.0), up=(0, 1, 0)), 0, 10)
+    with pytest.raises(gs.GsError) as e:
+        ctx.gs_project(p, scene["n"], 0, [bad])
+    assert e.value.status == gs.GS_EINVAL
+    fresh = gs.Context(0)
+    with pytest.raises(gs.GsError) as e:
+        fresh.gs_bin_sort()
+    assert e.value.status == gs.GS_ESTATE
+    fresh.close()
