@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Training throughput of the GB300 tile rasterizer.
+
+Workload (Kingsnake-scale stand-in): 4,000,000 Gaussians on the 0.5 level of
+a seeded 200-blob field, SH degree 3, FP32 parameters and Adam state; 256
+orbit cameras (16 azimuths x 16 elevations, radius 4, 60 degree FOV) at
+2048x2048; targets are renders of the reference set, the trained set starts
+from a seeded +-5% perturbation of it.  One step = projection, binning (scan,
+duplication, onesweep sort, ranges), forward compositing, L1 loss, backward
+compositing, projection backward and Adam, over a batch of B=16 views.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "train views/s @4M Gauss 2048² batched vs 1-view; render p50/p99 ms"
+HP = dict(lr_mean=1.6e-4 * 1.0, lr_scale=5e-3, lr_quat=1e-3, lr_opacity=0.05, lr_sh_dc=2.5e-3,
+          lr_sh_rest=2.5e-3 / 20, beta1=0.9, beta2=0.999, eps=1e-15)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--n", type=int, default=4_000_000)
+    ap.add_argument("--res", type=int, default=2048)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--plain-views", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cache", default=os.environ.get("GS_SCENE_CACHE", "/tmp/gs_scene_cache"))
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- workload
+
+def workload(args, device=None):
+    from paper_2509_05216_gb300 import inputs
+    os.makedirs(args.cache, exist_ok=True)
+    path = os.path.join(args.cache, "blobs_n%d_s4.npz" % args.n)
+    if os.path.exists(path):
+        z = np.load(path)
+        scene = {"params": z["params"], "n": int(z["n"]), "deg": int(z["deg"])}
+    else:
+        scene = inputs.blobs_scene(args.n, seed=4, deg=3, res=128, device=device)
+        tmp = path + ".%d.tmp.npz" % os.getpid()
+        np.savez(tmp, params=scene["params"], n=scene["n"], deg=scene["deg"])
+        os.replace(tmp, path)
+    cams = inputs.orbit_cameras(16, 16, 4.0, args.res, args.res)
+    trained = inputs.perturb(scene, 104)
+    return scene, trained, cams
+
+
+def config_dict(args, n_gpus):
+    return {"workload": "blobs-isosurface-4M-2048sq-B16", "gaussians": args.n, "sh_degree": 3,
+            "resolution": [args.res, args.res], "batch_views": args.batch, "orbit_cameras": 256,
+            "global_batch": args.batch * n_gpus, "parallelism": "replicas x%d" % n_gpus,
+            "l2": "inputs larger than L2 (944 MB parameters, 805 MB targets per step)"}
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+class Trainer:
+    """Training state on one GPU and the step through the C ABI."""
+
+    def __init__(self, ctx, trained, device):
+        import torch
+        self.ctx = ctx
+        self.n, self.deg = trained["n"], trained["deg"]
+        self.p = torch.from_numpy(trained["params"]).to(device)
+        self.m = torch.zeros_like(self.p)
+        self.v = torch.zeros_like(self.p)
+        self.g = torch.zeros_like(self.p)
+        self.loss = torch.zeros(1, device=device)
+        self.t = 0
+
+    def step(self, cams, target, img, dimg):
+        c = self.ctx
+        c.gs_project(self.p, self.n, self.deg, cams)
+        c.gs_bin_sort()
+        c.gs_raster_fwd(img)
+        c.gs_l1_loss(img, target, self.loss, dimg)
+        c.gs_raster_bwd(self.p, self.n, self.deg, dimg, self.g)
+        self.t += 1
+        c.gs_adam(self.p, self.g, self.m, self.v, self.n, self.deg, HP, self.t)
+
+
+def render_targets(ctx, scene, cams, B, nbatch, device):
+    import torch
+    from paper_2509_05216_gb300 import gs
+    p = torch.from_numpy(scene["params"]).to(device)
+    _, total = gs.image_offsets(cams[:B])
+    out = []
+    for b in range(nbatch):
+        cb = cams[b * B:(b + 1) * B]
+        t = torch.empty(total, device=device)
+        ctx.gs_project(p, scene["n"], scene["deg"], cb)
+        ctx.gs_bin_sort()
+        ctx.gs_raster_fwd(t)
+        out.append(t)
+    ctx.gs_sync()
+    return out
+
+
+# Algorithmic work per launch (documented in the design doc): bytes for the
+# HBM-bound kernels, FP32 operations for the compositing kernels.
+RASTER_OPS_FWD = 24   # FP32 ops per evaluated (pixel, Gaussian) pair, forward
+RASTER_OPS_BWD = 60   # FP32 ops per evaluated pair, backward
+
+
+def algorithmic_work(name, n, P, B, I, pairs, pixels, passes):
+    if name == "project_fwd":
+        return "hbm", n * (4 * P + B * 52.0)
+    if name == "project_bwd":
+        return "hbm", n * (8 * P + B * 48.0)
+    if name == "adam":
+        return "hbm", 28.0 * P * n
+    if name == "onesweep_pass":
+        return "hbm", 24.0 * I
+    if name == "digit_histogram":
+        return "hbm", 8.0 * I
+    if name == "duplicate":
+        return "hbm", n * B * 4.0 + 12.0 * I
+    if name == "tile_ranges":
+        return "hbm", 8.0 * I
+    if name == "l1_loss":
+        return "hbm", 12.0 * 3 * pixels
+    if name == "raster_fwd":
+        return "alu", RASTER_OPS_FWD * pairs
+    if name == "raster_bwd":
+        return "alu", RASTER_OPS_BWD * pairs
+    return None, None
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2509_05216_gb300 import gs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, trained, cams = workload(args, device=dev)
+    B = args.batch
+    nbatch = len(cams) // B
+    ctx = gs.Context(local)
+    t0 = time.time()
+    targets = render_targets(ctx, scene, cams, B, min(nbatch, args.warmup + args.steps), dev)
+    _, total = gs.image_offsets(cams[:B])
+    img = torch.empty(total, device=dev)
+    dimg = torch.empty(total, device=dev)
+    tr = Trainer(ctx, trained, dev)
+
+    def batch(i):
+        b = i % len(targets)
+        return cams[b * B:(b + 1) * B], targets[b]
+
+    for i in range(args.warmup):
+        tr.step(*batch(i), img, dimg)
+    ctx.gs_sync()
+    # timed region: K batched steps
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile_reset()
+    ctx.profile_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for i in range(args.steps):
+            tr.step(*batch(args.warmup + i), img, dimg)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    ctx.profile_enable(False)
+    kstats = ctx.profile_read()
+    ctx.gs_sync()
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    views = args.steps * B * world
+    value = views / (t_max / 1000.0)
+
+    # work counters of one batched step (for the roofline)
+    inst, bins, pixels = ctx.gs_get_counts()
+    nl = ctx.gs_get_buffer(gs.GS_BUF_NLAST)
+    pairs = float(nl.to(torch.float64).sum().item())
+    P = tr.p.shape[0]
+    launches = sum(k["launches"] for k in kstats)
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    per_kernel = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
+                              "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in kstats), 1e-9), 4)}
+                  for k in kstats}
+    passes = next((k["launches"] for k in kstats if k["name"] == "onesweep_pass"), 0) / max(args.steps, 1)
+    kind, work = algorithmic_work(dom["name"], tr.n, P, B, inst, pairs, pixels, passes)
+    avg_ms = dom["total_ms"] / max(dom["launches"], 1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if kind == "hbm":
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = work / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom["name"],
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    else:
+        clk_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * 2 * clk_max * 1e6 / 1e12  # FP32 TFLOP/s, FMA = 2
+        achieved = work / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom["name"],
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+
+    # plain path: one view per launch, Adam after each view
+    ctx2 = gs.Context(local)
+    tr2 = Trainer(ctx2, trained, dev)
+    one_img = torch.empty(3 * args.res * args.res, device=dev)
+    one_dimg = torch.empty_like(one_img)
+    for i in range(2):
+        tr2.step([cams[i]], targets[0][i * one_img.numel():(i + 1) * one_img.numel()], one_img, one_dimg)
+    ctx2.gs_sync()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.plain_views):
+        b = i % B
+        tr2.step([cams[b]], targets[0][b * one_img.numel():(b + 1) * one_img.numel()], one_img, one_dimg)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain = args.plain_views / (e0.elapsed_time(e1) / 1000.0)
+    ctx2.close()
+
+    # end to end: targets from pinned host memory, loss read back each step
+    host_t = [t.cpu().pin_memory() for t in targets[:2]]
+    dev_t = torch.empty(total, device=dev)
+    loss_h = torch.empty(1, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for i in range(args.e2e_steps):
+        b = i % 2
+        dev_t.copy_(host_t[b], non_blocking=True)
+        tr.step(cams[b * B:(b + 1) * B], dev_t, img, dimg)
+        loss_h.copy_(tr.loss, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e = args.e2e_steps * B * world / (e0.elapsed_time(e1) / 1000.0)
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "views/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded blob-isosurface scene, random-init perturbation of a reference set)",
+        "config": config_dict(args, world),
+        "plain_1view_views_per_s": round(plain, 3), "batched_over_plain": round(value / plain / world, 3),
+        "e2e": {"value": round(e2e, 3), "unit": "views/s", "h2d_bytes_per_step": total * 4,
+                "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
+        "instances_per_step": int(inst), "pairs_per_step": pairs, "kernels": per_kernel,
+        "setup_s": round(time.time() - t0, 1),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scene, trained, cams, args)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- oracle (CPU) arm
+
+def cpu_sample(trained, scene, cams, args, budget_s):
+    """Time the FP64 oracle on a bounded sample of one training view: forward
+    and gradient over a random subset of tiles (plus the projection of all
+    Gaussians, which the oracle needs for any tile).  Returns views/s scaled
+    by the tile fraction, the sample description and the thread count."""
+    from oracle import oracle
+    cam = cams[0]
+    gw = (cam["width"] + 15) // 16
+    ntiles = gw * ((cam["height"] + 15) // 16)
+    rng = np.random.default_rng(0)
+    frac = 1.0 / 8.0
+    want = np.zeros(ntiles, np.uint8)
+    want[rng.choice(ntiles, max(1, int(ntiles * frac)), replace=False)] = 1
+    t0 = time.time()
+    img, _, _, _ = oracle.render(trained, cam, tile_want=want)
+    ref, _, _, _ = oracle.render(scene, cam, tile_want=want)
+    _, dimg = oracle.l1(img, ref)
+    dimg = dimg.reshape(img.shape)
+    oracle.render_grad(trained, [cam], [dimg])
+    dt = time.time() - t0
+    used = int(want.sum())
+    return {"value": round((used / ntiles) / dt, 6), "unit": "views/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "one 2048x2048 view: forward + gradient over %d of %d tiles (%.1f s), scaled by the tile "
+                      "fraction; projection of all %d Gaussians included" % (used, ntiles, dt, trained["n"])}
+
+
+def cpu_baseline(scene, trained, cams, args):
+    return cpu_sample(trained, scene, cams, args, args.cpu_seconds)
+
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene, trained, cams = workload(args, device=None)
+    samples = []
+    for _ in range(args.warmup):
+        pass
+    for _ in range(max(1, min(args.steps, 2))):
+        samples.append(cpu_sample(trained, scene, cams, args, args.cpu_seconds))
+    v = statistics.median(s["value"] for s in samples)
+    out = {"metric": METRIC, "value": v, "unit": "views/s", "n_gpus": world, "steps": len(samples),
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": config_dict(args, world), "impl": "reference",
+           "cpu_baseline": {"value": v, "unit": "views/s", "cores": samples[0]["cores"], "kind": "oracle",
+                            "sample": samples[0]["sample"]},
+           "e2e": {"value": v, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

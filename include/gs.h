@@ -195,6 +195,28 @@ gs_status gs_get_buffer(gs_ctx* ctx, int32_t which, void** ptr, int64_t* count);
  * Synchronises the stream to read the device-side instance count. */
 gs_status gs_get_counts(gs_ctx* ctx, int64_t* instances, int64_t* bins, int64_t* pixels);
 
+/* ---------------------------------------------------------------- profiling */
+
+/* Per-kernel accounting: every launch the library makes is counted; while
+ * profiling is enabled, CUDA events on the context's stream bracket each
+ * launch and their elapsed time is summed per kernel. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms; /* summed event time (profiling enabled only) */
+} gs_kernel_stat;
+
+/* Turn event timing on (enable != 0) or off.  Errors: GS_EINVAL. */
+gs_status gs_profile_enable(gs_ctx* ctx, int32_t enable);
+
+/* Copy up to `cap` kernel statistics into out (host array) and set *count to
+ * the number of kernels seen.  Synchronises the stream when timings are
+ * pending.  Errors: GS_EINVAL, GS_ECUDA. */
+gs_status gs_profile_read(gs_ctx* ctx, gs_kernel_stat* out, int32_t cap, int32_t* count);
+
+/* Zero the launch counts and timings (synchronises pending timings away). */
+gs_status gs_profile_reset(gs_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

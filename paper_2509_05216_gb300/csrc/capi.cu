@@ -45,6 +45,21 @@ struct gs_ctx {
 
   DevBuf views, rec0, rec1, rec2, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial;
+
+  // launch accounting and optional per-kernel event timing
+  struct KStat {
+    std::string name;
+    int64_t launches = 0;
+    double ms = 0.0;
+  };
+  std::vector<KStat> kstats;
+  struct Pending {
+    int kernel;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  bool profiling = false;
 };
 
 namespace {
@@ -118,6 +133,45 @@ gs_status check_params(gs_ctx* c, const gs_params* p, const char* what) {
   return GS_OK;
 }
 
+int kernel_index(gs_ctx* c, const char* name) {
+  for (size_t i = 0; i < c->kstats.size(); i++)
+    if (c->kstats[i].name == name) return (int)i;
+  c->kstats.push_back(gs_ctx::KStat{name, 0, 0.0});
+  return (int)c->kstats.size() - 1;
+}
+
+cudaEvent_t take_event(gs_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one library launch (of `kernels` kernels) for the accounting.
+struct LaunchScope {
+  gs_ctx* c;
+  int k;
+  cudaEvent_t a = nullptr;
+  LaunchScope(gs_ctx* ctx, const char* name, int kernels = 1) : c(ctx), k(kernel_index(ctx, name)) {
+    c->kstats[k].launches += kernels;
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~LaunchScope() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back(gs_ctx::Pending{k, a, b});
+    }
+  }
+};
+
 void set_device(gs_ctx* c) { cudaSetDevice(c->device); }
 
 }  // namespace
@@ -166,6 +220,11 @@ void gs_destroy(gs_ctx* c) {
                     &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
+  for (const auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->status_d) cudaFree(c->status_d);
   if (c->status_h) cudaFreeHost(c->status_h);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -251,7 +310,10 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   a.rec2 = P<float4>(c->rec2);
   a.tiles = P<uint32_t>(c->tiles);
   a.block_sums = P<uint32_t>(c->block_sums);
-  launch_project_fwd(a, params->sh_degree, c->stream);
+  {
+    LaunchScope ls(c, "project_fwd");
+    launch_project_fwd(a, params->sh_degree, c->stream);
+  }
   GS_CHECK_LAUNCH(c);
   c->B = B;
   c->n = n;
@@ -271,8 +333,11 @@ gs_status gs_bin_sort(gs_ctx* c) {
   c->sorted = c->rastered = false;
   GS_TRY(ensure(c, c->block_offsets, sizeof(uint32_t) * c->nblocks));
   GS_TRY(ensure(c, c->total, sizeof(uint64_t)));
-  launch_scan_block_sums(P<uint32_t>(c->block_sums), c->nblocks, P<uint32_t>(c->block_offsets),
-                         P<uint64_t>(c->total), c->stream);
+  {
+    LaunchScope ls(c, "scan_block_sums");
+    launch_scan_block_sums(P<uint32_t>(c->block_sums), c->nblocks, P<uint32_t>(c->block_offsets),
+                           P<uint64_t>(c->total), c->stream);
+  }
   GS_CHECK_LAUNCH(c);
   int64_t I;
   if (c->cfg.instance_capacity > 0) {
@@ -301,7 +366,10 @@ gs_status gs_bin_sort(gs_ctx* c) {
   d.vals = P<uint32_t>(c->vals0);
   d.capacity = I;
   d.status = c->status_d;
-  launch_duplicate(d, c->stream);
+  if (I > 0) {
+    LaunchScope ls(c, "duplicate");
+    launch_duplicate(d, c->stream);
+  }
   GS_CHECK_LAUNCH(c);
 
   // radix passes over the 32 depth bits and the bits of the largest bin
@@ -312,7 +380,10 @@ gs_status gs_bin_sort(gs_ctx* c) {
   if (I > 1) {
     GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
     GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * 8 * 256, c->stream));
-    launch_digit_histogram(P<uint64_t>(c->keys0), I, npass, P<uint32_t>(c->hist), c->stream);
+    {
+      LaunchScope ls(c, "digit_histogram");
+      launch_digit_histogram(P<uint64_t>(c->keys0), I, npass, P<uint32_t>(c->hist), c->stream);
+    }
     GS_CHECK_LAUNCH(c);
     uint32_t* h_host = reinterpret_cast<uint32_t*>(c->pinned);
     GS_CUDA(c, cudaMemcpyAsync(h_host, c->hist.p, sizeof(uint32_t) * npass * 256, cudaMemcpyDeviceToHost,
@@ -325,7 +396,10 @@ gs_status gs_bin_sort(gs_ctx* c) {
         if ((int64_t)h_host[p * 256 + d] == I) trivial = true;
       if (!trivial) passes.push_back(p);
     }
-    launch_digit_scan(P<uint32_t>(c->hist), npass, c->stream);
+    {
+      LaunchScope ls(c, "digit_scan");
+      launch_digit_scan(P<uint32_t>(c->hist), npass, c->stream);
+    }
     GS_CHECK_LAUNCH(c);
     const size_t lb = sort_lookback_bytes(I);
     if (!passes.empty()) {
@@ -340,15 +414,21 @@ gs_status gs_bin_sort(gs_ctx* c) {
       const uint32_t* vin = P<uint32_t>(cur ? c->vals1 : c->vals0);
       uint64_t* kout = P<uint64_t>(cur ? c->keys0 : c->keys1);
       uint32_t* vout = P<uint32_t>(cur ? c->vals0 : c->vals1);
-      launch_onesweep_pass(kin, vin, kout, vout, I, p, P<uint32_t>(c->hist) + p * 256,
-                           reinterpret_cast<uint32_t*>(P<unsigned char>(c->lookback) + lb * q),
-                           P<uint32_t>(c->counters) + q, c->status_d, c->stream);
+      {
+        LaunchScope ls(c, "onesweep_pass");
+        launch_onesweep_pass(kin, vin, kout, vout, I, p, P<uint32_t>(c->hist) + p * 256,
+                             reinterpret_cast<uint32_t*>(P<unsigned char>(c->lookback) + lb * q),
+                             P<uint32_t>(c->counters) + q, c->status_d, c->stream);
+      }
       GS_CHECK_LAUNCH(c);
       cur ^= 1;
     }
   }
   GS_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * c->bins, c->stream));
-  launch_tile_ranges(P<uint64_t>(cur ? c->keys1 : c->keys0), I, P<uint2>(c->ranges), c->stream);
+  if (I > 0) {
+    LaunchScope ls(c, "tile_ranges");
+    launch_tile_ranges(P<uint64_t>(cur ? c->keys1 : c->keys0), I, P<uint2>(c->ranges), c->stream);
+  }
   GS_CHECK_LAUNCH(c);
   c->sorted_in = cur;
   c->sorted = true;
@@ -379,7 +459,10 @@ gs_status gs_raster_fwd(gs_ctx* c, float* images) {
   GS_TRY(ensure(c, c->nlast, sizeof(uint32_t) * c->pixels));
   RasterArgs r = raster_args(c);
   r.image = images;
-  launch_raster_fwd(r, c->bins, c->raster_ppt, c->stream);
+  {
+    LaunchScope ls(c, "raster_fwd");
+    launch_raster_fwd(r, c->bins, c->raster_ppt, c->stream);
+  }
   GS_CHECK_LAUNCH(c);
   c->rastered = true;
   return GS_OK;
@@ -402,7 +485,10 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   RasterArgs r = raster_args(c);
   r.dimage = dL_dimages;
   r.g2d = P<float4>(c->g2d);
-  launch_raster_bwd(r, c->bins, c->raster_ppt, c->stream);
+  {
+    LaunchScope ls(c, "raster_bwd");
+    launch_raster_bwd(r, c->bins, c->raster_ppt, c->stream);
+  }
   GS_CHECK_LAUNCH(c);
   ProjectBwdArgs b{};
   b.params = params->data;
@@ -416,7 +502,10 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
     // padding columns are not written by the kernel; keep them zero
     GS_CUDA(c, cudaMemsetAsync(grads->data, 0, sizeof(float) * n_planes(c->deg) * grads->stride, c->stream));
   }
-  launch_project_bwd(b, c->deg, c->stream);
+  {
+    LaunchScope ls(c, "project_bwd");
+    launch_project_bwd(b, c->deg, c->stream);
+  }
   GS_CHECK_LAUNCH(c);
   return GS_OK;
 }
@@ -428,7 +517,10 @@ gs_status gs_l1_loss(gs_ctx* c, const float* x, const float* y, int64_t count, f
   set_device(c);
   const int parts = l1_parts(count);
   GS_TRY(ensure(c, c->l1_partial, sizeof(float) * parts));
-  launch_l1(x, y, count, P<float>(c->l1_partial), parts, loss, dL_dx, c->stream);
+  {
+    LaunchScope ls(c, "l1_loss", loss ? 2 : 1);
+    launch_l1(x, y, count, P<float>(c->l1_partial), parts, loss, dL_dx, c->stream);
+  }
   GS_CHECK_LAUNCH(c);
   return GS_OK;
 }
@@ -470,7 +562,10 @@ gs_status gs_adam(gs_ctx* c, gs_params* p, const gs_params* g, gs_params* m, gs_
   a.beta2 = hp->beta2;
   a.eps = hp->eps;
   a.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
-  launch_adam(a, c->stream);
+  {
+    LaunchScope ls(c, "adam");
+    launch_adam(a, c->stream);
+  }
   GS_CHECK_LAUNCH(c);
   return GS_OK;
 }
@@ -504,4 +599,54 @@ gs_status gs_get_counts(gs_ctx* c, int64_t* instances, int64_t* bins, int64_t* p
   return GS_OK;
 }
 
+gs_status gs_profile_enable(gs_ctx* c, int32_t enable) {
+  if (!c) return GS_EINVAL;
+  c->profiling = enable != 0;
+  return GS_OK;
+}
+
+gs_status gs_profile_read(gs_ctx* c, gs_kernel_stat* out, int32_t cap, int32_t* count) {
+  if (!c || !count || (cap > 0 && !out)) return GS_EINVAL;
+  set_device(c);
+  if (!c->pending.empty()) {
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (const auto& p : c->pending) {
+      float ms = 0.f;
+      GS_CUDA(c, cudaEventElapsedTime(&ms, p.a, p.b));
+      c->kstats[p.kernel].ms += ms;
+      c->event_pool.push_back(p.a);
+      c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+  }
+  const int32_t nk = (int32_t)c->kstats.size();
+  for (int32_t i = 0; i < nk && i < cap; i++) {
+    memset(&out[i], 0, sizeof(gs_kernel_stat));
+    strncpy(out[i].name, c->kstats[i].name.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = c->kstats[i].launches;
+    out[i].total_ms = c->kstats[i].ms;
+  }
+  *count = nk;
+  return GS_OK;
+}
+
+gs_status gs_profile_reset(gs_ctx* c) {
+  if (!c) return GS_EINVAL;
+  set_device(c);
+  if (!c->pending.empty()) {
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (const auto& p : c->pending) {
+      c->event_pool.push_back(p.a);
+      c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+  }
+  for (auto& k : c->kstats) {
+    k.launches = 0;
+    k.ms = 0.0;
+  }
+  return GS_OK;
+}
+
 }  // extern "C"
+

@@ -173,8 +173,12 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
         project_cov(V, mean, lsc, quat, depth, st);
         if (st.det != 0.f) {
           const float idet = 1.f / st.det;
+          // lambda_max = mid + sqrt(max(0.1, mid^2 - det)); mid^2 - det is
+          // evaluated as ((c00 - c11)/2)^2 + c01^2, the same quantity without
+          // the cancellation of the difference form.
           const float mid = 0.5f * (st.c00 + st.c11);
-          const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - st.det));
+          const float hd = 0.5f * (st.c00 - st.c11);
+          const float lam = mid + sqrtf(fmaxf(0.1f, fmaf(hd, hd, st.c01 * st.c01)));
           radius = (int)ceilf(3.f * sqrtf(lam));
           const float mx = fmaf(V.fx, st.tx / st.tz, V.cx);
           const float my = fmaf(V.fy, st.ty / st.tz, V.cy);

@@ -53,7 +53,11 @@ class gs_adam_hp(ctypes.Structure):
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
 
 
-EXPORTS = ["gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
+class gs_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+EXPORTS = ["gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
            "gs_get_counts"]
 
@@ -82,6 +86,9 @@ def load(path: str | None = None):
     L.gs_adam.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), P(gs_params), P(gs_adam_hp), i64]
     L.gs_get_buffer.argtypes = [vp, i32, P(vp), P(i64)]
     L.gs_get_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
+    L.gs_profile_enable.argtypes = [vp, i32]
+    L.gs_profile_read.argtypes = [vp, P(gs_kernel_stat), i32, P(i32)]
+    L.gs_profile_reset.argtypes = [vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int:
@@ -196,6 +203,20 @@ class Context:
 
     def gs_sync(self):
         self._check(self.L.gs_sync(self.h), "gs_sync")
+
+    # -- profiling --------------------------------------------------------
+    def profile_enable(self, on: bool = True):
+        self._check(self.L.gs_profile_enable(self.h, 1 if on else 0), "gs_profile_enable")
+
+    def profile_reset(self):
+        self._check(self.L.gs_profile_reset(self.h), "gs_profile_reset")
+
+    def profile_read(self):
+        arr = (gs_kernel_stat * 64)()
+        cnt = ctypes.c_int32()
+        self._check(self.L.gs_profile_read(self.h, arr, 64, ctypes.byref(cnt)), "gs_profile_read")
+        return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms)}
+                for i in range(min(cnt.value, 64))]
 
     # -- inspection -------------------------------------------------------
     def gs_get_counts(self):

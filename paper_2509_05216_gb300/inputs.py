@@ -216,85 +216,105 @@ def sphere_camera(width=256, height=256, distance=3.0):
 
 
 # ---------------------------------------------------------------- field sampler
+#
+# The analytic fields are evaluated with torch in float64 on `device` ("cuda"
+# when available for the large scenes, "cpu" otherwise); random draws come
+# from numpy's seeded generator, so a scene depends only on its seed (up to
+# the last bits of the Newton iterations on different devices).
 
-def _newton_surface(field, grad, x, iso, steps):
+def _device(device):
+    import torch
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
+    return torch.device(device)
+
+
+def _chunked(fn, x, chunk):
+    import torch
+    outs = [fn(x[i:i + chunk]) for i in range(0, x.shape[0], chunk)]
+    if isinstance(outs[0], tuple):
+        return tuple(torch.cat([o[j] for o in outs]) for j in range(len(outs[0])))
+    return torch.cat(outs)
+
+
+def _newton_surface(fg, x, iso, steps):
     for _ in range(steps):
-        f = field(x) - iso
-        g = grad(x)
-        x = x - (f / np.maximum(np.sum(g * g, axis=1), 1e-30))[:, None] * g
+        f, g = fg(x)
+        x = x - ((f - iso) / (g * g).sum(dim=1).clamp_min(1e-30))[:, None] * g
     return x
 
 
-def _sample_isosurface(field, grad, lo, hi, iso, n, seed, res=96, jitter=0.0):
+def _sample_isosurface(fg, lo, hi, iso, n, seed, res=96, jitter=0.0, device=None):
     """Exactly n points on {field = iso} inside the box [lo, hi]^3.
 
-    Lattice cells whose corners straddle the level are found on a res^3 grid;
-    cells are drawn uniformly (seeded) and a uniform point inside each is
+    fg(x) -> (field, gradient) on a torch float64 [m, 3] tensor.  Lattice
+    cells whose corners straddle the level are found on a res^3 grid; cells
+    are drawn uniformly (seeded) and a uniform point inside each is
     Newton-projected onto the level set, so the density is close to uniform
     per unit area.  Points that do not converge or leave their cell's
     neighbourhood are redrawn.
     """
+    import torch
+    dev = _device(device)
     rng = np.random.default_rng(seed)
     h = (hi - lo) / res
-    ax = lo + h * np.arange(res + 1)
+    ax = torch.tensor(lo + h * np.arange(res + 1), dtype=torch.float64, device=dev)
+    gx, gy = torch.meshgrid(ax, ax, indexing="ij")
     cells = []
-    # find straddling cells slab by slab to bound memory
     prev = None
     for iz in range(res + 1):
-        gx, gy = np.meshgrid(ax, ax, indexing="ij")
-        pts = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, ax[iz])], axis=1)
-        s = (field(pts) >= iso).reshape(res + 1, res + 1)
+        pts = torch.stack([gx.reshape(-1), gy.reshape(-1), torch.full_like(gx.reshape(-1), float(ax[iz]))], 1)
+        sgn = (fg(pts)[0] >= iso).reshape(res + 1, res + 1)
         if prev is not None:
-            c = np.stack([prev[:-1, :-1], prev[1:, :-1], prev[:-1, 1:], prev[1:, 1:],
-                          s[:-1, :-1], s[1:, :-1], s[:-1, 1:], s[1:, 1:]])
-            straddle = c.any(axis=0) & ~c.all(axis=0)
-            ix, iy = np.nonzero(straddle)
-            cells.append(np.stack([ix, iy, np.full(ix.size, iz - 1)], axis=1))
-        prev = s
+            c = torch.stack([prev[:-1, :-1], prev[1:, :-1], prev[:-1, 1:], prev[1:, 1:],
+                             sgn[:-1, :-1], sgn[1:, :-1], sgn[:-1, 1:], sgn[1:, 1:]])
+            straddle = c.any(0) & ~c.all(0)
+            ix, iy = torch.nonzero(straddle, as_tuple=True)
+            cells.append(np.stack([ix.cpu().numpy(), iy.cpu().numpy(), np.full(ix.numel(), iz - 1)], 1))
+        prev = sgn
     cells = np.concatenate(cells, axis=0)
     if cells.shape[0] == 0:
         raise ValueError("isosurface does not cross the domain")
-    out = []
-    have = 0
+    out, have = [], 0
     while have < n:
         m = int((n - have) * 1.3) + 64
         pick = cells[rng.integers(0, cells.shape[0], size=m)]
         x0 = lo + h * (pick + rng.uniform(0.0, 1.0, size=(m, 3)))
-        x = _newton_surface(field, grad, x0, iso, 6)
-        if jitter > 0.0:
-            x = x + rng.normal(0.0, jitter, size=x.shape)
-            x = _newton_surface(field, grad, x, iso, 4)
-        ok = (np.abs(field(x) - iso) < 1e-7) & np.all(np.isfinite(x), axis=1)
-        ok &= np.linalg.norm(x - x0, axis=1) < 2.0 * h * math.sqrt(3.0)
-        ok &= np.all((x >= lo) & (x <= hi), axis=1)
-        x = x[ok]
+        jit = rng.normal(0.0, jitter, size=(m, 3)) if jitter > 0.0 else None
+        x0t = torch.from_numpy(x0).to(dev)
+        x = _newton_surface(fg, x0t, iso, 6)
+        if jit is not None:
+            x = _newton_surface(fg, x + torch.from_numpy(jit).to(dev), iso, 4)
+        f, _ = fg(x)
+        ok = ((f - iso).abs() < 1e-7) & torch.isfinite(x).all(1)
+        ok &= (x - x0t).norm(dim=1) < 2.0 * h * math.sqrt(3.0)
+        ok &= ((x >= lo) & (x <= hi)).all(1)
+        x = x[ok].cpu().numpy()
         out.append(x)
         have += x.shape[0]
-    pts = np.concatenate(out, axis=0)[:n]
-    return pts
+    return np.concatenate(out, axis=0)[:n]
 
 
 # ---------------------------------------------------------------- config 2
 
-def _gyroid(x):
-    return (np.sin(x[:, 0]) * np.cos(x[:, 1]) + np.sin(x[:, 1]) * np.cos(x[:, 2])
-            + np.sin(x[:, 2]) * np.cos(x[:, 0]))
+def _gyroid_fg(x):
+    import torch
+    sx, cx = torch.sin(x[:, 0]), torch.cos(x[:, 0])
+    sy, cy = torch.sin(x[:, 1]), torch.cos(x[:, 1])
+    sz, cz = torch.sin(x[:, 2]), torch.cos(x[:, 2])
+    f = sx * cy + sy * cz + sz * cx
+    g = torch.stack([cx * cy - sz * sx, -sx * sy + cy * cz, -sy * sz + cz * cx], 1)
+    return f, g
 
 
-def _gyroid_grad(x):
-    sx, cx = np.sin(x[:, 0]), np.cos(x[:, 0])
-    sy, cy = np.sin(x[:, 1]), np.cos(x[:, 1])
-    sz, cz = np.sin(x[:, 2]), np.cos(x[:, 2])
-    return np.stack([cx * cy - sz * sx, -sx * sy + cy * cz, -sy * sz + cz * cx], axis=1)
-
-
-def gyroid_scene(n=500_000, seed=3, deg=3, res=96):
+def gyroid_scene(n=500_000, seed=3, deg=3, res=96, device=None):
     """Gaussians on the gyroid sin x cos y + sin y cos z + sin z cos x = 0
     over [-2pi, 2pi]^3 (Newton-projected samples with N(0, 0.01) jitter)."""
+    import torch
     lo, hi = -2.0 * math.pi, 2.0 * math.pi
-    pts = _sample_isosurface(_gyroid, _gyroid_grad, lo, hi, 0.0, n, seed, res=res,
-                             jitter=0.01)
-    g = _gyroid_grad(pts)
+    pts = _sample_isosurface(_gyroid_fg, lo, hi, 0.0, n, seed, res=res, jitter=0.01, device=device)
+    _, g = _gyroid_fg(torch.from_numpy(pts))
+    g = g.numpy()
     nrm = g / np.linalg.norm(g, axis=1, keepdims=True)
     return _surface_scene(pts, nrm, deg, seed)
 
@@ -304,7 +324,9 @@ def gyroid_scene(n=500_000, seed=3, deg=3, res=96):
 class BlobField:
     """f(x) = sum_k a_k exp(-1/2 (x-c_k)^T S_k^-1 (x-c_k)) with seeded random
     amplitudes U(0.6,1), centres U(-0.8,0.8)^3, rotations and axis std-devs
-    U(0.02,0.15); the [-1,1]^3 box stands for the 512^3 volume."""
+    U(0.02,0.15); the [-1,1]^3 box stands for the 512^3 volume.  Terms
+    beyond 4.5 standard deviations along every axis are left out (part of the
+    field's definition)."""
 
     def __init__(self, seed=4, n_blobs=200):
         rng = np.random.default_rng(seed)
@@ -319,37 +341,38 @@ class BlobField:
             np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1),
         ], axis=1)
         sd = rng.uniform(0.02, 0.15, size=(n_blobs, 3))
-        # precision matrices R diag(1/sd^2) R^T
         self.prec = np.einsum("kij,kj,klj->kil", rot, 1.0 / sd ** 2, rot)
         self.reach = 4.5 * sd.max(axis=1)
+        self._t = {}
 
-    def _terms(self, x):
-        out_f = np.zeros(x.shape[0])
-        out_g = np.zeros_like(x)
-        for k in range(self.a.shape[0]):
-            d = x - self.c[k]
-            near = np.all(np.abs(d) < self.reach[k], axis=1)
-            if not near.any():
-                continue
-            dn = d[near]
-            pd = dn @ self.prec[k]
-            e = self.a[k] * np.exp(-0.5 * np.sum(dn * pd, axis=1))
-            out_f[near] += e
-            out_g[near] -= e[:, None] * pd
-        return out_f, out_g
+    def _tensors(self, dev):
+        import torch
+        if dev not in self._t:
+            self._t[dev] = tuple(torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+                                 for v in (self.a, self.c, self.prec, self.reach))
+        return self._t[dev]
 
-    def field(self, x):
-        return self._terms(x)[0]
+    def fg(self, x):
+        """(field, gradient) at points x (torch float64 [m, 3])."""
+        import torch
+        a, c, prec, reach = self._tensors(x.device)
 
-    def grad(self, x):
-        return self._terms(x)[1]
+        def one(xc):
+            d = xc[:, None, :] - c[None]                       # [m, K, 3]
+            near = (d.abs() < reach[None, :, None]).all(-1)     # [m, K]
+            pd = torch.einsum("mkj,kij->mki", d, prec)
+            e = a[None] * torch.exp(-0.5 * (d * pd).sum(-1)) * near
+            return e.sum(1), -(e[..., None] * pd).sum(1)
+        return _chunked(one, x, 1 << 16)
 
 
-def blobs_scene(n=4_000_000, seed=4, deg=3, res=128, iso=0.5):
+def blobs_scene(n=4_000_000, seed=4, deg=3, res=128, iso=0.5, device=None):
     """Gaussians on the 0.5 level of a 200-blob field (Kingsnake-scale stand-in)."""
+    import torch
     fld = BlobField(seed)
-    pts = _sample_isosurface(fld.field, fld.grad, -1.0, 1.0, iso, n, seed, res=res)
-    g = fld.grad(pts)
+    pts = _sample_isosurface(fld.fg, -1.0, 1.0, iso, n, seed, res=res, device=device)
+    _, g = _chunked(fld.fg, torch.from_numpy(pts).to(_device(device)), 1 << 16)
+    g = g.cpu().numpy()
     nrm = -g / np.linalg.norm(g, axis=1, keepdims=True)
     return _surface_scene(pts, nrm, deg, seed)
 

@@ -52,10 +52,16 @@ def test_projection_matches_oracle(ctx, oracle, name):
         tiles = r2[sl, 3].view(np.uint32)
         margin = (pr["flags"] & oracle.G_MARG_RECT) != 0
         # visibility and radius agree except on marginal rects
-        assert np.array_equal((tiles > 0)[~margin], vis[~margin])
+        bad = ((tiles > 0) != vis) & ~margin
+        assert not bad.any(), ("visibility differs", np.nonzero(bad)[0][:8], pr["ext"][bad][:8])
         rad = r2[sl, 2].view(np.int32)
         both = vis & (tiles > 0)
-        assert np.array_equal(rad[both & ~margin], pr["radius"][both & ~margin])
+        # the radius ceil itself may flip where 3 sqrt(lambda) is within FP32
+        # reach of an integer (the rect usually does not change then)
+        ext = pr["ext"]
+        near_int = np.abs(ext - np.round(ext)) <= 1e-5 * ext
+        bad = both & ~margin & ~near_int & (rad != pr["radius"])
+        assert not bad.any(), ("radius differs", rad[bad][:8], pr["radius"][bad][:8], pr["ext"][bad][:8])
         # depth: the same FP32 evaluation on both sides
         dep = r2[sl, 1]
         assert np.array_equal(dep[both], pr["depth"][both].astype(np.float32))
