@@ -164,6 +164,33 @@ gs_status gs_raster_bwd(gs_ctx* ctx, const gs_params* params, const float* dL_di
 gs_status gs_l1_loss(gs_ctx* ctx, const float* x, const float* y, int64_t count, float* loss,
                      float* dL_dx);
 
+/* L1 loss that allocates no device memory (the paper has no counterpart; this
+ * is a service for callers that may not allocate).  Same result as
+ * gs_l1_loss: *loss = mean |x - y| and dL_dx = sign(x - y) / count, either
+ * output may be NULL.  It exists for callers that cannot call cudaMalloc --
+ * an application that gives this library a fixed piece of device memory and
+ * forbids further allocation, a render or training loop that must never
+ * allocate (an allocation can synchronise the device) once running, a plugin
+ * whose host owns all device memory -- so it takes no context (creating one
+ * allocates) and keeps its per-block partial sums in a 16 KiB array compiled
+ * into the library, present on every GPU that loads the library until the
+ * process exits.
+ *  - Runs on the calling thread's current CUDA device, on `stream` (a
+ *    cudaStream_t, NULL = legacy default stream); x, y, loss and dL_dx are
+ *    device pointers on that device.
+ *  - The first call on a device looks up the array's device address (set-up,
+ *    once per device); make that first call before any stream capture.
+ *  - count must be in 1 .. 268,435,456 (4096 partial sums of 65,536
+ *    elements); larger counts return GS_EINVAL and launch nothing.
+ *  - All calls on a device share the array: calls whose kernels overlap on
+ *    the GPU (different streams, no ordering between them) race and give
+ *    wrong losses.  Every slot read in a call is written earlier in that same
+ *    call, so nothing needs clearing between calls.
+ * Errors: GS_EINVAL (x or y NULL, count out of range), GS_ECUDA (set-up or
+ * launch failed). */
+gs_status gs_l1_loss_noalloc(const float* x, const float* y, int64_t count, float* loss, float* dL_dx,
+                             void* stream);
+
 /* Step 5, Adam with bias correction (torch.optim.Adam semantics), dense over
  * all planes, per-group learning rate; step counts from 1.  p, m, v are
  * updated in place; g is read.  All four share n, stride and degree.

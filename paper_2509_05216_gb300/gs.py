@@ -57,7 +57,7 @@ class gs_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
-EXPORTS = ["gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
+EXPORTS = ["gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
            "gs_get_counts"]
 
@@ -86,6 +86,7 @@ def load(path: str | None = None):
     L.gs_adam.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), P(gs_params), P(gs_adam_hp), i64]
     L.gs_get_buffer.argtypes = [vp, i32, P(vp), P(i64)]
     L.gs_get_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
+    L.gs_l1_loss_noalloc.argtypes = [vp, vp, i64, vp, vp, vp]
     L.gs_profile_enable.argtypes = [vp, i32]
     L.gs_profile_read.argtypes = [vp, P(gs_kernel_stat), i32, P(i32)]
     L.gs_profile_reset.argtypes = [vp]
@@ -238,6 +239,22 @@ class Context:
                                dtype={"<f4": torch.float32, "<i8": torch.int64, "<i4": torch.int32}[spec[1]])
         t = torch.as_tensor(_DevArray(ptr.value, *spec), device="cuda:%d" % self.device)
         return t.clone()
+
+
+def gs_l1_loss_noalloc(x: torch.Tensor, y: torch.Tensor, loss: torch.Tensor | None,
+                       grad: torch.Tensor | None):
+    """L1 loss through the allocation-free entry point (no context needed):
+    for callers that may not allocate device memory.  Runs on x's device and
+    the current stream; raises GsError on a non-OK status."""
+    L = load()
+    assert x.is_cuda and x.is_contiguous() and y.is_contiguous() and x.numel() == y.numel()
+    with torch.cuda.device(x.device):
+        s = torch.cuda.current_stream(x.device).cuda_stream
+        st = L.gs_l1_loss_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
+                                  ctypes.c_void_p(loss.data_ptr() if loss is not None else 0),
+                                  ctypes.c_void_p(grad.data_ptr() if grad is not None else 0), ctypes.c_void_p(s))
+    if st != GS_OK:
+        raise GsError(st, "gs_l1_loss_noalloc(count=%d)" % x.numel())
 
 
 def image_offsets(cams):
