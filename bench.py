@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--plain-views", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
+    ap.add_argument("--serve-rate", type=float, default=100.0, help="render requests/s (0: skip serving)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--fwd-variant", type=int, default=0, help="force the forward compositing variant")
+    ap.add_argument("--bwd-variant", type=int, default=0, help="force the backward compositing variant")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cache", default=os.environ.get("GS_SCENE_CACHE", "/tmp/gs_scene_cache"))
     return ap.parse_args()
@@ -202,7 +207,7 @@ def algorithmic_work(name, n, P, B, I, pairs, pixels, passes):
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
-    from paper_2509_05216_gb300 import gs
+    from paper_2509_05216_gb300 import autotune, gs
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,6 +234,16 @@ def gpu_arm(args):
     for i in range(args.warmup):
         tr.step(*batch(i), img, dimg)
     ctx.gs_sync()
+    # launch options picked by the autotuner (timed on this workload, cached)
+    key = autotune.workload_key(tr.n, cams[:B], B)
+    if args.fwd_variant or args.bwd_variant:
+        tuned = {gs.GS_OPT_RASTER_FWD: args.fwd_variant or 2, gs.GS_OPT_RASTER_BWD: args.bwd_variant or 8}
+        for opt, val in tuned.items():
+            ctx.gs_set_option(opt, val)
+    else:
+        tuned = autotune.tune([ctx], lambda: tr.step(*batch(0), img, dimg), key,
+                              use_cache=not args.retune)
+    ctx.gs_sync()
     # timed region: K batched steps
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -238,10 +253,12 @@ def gpu_arm(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
         ev0.record(stream)
         for i in range(args.steps):
             tr.step(*batch(args.warmup + i), img, dimg)
         ev1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -294,6 +311,13 @@ def gpu_arm(args):
     tr2 = Trainer(ctx2, trained, dev)
     one_img = torch.empty(3 * args.res * args.res, device=dev)
     one_dimg = torch.empty_like(one_img)
+    one_t = targets[0][:one_img.numel()]
+    if args.fwd_variant or args.bwd_variant:
+        for opt, val in tuned.items():
+            ctx2.gs_set_option(opt, val)
+    else:
+        autotune.tune([ctx2], lambda: tr2.step([cams[0]], one_t, one_img, one_dimg),
+                      autotune.workload_key(tr2.n, cams[:1], 1), use_cache=not args.retune)
     for i in range(2):
         tr2.step([cams[i]], targets[0][i * one_img.numel():(i + 1) * one_img.numel()], one_img, one_dimg)
     ctx2.gs_sync()
@@ -334,8 +358,17 @@ def gpu_arm(args):
                 "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
         "instances_per_step": int(inst), "pairs_per_step": pairs, "kernels": per_kernel,
-        "setup_s": round(time.time() - t0, 1),
+        "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
     }
+    if args.serve_rate > 0:
+        tr.ctx.gs_sync()
+        torch.cuda.synchronize(dev)
+        batched = serve_run(tr.p, tr.n, tr.deg, local, args.serve_rate, args.serve_seconds, 2, 16)
+        single = serve_run(tr.p, tr.n, tr.deg, local, args.serve_rate, args.serve_seconds, 1, 1)
+        out["render"] = {"p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"],
+                         "frames_per_s": batched["frames_per_s"], "rate_req_per_s": args.serve_rate,
+                         "one_request_per_launch": {k: single[k] for k in ("p50_ms", "p99_ms", "frames_per_s")},
+                         "resolutions": ["%dx%d" % r for r in SERVE_RES]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene, trained, cams, args)
     ctx.close()
@@ -343,6 +376,71 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- serving
+
+SERVE_RES = [(512, 512), (1024, 1024), (2048, 2048), (3840, 2160)]
+
+
+def serve_run(params, n, deg, device, rate, duration_s, slots, max_batch, seed=6):
+    """Poisson arrivals at `rate` req/s for `duration_s`; each request a random
+    orbit camera (radius 4) at a resolution drawn uniformly from SERVE_RES.
+    Returns latency percentiles (submit -> poll-complete, host clock) and
+    frames/s."""
+    import torch
+    from paper_2509_05216_gb300 import gs, inputs
+    rng = np.random.default_rng(seed)
+    srv = gs.Server(params, n, deg, device=device, slots=slots, max_batch_views=max_batch,
+                    memory_budget_bytes=48 << 30, output_pool_bytes=8 << 30)
+    k = max(1, int(rate * duration_s))
+    gaps = rng.exponential(1.0 / rate, size=k)
+    cams = []
+    for i in range(k):
+        w, h = SERVE_RES[rng.integers(0, len(SERVE_RES))]
+        cams.append(inputs.random_orbit_camera(rng, 4.0, w, h))
+    # warm-up: one request per resolution
+    for w, h in SERVE_RES:
+        t = srv.gs_serve_submit(inputs.random_orbit_camera(rng, 4.0, w, h))
+        srv.gs_serve_poll(t)
+        srv.gs_serve_release(t)
+    sub = [0.0] * k
+    done = [0.0] * k
+    tickets = [None] * k
+    ready = threading.Semaphore(0)
+
+    def poller():
+        for i in range(k):
+            ready.acquire()
+            st, _ = srv.gs_serve_poll(tickets[i])
+            done[i] = time.perf_counter()
+            srv.gs_serve_release(tickets[i])
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    nxt = t0
+    for i in range(k):
+        nxt += gaps[i]
+        dt = nxt - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        while True:
+            try:
+                sub[i] = time.perf_counter()
+                tickets[i] = srv.gs_serve_submit(cams[i])
+                break
+            except gs.GsError:
+                time.sleep(0.0005)  # queue or pool full: back-pressure
+        ready.release()
+    th.join()
+    t1 = max(done)
+    lat = np.array(done) - np.array(sub)
+    stats = srv.gs_serve_stats()
+    srv.close()
+    return {"rate": rate, "requests": k, "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+            "frames_per_s": round(k / (t1 - t0), 2), "batches": stats["batches"]}
 
 
 # ---------------------------------------------------------------- oracle (CPU) arm

@@ -115,6 +115,19 @@ gs_status gs_set_stream(gs_ctx* ctx, void* stream);
  * GS_ECAPACITY or GS_ETIMEOUT) and clear it. */
 gs_status gs_sync(gs_ctx* ctx);
 
+/* Tunable options of a context (the autotuner sets these). */
+typedef enum {
+  GS_OPT_RASTER_FWD = 0, /* forward compositing kernel: 1, 2 or 4 = pixels per
+                            thread with one block per tile, 8 = one warp per
+                            tile.  All variants give the same result up to
+                            FP32 rounding. */
+  GS_OPT_RASTER_BWD = 1  /* backward compositing kernel, same values */
+} gs_option;
+
+/* Set / read an option.  Errors: GS_EINVAL (unknown option, bad value). */
+gs_status gs_set_option(gs_ctx* ctx, int32_t option, int64_t value);
+gs_status gs_get_option(gs_ctx* ctx, int32_t option, int64_t* value);
+
 /* ---------------------------------------------------------------- the path */
 
 /* Step 1, projection (EWA splatting of 3D-GS, Section I; Gaussians from the
@@ -197,6 +210,55 @@ gs_status gs_l1_loss_noalloc(const float* x, const float* y, int64_t count, floa
  * Errors: GS_EINVAL (mismatched sets, step < 1), GS_ECUDA. */
 gs_status gs_adam(gs_ctx* ctx, gs_params* p, const gs_params* g, gs_params* m, gs_params* v,
                   const gs_adam_hp* hp, int64_t step);
+
+/* ---------------------------------------------------------------- serving */
+
+/* Render server: the trained Gaussians stay resident and camera requests of
+ * any resolution are batched continuously (the paper's goal is interactive
+ * visualisation of the trained model, Sections I and V).  A worker thread
+ * forms a batch from the oldest pending requests whenever a slot is free and
+ * the batch's memory estimate (per-view workspace + output) fits the budget,
+ * and renders it (projection, binning, forward compositing) on the slot's own
+ * context and stream, so batches overlap on the device.  Each result is the
+ * same whether rendered alone or in a mix. */
+typedef struct gs_server gs_server;
+
+typedef struct {
+  int32_t slots;               /* batches in flight, 1..16 (default 2) */
+  int32_t max_batch_views;     /* views per batch, 1..64 (default 16) */
+  int32_t max_queue;           /* pending requests before GS_EBUSY (default 4096) */
+  int32_t reserved;
+  int64_t memory_budget_bytes; /* estimate of running batches (default 16 GiB) */
+  int64_t output_pool_bytes;   /* server-owned output pool; 0 = callers pass outputs */
+} gs_serve_cfg;
+
+/* Start a server on `device` for the resident set (device memory owned by
+ * the caller, unchanged while the server lives).  cfg may be NULL.
+ * Errors: GS_EINVAL, GS_ENOMEM, GS_ECUDA. */
+gs_status gs_serve_create(gs_server** out, int device, const gs_params* resident, const gs_serve_cfg* cfg);
+
+/* Stop the worker, wait for running batches and free the server. */
+void gs_serve_destroy(gs_server* srv);
+
+/* Queue one camera.  out_device: device buffer of 3*W*H floats (planar RGB)
+ * that receives the image, or NULL to use the server's output pool (then
+ * gs_serve_release frees the region).  *ticket identifies the request.
+ * Errors: GS_EINVAL (bad camera, NULL output without a pool), GS_EBUSY
+ * (queue full, output pool full, or the request alone exceeds the budget). */
+gs_status gs_serve_submit(gs_server* srv, const gs_camera* cam, float* out_device, uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = do not wait) for a request.  On completion
+ * returns GS_OK with *image = its device image and *result = its status;
+ * GS_EAGAIN if not done in time; GS_EINVAL for an unknown ticket. */
+gs_status gs_serve_poll(gs_server* srv, uint64_t ticket, int64_t timeout_us, const float** image,
+                        gs_status* result);
+
+/* Forget a completed request (and free its pool region).  GS_EBUSY if it is
+ * still pending or running. */
+gs_status gs_serve_release(gs_server* srv, uint64_t ticket);
+
+/* Counters: batches launched, views rendered, requests pending. */
+gs_status gs_serve_stats(gs_server* srv, int64_t* batches, int64_t* rendered, int64_t* pending);
 
 /* ---------------------------------------------------------------- inspection */
 

@@ -1,0 +1,90 @@
+"""Project-written autotuner for the rasterizer's launch options.
+
+For a workload key (Gaussian count, resolution mix, views per batch, GPU name)
+it times the real training step under every candidate value of each option
+(CUDA events on the current stream, after a warm-up step) and keeps the
+fastest.  Results are cached as JSON so a later run with the same key skips
+the search.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import gs
+
+CANDIDATES = {gs.GS_OPT_RASTER_FWD: [2, 8, 4, 1], gs.GS_OPT_RASTER_BWD: [8, 2, 4, 1]}
+
+
+def workload_key(n, cams, batch):
+    res = sorted({(c["width"], c["height"]) for c in cams})
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    return "n%d|res%s|b%d|%s" % (n, ",".join("%dx%d" % r for r in res), batch, name)
+
+
+def _cache_path():
+    return os.environ.get("GS_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache",
+                                                             "gs_gb300_autotune.json"))
+
+
+def _load():
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save(db):
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".%d.tmp" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def time_step(step, reps=2):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step()
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def tune(ctxs, step, key, candidates=None, reps=2, use_cache=True):
+    """Pick option values for `ctxs` (contexts the step uses) by timing `step`.
+
+    Returns {option: value} and leaves the chosen values set."""
+    candidates = candidates or CANDIDATES
+    db = _load() if use_cache else {}
+    if key in db:
+        chosen = {int(k): v for k, v in db[key]["options"].items()}
+    else:
+        chosen, report = {}, {}
+        for opt, values in candidates.items():
+            best, best_ms = None, float("inf")
+            for v in values:
+                for c in ctxs:
+                    c.gs_set_option(opt, v)
+                ms = time_step(step, reps)
+                report["%d=%d" % (opt, v)] = round(ms, 3)
+                if ms < best_ms:
+                    best, best_ms = v, ms
+            chosen[opt] = best
+        db[key] = {"options": {str(k): v for k, v in chosen.items()}, "ms": report}
+        if use_cache:
+            _save(db)
+    for opt, v in chosen.items():
+        for c in ctxs:
+            c.gs_set_option(opt, v)
+    return chosen

@@ -61,24 +61,24 @@ void launch_scan_block_sums(const uint32_t* sums, int64_t nb, uint32_t* offsets,
 
 // ---------------------------------------------------------------- duplicate
 
-// Same block partition as the projection (one thread per Gaussian, looping
-// over views): instances are emitted in (Gaussian, view, ty, tx) order.
+// Same block partition as the projection (256 Gaussians per block, all views).
+// Each warp emits the instances of its 32 Gaussians view by view: the
+// warp's (Gaussian, view) items are expanded cooperatively, lane j writing
+// output position base + 32 i + j of the chunk i, so every store of keys and
+// values is coalesced.  Within a view the order is (Gaussian, ty, tx), so in
+// every bin the instances appear in increasing Gaussian index, which the
+// stable sort preserves for equal keys.
 __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = g < a.n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t mine = 0;
   if (live)
     for (int v = 0; v < a.B; v++) mine += a.tiles[(int64_t)v * a.stride + g];
-  // block exclusive scan of `mine`
+  // per-warp totals -> block exclusive scan over warps
   __shared__ uint32_t wsum[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t inc = mine;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
-    if (lane >= off) inc += y;
-  }
-  if (lane == 31) wsum[wid] = inc;
+  const uint32_t wtot = __reduce_add_sync(0xffffffffu, mine);
+  if (lane == 0) wsum[wid] = wtot;
   __syncthreads();
   if (wid == 0) {
     const int nw = blockDim.x >> 5;
@@ -92,30 +92,64 @@ __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
     wsum[lane] = winc - w;
   }
   __syncthreads();
-  if (!live || mine == 0) return;
-  int64_t pos = (int64_t)a.block_offsets[blockIdx.x] + wsum[wid] + (inc - mine);
-  if (pos + mine > a.capacity) {
-    atomicOr(a.status, kStatusCapacity);
+  int64_t base = (int64_t)a.block_offsets[blockIdx.x] + wsum[wid];
+  if (wtot == 0) return;
+  if (base + wtot > a.capacity) {
+    if (lane == 0) atomicOr(a.status, kStatusCapacity);
     return;
   }
+  const unsigned lt = (1u << lane) - 1u;
   for (int v = 0; v < a.B; v++) {
     const int64_t o = (int64_t)v * a.stride + g;
-    if (a.tiles[o] == 0) continue;
+    const uint32_t cnt = live ? a.tiles[o] : 0u;
+    // exclusive offsets of the warp's items in this view
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    const uint32_t excl = inc - cnt;
+    const uint32_t vtot = __shfl_sync(0xffffffffu, inc, 31);
+    if (vtot == 0) continue;
     const ViewRec& V = a.views[v];
-    const float4 r0 = a.rec0[o];
-    const float4 r2 = a.rec2[o];
-    int x0, x1, y0, y1;
-    tile_rect(V, r0.x, r0.y, __float_as_int(r2.z), x0, x1, y0, y1);
-    const uint64_t dbits = (uint64_t)__float_as_uint(r2.y);
-    const int64_t stop = pos + a.tiles[o];  // never write past this view's share
-    for (int ty = y0; ty < y1; ty++)
-      for (int tx = x0; tx < x1 && pos < stop; tx++) {
-        const uint64_t bin = (uint64_t)(V.tile_offset + ty * V.gw + tx);
-        a.keys[pos] = (bin << 32) | dbits;
-        a.vals[pos] = (uint32_t)g;
-        pos++;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    uint32_t dbits = 0;
+    if (cnt) {
+      const float4 r0 = a.rec0[o];
+      const float4 r2 = a.rec2[o];
+      tile_rect(V, r0.x, r0.y, __float_as_int(r2.z), x0, x1, y0, y1);
+      dbits = __float_as_uint(r2.y);
+    }
+    const int rw = x1 - x0;
+    for (uint32_t q0 = 0; q0 < vtot; q0 += 32) {
+      const uint32_t q = q0 + lane;
+      // owner: the last lane whose exclusive offset is <= q
+      int own = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cand = own + step;
+        const uint32_t ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+        if (cand < 32 && ec <= q) own = cand;
       }
+      const uint32_t e_own = __shfl_sync(0xffffffffu, excl, own);
+      const int ox0 = __shfl_sync(0xffffffffu, x0, own);
+      const int oy0 = __shfl_sync(0xffffffffu, y0, own);
+      const int orw = __shfl_sync(0xffffffffu, rw, own);
+      const uint32_t od = __shfl_sync(0xffffffffu, dbits, own);
+      const uint32_t oc = __shfl_sync(0xffffffffu, cnt, own);
+      if (q < vtot && q - e_own < oc && orw > 0) {
+        const uint32_t local = q - e_own;
+        const int tx = ox0 + (int)(local % (uint32_t)orw);
+        const int ty = oy0 + (int)(local / (uint32_t)orw);
+        const uint64_t bin = (uint64_t)(V.tile_offset + ty * V.gw + tx);
+        a.keys[base + q] = (bin << 32) | (uint64_t)od;
+        a.vals[base + q] = (uint32_t)(g - lane + own);
+      }
+    }
+    base += vtot;
   }
+  (void)lt;
 }
 
 void launch_duplicate(const DuplicateArgs& a, cudaStream_t s) {

@@ -34,7 +34,8 @@ struct gs_ctx {
   int* status_d = nullptr;
   int* status_h = nullptr;     // pinned
   uint64_t* pinned = nullptr;  // pinned scratch for small read-backs (16 KB)
-  int raster_ppt = 2;
+  int raster_fwd = 2;  // compositing variants (pixels per thread; 8 = one warp per tile)
+  int raster_bwd = 8;
 
   // last batch
   int B = 0, deg = 0;
@@ -194,10 +195,6 @@ gs_status gs_create(gs_ctx** out, int device, const gs_config* cfg) {
   gs_ctx* c = new gs_ctx();
   c->device = device;
   c->cfg = conf;
-  if (const char* e = getenv("GS_RASTER_PPT")) {
-    int v = atoi(e);
-    if (v == 1 || v == 2 || v == 4) c->raster_ppt = v;
-  }
   if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&c->status_d, sizeof(int)) != cudaSuccess ||
       cudaMemset(c->status_d, 0, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&c->status_h, sizeof(int)) != cudaSuccess ||
@@ -461,7 +458,7 @@ gs_status gs_raster_fwd(gs_ctx* c, float* images) {
   r.image = images;
   {
     LaunchScope ls(c, "raster_fwd");
-    launch_raster_fwd(r, c->bins, c->raster_ppt, c->stream);
+    launch_raster_fwd(r, c->bins, c->raster_fwd, c->stream);
   }
   GS_CHECK_LAUNCH(c);
   c->rastered = true;
@@ -487,7 +484,7 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   r.g2d = P<float4>(c->g2d);
   {
     LaunchScope ls(c, "raster_bwd");
-    launch_raster_bwd(r, c->bins, c->raster_ppt, c->stream);
+    launch_raster_bwd(r, c->bins, c->raster_bwd, c->stream);
   }
   GS_CHECK_LAUNCH(c);
   ProjectBwdArgs b{};
@@ -597,6 +594,29 @@ gs_status gs_get_counts(gs_ctx* c, int64_t* instances, int64_t* bins, int64_t* p
   if (bins) *bins = c->bins;
   if (pixels) *pixels = c->pixels;
   return GS_OK;
+}
+
+gs_status gs_set_option(gs_ctx* c, int32_t option, int64_t value) {
+  if (!c) return GS_EINVAL;
+  switch (option) {
+    case GS_OPT_RASTER_FWD:
+    case GS_OPT_RASTER_BWD:
+      if (value != 1 && value != 2 && value != 4 && value != 8)
+        return fail(c, GS_EINVAL, "raster variant must be 1, 2, 4 or 8");
+      (option == GS_OPT_RASTER_FWD ? c->raster_fwd : c->raster_bwd) = (int)value;
+      return GS_OK;
+    default:
+      return fail(c, GS_EINVAL, "unknown option %d", option);
+  }
+}
+
+gs_status gs_get_option(gs_ctx* c, int32_t option, int64_t* value) {
+  if (!c || !value) return GS_EINVAL;
+  switch (option) {
+    case GS_OPT_RASTER_FWD: *value = c->raster_fwd; return GS_OK;
+    case GS_OPT_RASTER_BWD: *value = c->raster_bwd; return GS_OK;
+    default: return fail(c, GS_EINVAL, "unknown option %d", option);
+  }
 }
 
 gs_status gs_profile_enable(gs_ctx* c, int32_t enable) {

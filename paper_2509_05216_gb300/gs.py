@@ -57,7 +57,16 @@ class gs_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
-EXPORTS = ["gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
+GS_OPT_RASTER_FWD, GS_OPT_RASTER_BWD = 0, 1
+
+class gs_serve_cfg(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch_views", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("memory_budget_bytes", ctypes.c_int64),
+                ("output_pool_bytes", ctypes.c_int64)]
+
+
+EXPORTS = ["gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
+           "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
            "gs_get_counts"]
 
@@ -86,6 +95,15 @@ def load(path: str | None = None):
     L.gs_adam.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), P(gs_params), P(gs_adam_hp), i64]
     L.gs_get_buffer.argtypes = [vp, i32, P(vp), P(i64)]
     L.gs_get_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
+    L.gs_serve_create.argtypes = [P(vp), ctypes.c_int, P(gs_params), P(gs_serve_cfg)]
+    L.gs_serve_destroy.argtypes = [vp]
+    L.gs_serve_destroy.restype = None
+    L.gs_serve_submit.argtypes = [vp, P(gs_camera), vp, P(ctypes.c_uint64)]
+    L.gs_serve_poll.argtypes = [vp, ctypes.c_uint64, i64, P(vp), P(ctypes.c_int)]
+    L.gs_serve_release.argtypes = [vp, ctypes.c_uint64]
+    L.gs_serve_stats.argtypes = [vp, P(i64), P(i64), P(i64)]
+    L.gs_set_option.argtypes = [vp, i32, i64]
+    L.gs_get_option.argtypes = [vp, i32, P(i64)]
     L.gs_l1_loss_noalloc.argtypes = [vp, vp, i64, vp, vp, vp]
     L.gs_profile_enable.argtypes = [vp, i32]
     L.gs_profile_read.argtypes = [vp, P(gs_kernel_stat), i32, P(i32)]
@@ -205,6 +223,15 @@ class Context:
     def gs_sync(self):
         self._check(self.L.gs_sync(self.h), "gs_sync")
 
+    # -- options ----------------------------------------------------------
+    def gs_set_option(self, option: int, value: int):
+        self._check(self.L.gs_set_option(self.h, option, int(value)), "gs_set_option")
+
+    def gs_get_option(self, option: int) -> int:
+        v = ctypes.c_int64()
+        self._check(self.L.gs_get_option(self.h, option, ctypes.byref(v)), "gs_get_option")
+        return v.value
+
     # -- profiling --------------------------------------------------------
     def profile_enable(self, on: bool = True):
         self._check(self.L.gs_profile_enable(self.h, 1 if on else 0), "gs_profile_enable")
@@ -255,6 +282,72 @@ def gs_l1_loss_noalloc(x: torch.Tensor, y: torch.Tensor, loss: torch.Tensor | No
                                   ctypes.c_void_p(grad.data_ptr() if grad is not None else 0), ctypes.c_void_p(s))
     if st != GS_OK:
         raise GsError(st, "gs_l1_loss_noalloc(count=%d)" % x.numel())
+
+
+class Server:
+    """Continuous-batching render server (gs_serve_*): the resident parameter
+    tensor must stay alive and unchanged while the server runs."""
+
+    def __init__(self, params: torch.Tensor, n: int, deg: int, device: int = 0, slots: int = 2,
+                 max_batch_views: int = 16, max_queue: int = 4096, memory_budget_bytes: int = 16 << 30,
+                 output_pool_bytes: int = 1 << 30):
+        self.L = load()
+        self.params = params  # keep alive
+        self.device = device
+        p = params_struct(params, n, deg)
+        cfg = gs_serve_cfg(slots, max_batch_views, max_queue, 0, memory_budget_bytes, output_pool_bytes)
+        h = ctypes.c_void_p()
+        st = self.L.gs_serve_create(ctypes.byref(h), device, ctypes.byref(p), ctypes.byref(cfg))
+        if st != GS_OK:
+            raise GsError(st, "gs_serve_create failed")
+        self.h = h
+        self._shape = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.gs_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def gs_serve_submit(self, cam, out: torch.Tensor | None = None) -> int:
+        c = camera_struct(cam)
+        t = ctypes.c_uint64()
+        st = self.L.gs_serve_submit(self.h, ctypes.byref(c), ctypes.c_void_p(out.data_ptr() if out is not None else 0),
+                                    ctypes.byref(t))
+        if st != GS_OK:
+            raise GsError(st, "gs_serve_submit")
+        self._shape[t.value] = (3, int(cam["height"]), int(cam["width"]))
+        return t.value
+
+    def gs_serve_poll(self, ticket: int, timeout_us: int = -1):
+        """Returns (status, image view or None); status GS_EAGAIN on timeout."""
+        ptr, res = ctypes.c_void_p(), ctypes.c_int()
+        st = self.L.gs_serve_poll(self.h, ticket, int(timeout_us if timeout_us >= 0 else 1 << 60),
+                                  ctypes.byref(ptr), ctypes.byref(res))
+        if st == GS_EAGAIN:
+            return GS_EAGAIN, None
+        if st != GS_OK:
+            raise GsError(st, "gs_serve_poll(%d)" % ticket)
+        if res.value != GS_OK:
+            return res.value, None
+        img = torch.as_tensor(_DevArray(ptr.value, self._shape[ticket], "<f4"), device="cuda:%d" % self.device)
+        return GS_OK, img
+
+    def gs_serve_release(self, ticket: int):
+        st = self.L.gs_serve_release(self.h, ticket)
+        self._shape.pop(ticket, None)
+        if st != GS_OK:
+            raise GsError(st, "gs_serve_release(%d)" % ticket)
+
+    def gs_serve_stats(self):
+        b, r, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self.L.gs_serve_stats(self.h, ctypes.byref(b), ctypes.byref(r), ctypes.byref(p))
+        return {"batches": b.value, "rendered": r.value, "pending": p.value}
 
 
 def image_offsets(cams):

@@ -98,9 +98,15 @@ def test_binning_is_bit_exact(ctx, name):
     assert np.array_equal(gr, ranges)
 
 
+VARIANTS = [1, 2, 4, 8]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("name", list(SCENES))
-def test_image_matches_oracle(ctx, oracle, name):
+def test_image_matches_oracle(ctx, oracle, name, variant):
     scene, cams = SCENES[name]()
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, variant)
+    ctx.gs_set_option(gs.GS_OPT_RASTER_BWD, variant)
     _, img = run_forward(ctx, scene, cams)
     views = gs.split_images(img, cams)
     tf = ctx.gs_get_buffer(gs.GS_BUF_TFINAL).cpu().numpy()
@@ -119,9 +125,12 @@ def test_image_matches_oracle(ctx, oracle, name):
         off += HW
 
 
+@pytest.mark.parametrize("fwd,bwd", [(1, 1), (2, 2), (4, 4), (8, 8), (2, 8), (8, 2)])
 @pytest.mark.parametrize("name", list(SCENES))
-def test_gradient_matches_oracle(ctx, oracle, name):
+def test_gradient_matches_oracle(ctx, oracle, name, fwd, bwd):
     scene, cams = SCENES[name]()
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, fwd)
+    ctx.gs_set_option(gs.GS_OPT_RASTER_BWD, bwd)
     p, _ = run_forward(ctx, scene, cams)
     rng = np.random.default_rng(7)
     dimgs = []
@@ -148,6 +157,30 @@ def test_gradient_matches_oracle(ctx, oracle, name):
     for v in range(len(cams)):
         got = g2d[v * stride: v * stride + n, :9][keep]
         assert rel_l2(got, ref2d[v][keep]) <= 1e-3
+
+
+def test_raster_variants_agree(ctx, oracle):
+    scene, cams = SCENES["random_deg3_mixed"]()
+    out = {}
+    for variant in VARIANTS:
+        ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, variant)
+        _, img = run_forward(ctx, scene, cams)
+        out[variant] = np.concatenate([t.cpu().numpy().reshape(3, -1) for t in gs.split_images(img, cams)], 1)
+    # FP32 evaluation order differs between variants: compare away from the
+    # oracle's marginal decisions
+    ok = np.concatenate([~oracle.render(scene, c)[2].reshape(-1) for c in cams])
+    for variant in VARIANTS[1:]:
+        assert np.abs(out[variant] - out[VARIANTS[0]])[:, ok].max() <= 1e-5
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, 2)
+
+
+def test_options_reject_bad_values(ctx):
+    with pytest.raises(gs.GsError):
+        ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, 3)
+    with pytest.raises(gs.GsError):
+        ctx.gs_set_option(99, 1)
+    assert ctx.gs_get_option(gs.GS_OPT_RASTER_FWD) in VARIANTS
+    assert ctx.gs_get_option(gs.GS_OPT_RASTER_BWD) in VARIANTS
 
 
 def test_batched_forward_equals_single_views(ctx):
