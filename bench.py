@@ -182,9 +182,9 @@ RASTER_OPS_BWD = 60   # FP32 ops per evaluated pair, backward
 
 def algorithmic_work(name, n, P, B, I, pairs, pixels, passes):
     if name == "project_fwd":
-        return "hbm", n * (4 * P + B * 52.0)
+        return "hbm", n * (4 * P + B * 60.0)
     if name == "project_bwd":
-        return "hbm", n * (8 * P + B * 48.0)
+        return "hbm", n * (8 * P + B * 36.0)
     if name == "adam":
         return "hbm", 28.0 * P * n
     if name == "onesweep_pass":

@@ -247,7 +247,7 @@ void gs_serve_destroy(gs_server* srv);
  * (queue full, output pool full, or the request alone exceeds the budget). */
 gs_status gs_serve_submit(gs_server* srv, const gs_camera* cam, float* out_device, uint64_t* ticket);
 
-/* Wait up to timeout_us (0 = do not wait) for a request.  On completion
+/* Wait up to timeout_us (0 = do not wait, negative = no limit) for a request.  On completion
  * returns GS_OK with *image = its device image and *result = its status;
  * GS_EAGAIN if not done in time; GS_EINVAL for an unknown ticket. */
 gs_status gs_serve_poll(gs_server* srv, uint64_t ticket, int64_t timeout_us, const float** image,
@@ -265,15 +265,18 @@ gs_status gs_serve_stats(gs_server* srv, int64_t* batches, int64_t* rendered, in
 /* Intermediate buffers of the last batch (device pointers owned by the
  * context, valid until the next call that rewrites them). */
 typedef enum {
-  GS_BUF_REC0 = 0,   /* float4 [B][N]: mu_x, mu_y, conic A, conic B */
-  GS_BUF_REC1 = 1,   /* float4 [B][N]: conic C, opacity, red, green */
-  GS_BUF_REC2 = 2,   /* float4 [B][N]: blue, depth, radius (int bits), tiles (uint bits) */
+  GS_BUF_REC0 = 0,   /* float4 [B][N]: mu_x, mu_y, cA, cB with cA = -A log2(e) / 2,
+                        cB = -B log2(e) for the conic (A, B, C) */
+  GS_BUF_REC1 = 1,   /* float4 [B][N]: cC = -C log2(e) / 2, opacity, red, green */
+  GS_BUF_REC2 = 2,   /* float4 [B][N]: blue, hx, hy (half-extents of the box around
+                        the alpha >= 1/255 ellipse), depth */
   GS_BUF_KEYS = 3,   /* uint64 [I]: sorted keys */
   GS_BUF_VALS = 4,   /* uint32 [I]: sorted Gaussian indices */
   GS_BUF_RANGES = 5, /* uint32 [bins][2]: [start, end) per bin */
   GS_BUF_TFINAL = 6, /* float [pixels]: transmittance after the last contributor */
   GS_BUF_NLAST = 7,  /* uint32 [pixels]: 1 + list position of the last contributor */
-  GS_BUF_G2D = 8     /* float [B][N][12]: dL/d(mu_x, mu_y, A, B, C, opacity, r, g, b) */
+  GS_BUF_G2D = 8,    /* float [9][B][N] planes: dL/d(mu_x, mu_y, A, B, C, opacity, r, g, b) */
+  GS_BUF_REC3 = 9    /* int2 [B][N]: radius, tiles touched (0: culled) */
 } gs_buffer;
 
 /* *ptr = device pointer of the buffer, *count = number of elements (of the

@@ -117,9 +117,8 @@ __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
     uint32_t dbits = 0;
     if (cnt) {
       const float4 r0 = a.rec0[o];
-      const float4 r2 = a.rec2[o];
-      tile_rect(V, r0.x, r0.y, __float_as_int(r2.z), x0, x1, y0, y1);
-      dbits = __float_as_uint(r2.y);
+      tile_rect(V, r0.x, r0.y, a.rec3[o].x, x0, x1, y0, y1);
+      dbits = __float_as_uint(a.rec2[o].w);
     }
     const int rw = x1 - x0;
     for (uint32_t q0 = 0; q0 < vtot; q0 += 32) {
@@ -169,7 +168,8 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kFlagAggregate = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
-constexpr int kSpinLimit = 1 << 20;  // about a second of polling
+constexpr int kSpinLimit = 1 << 20;  // look-back rounds before giving up (about a second)
+constexpr int kLookWindow = 16;       // statuses read per look-back round
 
 size_t sort_lookback_bytes(int64_t count) {
   const int64_t parts = (count + kSortTile - 1) / kSortTile;
@@ -207,18 +207,21 @@ void launch_digit_histogram(const uint64_t* keys, int64_t count, int npass, uint
 // One LSD pass: rank keys of the partition by digit (stable), find the
 // partition's offset for each digit by decoupled look-back over the earlier
 // partitions (bounded waits), then scatter through shared memory so that the
-// global writes are coalesced.  hist_pass: the 256 digit counts of this pass.
+// global writes are coalesced.  Keys are loaded up front (all loads in
+// flight before ranking); keys and then values go through one shared buffer,
+// which keeps the block at 46 KB of shared memory and 64 registers per thread
+// (four blocks per SM).  hist_pass: exclusive digit offsets of this pass.
 struct SortSmem {
   uint32_t warp_hist[kSortWarps][kRadix];  // per-warp digit counts -> offsets
   uint32_t digit_start[kRadix];            // exclusive scan of the tile's digit counts
   uint32_t global_base[kRadix];            // global destination of the digit's first key
   uint32_t part;
   int timed_out;
-  uint64_t keys[kSortTile];
-  uint32_t vals[kSortTile];
+  uint64_t buf[kSortTile];                 // keys, then values, in tile-sorted order
+  uint8_t dig[kSortTile];                  // digit of each tile-sorted position
 };
 
-__global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
+__global__ void __launch_bounds__(kSortThreads, 4) onesweep_pass_kernel(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t count, int shift, const uint32_t* __restrict__ hist_pass,
     uint32_t* lookback, uint32_t* counter, int* status) {
@@ -235,33 +238,35 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
   const int64_t nparts = (count + kSortTile - 1) / kSortTile;
   if ((int64_t)part >= nparts) return;
   const int64_t base = (int64_t)part * kSortTile;
+  const int64_t wbase = base + (int64_t)wid * kSortItems * 32 + lane;  // item i at wbase + 32 i
 
-  // load (warp-striped: warp w owns positions [w * items * 32, ...))
   uint64_t key[kSortItems];
-  uint32_t val[kSortItems];
-  uint32_t rank[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; i++) {
+    const int64_t p = wbase + 32 * i;
+    key[i] = p < count ? kin[p] : ~0ull;
+  }
+  // stable rank inside the warp (warp-striped order), 16-bit per item
+  uint32_t rk[kSortItems / 2];
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    const int64_t p = base + (int64_t)wid * kSortItems * 32 + i * 32 + lane;
-    const bool ok = p < count;
-    key[i] = ok ? kin[p] : ~0ull;
-    val[i] = ok ? vin[p] : 0u;
-    const unsigned vm = __ballot_sync(0xffffffffu, ok);
-    rank[i] = 0xffffffffu;
+    const bool ok = wbase + 32 * i < count;
+    const uint32_t d = ok ? (uint32_t)(key[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t r = 0, before = 0;
     if (ok) {
-      const uint32_t d = (uint32_t)(key[i] >> shift) & (kRadix - 1);
-      const unsigned peers = __match_any_sync(vm, d);
-      const uint32_t before = sm.warp_hist[wid][d];
-      rank[i] = before + __popc(peers & lt);
-      __syncwarp(vm);
-      if ((peers & lt) == 0) sm.warp_hist[wid][d] = before + __popc(peers);
+      before = sm.warp_hist[wid][d];
+      r = before + __popc(peers & lt);
     }
     __syncwarp();
+    if (ok && (peers & lt) == 0) sm.warp_hist[wid][d] = before + __popc(peers);
+    __syncwarp();
+    if (i & 1) rk[i >> 1] |= r << 16; else rk[i >> 1] = r;
   }
   __syncthreads();
 
-  // per digit: counts over warps -> warp offsets; tile count; look-back
+  // per digit: counts over warps -> warp offsets; publish the tile count
   const uint32_t d = tid;  // kSortThreads == kRadix
   uint32_t tile_count = 0;
 #pragma unroll
@@ -271,31 +276,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     tile_count += c;
   }
   volatile uint32_t* lb = lookback;
-  if (part == 0) {
-    lb[d] = kFlagPrefix | tile_count;
-  } else {
-    lb[(int64_t)part * kRadix + d] = kFlagAggregate | tile_count;
-  }
-  uint32_t excl = 0;
-  if (part > 0) {
-    int64_t j = (int64_t)part - 1;
-    int spins = 0;
-    while (true) {
-      const uint32_t w = lb[j * kRadix + d];
-      const uint32_t flag = w & ~kValueMask;
-      if (flag == 0) {
-        if (++spins > kSpinLimit) {
-          sm.timed_out = 1;
-          break;
-        }
-        continue;
-      }
-      excl += w & kValueMask;
-      if (flag == kFlagPrefix) break;
-      if (--j < 0) break;  // partition 0 always publishes a prefix
-    }
-    lb[(int64_t)part * kRadix + d] = kFlagPrefix | ((excl + tile_count) & kValueMask);
-  }
+  lb[(int64_t)part * kRadix + d] = (part == 0 ? kFlagPrefix : kFlagAggregate) | tile_count;
   // digit starts inside the tile (block exclusive scan over the 256 digits)
   {
     uint32_t inc = tile_count;
@@ -310,32 +291,83 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     uint32_t wpre = 0;
     for (int w = 0; w < wid; w++) wpre += wtot[w];
     sm.digit_start[d] = wpre + inc - tile_count;
-    sm.global_base[d] = hist_pass[d] + excl;
   }
+  __syncthreads();
+  const int n_here = (int)((count - base) < kSortTile ? (count - base) : kSortTile);
+  // keys -> tile-sorted positions in shared memory (frees the key registers
+  // before the look-back); remember the positions for the values
+#pragma unroll
+  for (int i = 0; i < kSortItems; i++) {
+    const bool ok = wbase + 32 * i < count;
+    const uint32_t r = (rk[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
+    uint32_t lp = 0xffffu;
+    if (ok) {
+      const uint32_t dd = (uint32_t)(key[i] >> shift) & (kRadix - 1);
+      lp = sm.digit_start[dd] + sm.warp_hist[wid][dd] + r;
+      sm.buf[lp] = key[i];
+      sm.dig[lp] = (uint8_t)dd;
+    }
+    if (i & 1) rk[i >> 1] = (rk[i >> 1] & 0xffffu) | (lp << 16); else rk[i >> 1] = (rk[i >> 1] & 0xffff0000u) | lp;
+  }
+  // decoupled look-back over the earlier partitions, kLookWindow statuses
+  // per round trip; a status that is not ready yet is re-read (bounded)
+  uint32_t excl = 0;
+  if (part > 0) {
+    int64_t j = (int64_t)part - 1;
+    int rounds = 0;
+    bool found = false;
+    while (!found) {
+      uint32_t w[kLookWindow];
+#pragma unroll
+      for (int t = 0; t < kLookWindow; t++)
+        w[t] = (j - t >= 0) ? (uint32_t)lb[(j - t) * kRadix + d] : (uint32_t)kFlagPrefix;
+      int used = 0;
+      bool stalled = false;
+#pragma unroll
+      for (int t = 0; t < kLookWindow; t++) {
+        if (found || stalled) continue;
+        const uint32_t flag = w[t] & ~kValueMask;
+        if (flag == 0) {
+          stalled = true;
+          continue;
+        }
+        excl += w[t] & kValueMask;
+        used++;
+        if (flag == kFlagPrefix) found = true;
+      }
+      j -= used;
+      if (!found && (++rounds > kSpinLimit || j < 0)) {
+        sm.timed_out = 1;
+        break;
+      }
+    }
+    lb[(int64_t)part * kRadix + d] = kFlagPrefix | ((excl + tile_count) & kValueMask);
+  }
+  sm.global_base[d] = hist_pass[d] + excl;
   __syncthreads();
   if (sm.timed_out) {
     if (tid == 0) atomicOr(status, kStatusTimeout);
     return;
   }
-  // local sorted position, through shared memory
-#pragma unroll
-  for (int i = 0; i < kSortItems; i++) {
-    if (rank[i] == 0xffffffffu) continue;
-    const uint32_t dd = (uint32_t)(key[i] >> shift) & (kRadix - 1);
-    const uint32_t lp = sm.digit_start[dd] + sm.warp_hist[wid][dd] + rank[i];
-    sm.keys[lp] = key[i];
-    sm.vals[lp] = val[i];
+  for (int lp = tid; lp < n_here; lp += kSortThreads) {
+    const uint32_t dd = sm.dig[lp];
+    const uint32_t dst = sm.global_base[dd] + (lp - sm.digit_start[dd]);
+    if (dst < (uint64_t)count) kout[dst] = sm.buf[lp];
   }
   __syncthreads();
-  const int n_here = (int)((count - base) < kSortTile ? (count - base) : kSortTile);
+  // values through the same buffer
+  uint32_t* vb = reinterpret_cast<uint32_t*>(sm.buf);
+#pragma unroll
+  for (int i = 0; i < kSortItems; i++) {
+    const int64_t p = wbase + 32 * i;
+    const uint32_t lp = (rk[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
+    if (p < count) vb[lp] = vin[p];
+  }
+  __syncthreads();
   for (int lp = tid; lp < n_here; lp += kSortThreads) {
-    const uint64_t k = sm.keys[lp];
-    const uint32_t dd = (uint32_t)(k >> shift) & (kRadix - 1);
+    const uint32_t dd = sm.dig[lp];
     const uint32_t dst = sm.global_base[dd] + (lp - sm.digit_start[dd]);
-    if (dst < (uint64_t)count) {
-      kout[dst] = k;
-      vout[dst] = sm.vals[lp];
-    }
+    if (dst < (uint64_t)count) vout[dst] = vb[lp];
   }
 }
 

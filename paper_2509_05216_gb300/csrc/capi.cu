@@ -44,7 +44,7 @@ struct gs_ctx {
   int sorted_in = 0;  // which ping-pong buffer holds the sorted list
   std::vector<ViewRec> views_h;
 
-  DevBuf views, rec0, rec1, rec2, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
+  DevBuf views, rec0, rec1, rec2, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial;
 
   // launch accounting and optional per-kernel event timing
@@ -212,7 +212,7 @@ void gs_destroy(gs_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->views, &c->rec0, &c->rec1, &c->rec2, &c->tiles, &c->block_sums, &c->block_offsets,
+  DevBuf* bufs[] = {&c->views, &c->rec0, &c->rec1, &c->rec2, &c->rec3, &c->tiles, &c->block_sums, &c->block_offsets,
                     &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->lookback,
                     &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial};
   for (DevBuf* b : bufs)
@@ -292,6 +292,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   GS_TRY(ensure(c, c->rec0, sizeof(float4) * B * stride));
   GS_TRY(ensure(c, c->rec1, sizeof(float4) * B * stride));
   GS_TRY(ensure(c, c->rec2, sizeof(float4) * B * stride));
+  GS_TRY(ensure(c, c->rec3, sizeof(int2) * B * stride));
   GS_TRY(ensure(c, c->tiles, sizeof(uint32_t) * B * stride));
   GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * nb));
   GS_CUDA(c, cudaMemcpyAsync(c->views.p, c->views_h.data(), sizeof(ViewRec) * B, cudaMemcpyHostToDevice,
@@ -305,6 +306,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   a.rec0 = P<float4>(c->rec0);
   a.rec1 = P<float4>(c->rec1);
   a.rec2 = P<float4>(c->rec2);
+  a.rec3 = P<int2>(c->rec3);
   a.tiles = P<uint32_t>(c->tiles);
   a.block_sums = P<uint32_t>(c->block_sums);
   {
@@ -357,6 +359,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   d.B = c->B;
   d.rec0 = P<float4>(c->rec0);
   d.rec2 = P<float4>(c->rec2);
+  d.rec3 = P<int2>(c->rec3);
   d.tiles = P<uint32_t>(c->tiles);
   d.block_offsets = P<uint32_t>(c->block_offsets);
   d.keys = P<uint64_t>(c->keys0);
@@ -476,12 +479,12 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   if (grads->n != c->n || grads->stride != c->stride || grads->sh_degree != c->deg)
     return fail(c, GS_EINVAL, "grads must match params in n, stride and sh_degree");
   set_device(c);
-  const size_t g2d_bytes = sizeof(float4) * 3 * c->B * c->stride;
+  const size_t g2d_bytes = sizeof(float) * 9 * c->B * c->stride;
   GS_TRY(ensure(c, c->g2d, g2d_bytes));
   GS_CUDA(c, cudaMemsetAsync(c->g2d.p, 0, g2d_bytes, c->stream));
   RasterArgs r = raster_args(c);
   r.dimage = dL_dimages;
-  r.g2d = P<float4>(c->g2d);
+  r.g2d = P<float>(c->g2d);
   {
     LaunchScope ls(c, "raster_bwd");
     launch_raster_bwd(r, c->bins, c->raster_bwd, c->stream);
@@ -493,14 +496,14 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   b.stride = c->stride;
   b.views = P<ViewRec>(c->views);
   b.B = c->B;
-  b.g2d = P<float4>(c->g2d);
+  b.g2d = P<float>(c->g2d);
   b.grads = grads->data;
   if (grads->stride > grads->n) {
     // padding columns are not written by the kernel; keep them zero
     GS_CUDA(c, cudaMemsetAsync(grads->data, 0, sizeof(float) * n_planes(c->deg) * grads->stride, c->stream));
   }
   {
-    LaunchScope ls(c, "project_bwd");
+    LaunchScope ls(c, "project_bwd", 2);
     launch_project_bwd(b, c->deg, c->stream);
   }
   GS_CHECK_LAUNCH(c);
@@ -574,12 +577,13 @@ gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
     case GS_BUF_REC0: if (!c->projected) return GS_ESTATE; *ptr = c->rec0.p; *count = bn; break;
     case GS_BUF_REC1: if (!c->projected) return GS_ESTATE; *ptr = c->rec1.p; *count = bn; break;
     case GS_BUF_REC2: if (!c->projected) return GS_ESTATE; *ptr = c->rec2.p; *count = bn; break;
+    case GS_BUF_REC3: if (!c->projected) return GS_ESTATE; *ptr = c->rec3.p; *count = bn; break;
     case GS_BUF_KEYS: if (!c->sorted) return GS_ESTATE; *ptr = c->sorted_in ? c->keys1.p : c->keys0.p; *count = c->instances; break;
     case GS_BUF_VALS: if (!c->sorted) return GS_ESTATE; *ptr = c->sorted_in ? c->vals1.p : c->vals0.p; *count = c->instances; break;
     case GS_BUF_RANGES: if (!c->sorted) return GS_ESTATE; *ptr = c->ranges.p; *count = c->bins; break;
     case GS_BUF_TFINAL: if (!c->rastered) return GS_ESTATE; *ptr = c->tfinal.p; *count = c->pixels; break;
     case GS_BUF_NLAST: if (!c->rastered) return GS_ESTATE; *ptr = c->nlast.p; *count = c->pixels; break;
-    case GS_BUF_G2D: if (!c->g2d.p) return GS_ESTATE; *ptr = c->g2d.p; *count = bn; break;
+    case GS_BUF_G2D: if (!c->g2d.p) return GS_ESTATE; *ptr = c->g2d.p; *count = 9 * bn; break;
     default: return fail(c, GS_EINVAL, "unknown buffer %d", which);
   }
   return GS_OK;

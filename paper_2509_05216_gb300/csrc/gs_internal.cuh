@@ -15,6 +15,7 @@ constexpr float kAlphaSkip = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;         // stop before T would fall below this
 constexpr float kDilation = 0.3f;       // added to the 2D covariance diagonal
 constexpr float kGuard = 1.3f;          // slope clamp, in half fields of view
+constexpr float kLog2e = 1.4426950408889634f;
 
 // Device status word bits.
 constexpr int kStatusCapacity = 1;

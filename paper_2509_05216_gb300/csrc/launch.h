@@ -16,6 +16,7 @@ struct ProjectArgs {
   float4* rec0;
   float4* rec1;
   float4* rec2;
+  int2* rec3;
   uint32_t* tiles;       // [B][stride]
   uint32_t* block_sums;  // [ceil(n / block)]
 };
@@ -25,7 +26,7 @@ struct ProjectBwdArgs {
   int64_t n, stride;
   const ViewRec* views;
   int B;
-  const float4* g2d;  // [B][stride][3] float4
+  const float* g2d;   // 9 planes of [B][stride]: dL/d(mu_x, mu_y, A, B, C, opacity, r, g, b)
   float* grads;       // [P][stride]
 };
 
@@ -35,6 +36,7 @@ struct DuplicateArgs {
   int B;
   const float4* rec0;
   const float4* rec2;
+  const int2* rec3;
   const uint32_t* tiles;
   const uint32_t* block_offsets;  // exclusive scan of the projection block sums
   uint64_t* keys;
@@ -56,7 +58,7 @@ struct RasterArgs {
   float* tfinal;        // [pixels]
   uint32_t* nlast;      // [pixels]
   const float* dimage;  // backward only
-  float4* g2d;          // backward only: [B][stride][3]
+  float* g2d;           // backward only: 9 planes of [B][stride]
 };
 
 int project_fwd_block();

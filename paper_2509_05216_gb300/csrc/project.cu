@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
     int radius = 0;
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
     float depth = 0.f, blue = 0.f;
+    float2 ex = make_float2(-3.0e38f, -3.0e38f);
     if (live) {
       depth = depth_key(V, mean[0], mean[1], mean[2]);
       if (depth > V.znear) {
@@ -199,9 +200,23 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
               for (int k = 0; k < K; k++) acc = fmaf(sh[3 * k + c], Y[k], acc);
               rgb[c] = fmaxf(acc, 0.f);
             }
-            r0 = make_float4(mx, my, st.c11 * idet, -st.c01 * idet);
-            r1 = make_float4(st.c00 * idet, opacity, rgb[0], rgb[1]);
+            // compositing form of the conic: p2 = cA dx^2 + cB dx dy + cC dy^2
+            // is the exponent in base 2 (power * log2 e); hx, hy bound the
+            // box around the ellipse where opacity * exp(power) >= 1/255
+            // (d^T conic d <= 2 ln(255 opacity), whose extents are
+            // sqrt(tau Sigma'_xx), sqrt(tau Sigma'_yy)), slightly widened.
+            const float A = st.c11 * idet, Bc = -st.c01 * idet, C = st.c00 * idet;
+            float hx = -3.0e38f, hy = -3.0e38f;  // never reaches 1/255
+            const float t255 = 255.f * opacity;
+            if (t255 > 1.f) {
+              const float tau = 2.f * logf(t255) * 1.001f + 1e-3f;
+              hx = sqrtf(tau * st.c00) * 1.001f + 0.01f;
+              hy = sqrtf(tau * st.c11) * 1.001f + 0.01f;
+            }
+            r0 = make_float4(mx, my, -0.5f * kLog2e * A, -kLog2e * Bc);
+            r1 = make_float4(-0.5f * kLog2e * C, opacity, rgb[0], rgb[1]);
             blue = rgb[2];
+            ex = make_float2(hx, hy);
           } else {
             radius = 0;
           }
@@ -209,7 +224,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
       }
       a.rec0[o] = r0;
       a.rec1[o] = r1;
-      a.rec2[o] = make_float4(blue, depth, __int_as_float(tiles ? radius : 0), __uint_as_float(tiles));
+      a.rec2[o] = make_float4(blue, ex.x, ex.y, depth);
+      a.rec3[o] = make_int2(tiles ? radius : 0, (int)tiles);
       a.tiles[o] = tiles;
     }
     total += tiles;
@@ -229,14 +245,77 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
   }
 }
 
-// Backward: dL/d(mu2D, conic, opacity, rgb) per (view, Gaussian) -> dL/dparams.
+// Backward, colour part: dL/drgb per (view, Gaussian) -> dL/dSH and the
+// part of dL/dmean that flows through the view direction.  Writes the SH
+// gradient planes and initialises the mean planes.
 template <int DEG>
-__global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
+__global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a) {
   constexpr int K = ShEval<DEG>::K;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.n) return;
   const float* P = a.params;
-  const int64_t S = a.stride;
+  const int64_t S = a.stride, plane = (int64_t)a.B * S;
+  float mean[3], sh[3 * K], gsh[3 * K];
+#pragma unroll
+  for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
+#pragma unroll
+  for (int i = 0; i < 3 * K; i++) {
+    sh[i] = __ldg(P + (11 + i) * S + g);
+    gsh[i] = 0.f;
+  }
+  float gm[3] = {0.f, 0.f, 0.f};
+  for (int v = 0; v < a.B; v++) {
+    const int64_t o = (int64_t)v * S + g;
+    const float grgb[3] = {__ldg(a.g2d + 6 * plane + o), __ldg(a.g2d + 7 * plane + o), __ldg(a.g2d + 8 * plane + o)};
+    if (grgb[0] == 0.f && grgb[1] == 0.f && grgb[2] == 0.f) continue;
+    const ViewRec& V = a.views[v];
+    // rgb_c = max(0, 0.5 + sum_k sh_kc Y_k(d)), d = (mu - campos) / |mu - campos|
+    float dx = mean[0] - V.campos[0], dy = mean[1] - V.campos[1], dz = mean[2] - V.campos[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv; dy *= inv; dz *= inv;
+    float Y[K];
+    ShEval<DEG>::basis(dx, dy, dz, Y);
+    float gc[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      float acc = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; k++) acc = fmaf(sh[3 * k + c], Y[k], acc);
+      gc[c] = acc < 0.f ? 0.f : grgb[c];
+    }
+    float wk[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        gsh[3 * k + c] = fmaf(gc[c], Y[k], gsh[3 * k + c]);
+        acc = fmaf(gc[c], sh[3 * k + c], acc);
+      }
+      wk[k] = acc;
+    }
+    float gdx, gdy, gdz;
+    ShEval<DEG>::grad(dx, dy, dz, wk, gdx, gdy, gdz);
+    const float dd = gdx * dx + gdy * dy + gdz * dz;
+    gm[0] += (gdx - dx * dd) * inv;
+    gm[1] += (gdy - dy * dd) * inv;
+    gm[2] += (gdz - dz * dd) * inv;
+  }
+  float* G = a.grads;
+#pragma unroll
+  for (int i = 0; i < 3; i++) G[i * S + g] = gm[i];
+#pragma unroll
+  for (int i = 0; i < 3 * K; i++) G[(11 + i) * S + g] = gsh[i];
+}
+
+// Backward, geometry part: dL/d(mu2D, conic, opacity) per (view, Gaussian)
+// -> dL/d(mean, log-scale, quaternion, opacity logit); adds to the mean
+// planes written by the colour part.
+__global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n) return;
+  const float* P = a.params;
+  const int64_t S = a.stride, plane = (int64_t)a.B * S;
   float mean[3], lsc[3], quat[4];
 #pragma unroll
   for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
@@ -248,23 +327,24 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
   const float opacity = 1.f / (1.f + expf(-op));
 
   float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gop = 0.f;
-  float gsh[3 * K];
+  // prefetch the first view's six gradient values
+  float cur[6], nxt[6];
 #pragma unroll
-  for (int i = 0; i < 3 * K; i++) gsh[i] = 0.f;
-
+  for (int q = 0; q < 6; q++) cur[q] = __ldg(a.g2d + q * plane + g);
   for (int v = 0; v < a.B; v++) {
-    const int64_t o = ((int64_t)v * S + g) * 3;
-    const float4 g0 = a.g2d[o], g1 = a.g2d[o + 1], g2 = a.g2d[o + 2];
-    if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
-        g1.z == 0.f && g1.w == 0.f && g2.x == 0.f)
-      continue;
+    if (v + 1 < a.B) {
+#pragma unroll
+      for (int q = 0; q < 6; q++) nxt[q] = __ldg(a.g2d + q * plane + (int64_t)(v + 1) * S + g);
+    }
+    const float gmx = cur[0], gmy = cur[1], gA = cur[2], gB = cur[3], gC = cur[4], gsig = cur[5];
+#pragma unroll
+    for (int q = 0; q < 6; q++) cur[q] = nxt[q];
+    if (gmx == 0.f && gmy == 0.f && gA == 0.f && gB == 0.f && gC == 0.f && gsig == 0.f) continue;
     const ViewRec& V = a.views[v];
     const float depth = depth_key(V, mean[0], mean[1], mean[2]);
     if (!(depth > V.znear)) continue;
     ProjState st;
     project_cov(V, mean, lsc, quat, depth, st);
-    const float gmx = g0.x, gmy = g0.y, gA = g0.z, gB = g0.w, gC = g1.x, gsig = g1.y;
-    const float grgb[3] = {g1.z, g1.w, g2.x};
 
     // conic = (c11, -c01, c00) / det  ->  Sigma'
     const float id = 1.f / st.det, id2 = id * id;
@@ -276,6 +356,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
     const float gh = 0.5f * gc01;
     // Sigma' = T Sigma T^T: dL/dSigma = T^T G T, dL/dT = 2 G T Sigma
     float GT[6];
+#pragma unroll
     for (int j = 0; j < 3; j++) {
       GT[j] = gc00 * st.T[j] + gh * st.T[3 + j];
       GT[3 + j] = gh * st.T[j] + gc11 * st.T[3 + j];
@@ -283,11 +364,15 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
     const float* Sg = st.Sig;
     const float Sfull[9] = {Sg[0], Sg[1], Sg[2], Sg[1], Sg[3], Sg[4], Sg[2], Sg[4], Sg[5]};
     float gT[6];
+#pragma unroll
     for (int i = 0; i < 2; i++)
+#pragma unroll
       for (int b = 0; b < 3; b++)
         gT[3 * i + b] = 2.f * (GT[3 * i] * Sfull[b] + GT[3 * i + 1] * Sfull[3 + b] + GT[3 * i + 2] * Sfull[6 + b]);
     float gS[9];
+#pragma unroll
     for (int i = 0; i < 3; i++)
+#pragma unroll
       for (int j = 0; j < 3; j++) gS[3 * i + j] = st.T[i] * GT[j] + st.T[3 + i] * GT[3 + j];
     // T = J W
     const float* R = V.R;
@@ -312,21 +397,20 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
     gty += gmy * V.fy * itz;
     gtz -= (gmx * V.fx * st.tx + gmy * V.fy * st.ty) * itz2;
     // t = W mu + tau
+#pragma unroll
     for (int j = 0; j < 3; j++) gm[j] += R[j] * gtx + R[3 + j] * gty + R[6 + j] * gtz;
-    // Sigma = M M^T, M = Rq diag(s): dL/dM = 2 gS M
-    float gM[9];
-    for (int i = 0; i < 3; i++)
-      for (int j = 0; j < 3; j++) {
-        float acc = 0.f;
-        for (int k = 0; k < 3; k++) acc += (gS[3 * i + k] + gS[3 * k + i]) * st.Rq[3 * k + j] * st.s[j];
-        gM[3 * i + j] = acc;
-      }
+    // Sigma = M M^T, M = Rq diag(s): dL/dM = (gS + gS^T) M
     float gR[9];
+#pragma unroll
     for (int j = 0; j < 3; j++) {
       float gsj = 0.f;
+#pragma unroll
       for (int i = 0; i < 3; i++) {
-        gsj += gM[3 * i + j] * st.Rq[3 * i + j];
-        gR[3 * i + j] = gM[3 * i + j] * st.s[j];
+        float gMij = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++) gMij += (gS[3 * i + k] + gS[3 * k + i]) * st.Rq[3 * k + j] * st.s[j];
+        gsj += gMij * st.Rq[3 * i + j];
+        gR[3 * i + j] = gMij * st.s[j];
       }
       gls[j] += gsj * st.s[j];
     }
@@ -341,46 +425,18 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
     gqn[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] +
                     y * gR[7]);
     const float dq = gqn[0] * st.qn[0] + gqn[1] * st.qn[1] + gqn[2] * st.qn[2] + gqn[3] * st.qn[3];
+#pragma unroll
     for (int i = 0; i < 4; i++) gq[i] += (gqn[i] - st.qn[i] * dq) * st.qinv;
-    // opacity
     gop += gsig * opacity * (1.f - opacity);
-    // colour: rgb_c = max(0, 0.5 + sum_k sh_kc Y_k(d)), d = (mu - campos) / |mu - campos|
-    float dx = mean[0] - V.campos[0], dy = mean[1] - V.campos[1], dz = mean[2] - V.campos[2];
-    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-    dx *= inv; dy *= inv; dz *= inv;
-    float Y[K];
-    ShEval<DEG>::basis(dx, dy, dz, Y);
-    float gc[3];
-    for (int c = 0; c < 3; c++) {
-      float acc = 0.5f;
-      for (int k = 0; k < K; k++) acc = fmaf(__ldg(P + (11 + 3 * k + c) * S + g), Y[k], acc);
-      gc[c] = acc < 0.f ? 0.f : grgb[c];
-    }
-    float wk[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      float acc = 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        gsh[3 * k + c] += gc[c] * Y[k];
-        acc += gc[c] * __ldg(P + (11 + 3 * k + c) * S + g);
-      }
-      wk[k] = acc;
-    }
-    float gdx, gdy, gdz;
-    ShEval<DEG>::grad(dx, dy, dz, wk, gdx, gdy, gdz);
-    const float dd = gdx * dx + gdy * dy + gdz * dz;
-    gm[0] += (gdx - dx * dd) * inv;
-    gm[1] += (gdy - dy * dd) * inv;
-    gm[2] += (gdz - dz * dd) * inv;
   }
   float* G = a.grads;
-  for (int i = 0; i < 3; i++) G[i * S + g] = gm[i];
+#pragma unroll
+  for (int i = 0; i < 3; i++) G[i * S + g] += gm[i];
+#pragma unroll
   for (int i = 0; i < 3; i++) G[(3 + i) * S + g] = gls[i];
+#pragma unroll
   for (int i = 0; i < 4; i++) G[(6 + i) * S + g] = gq[i];
   G[10 * S + g] = gop;
-#pragma unroll
-  for (int i = 0; i < 3 * K; i++) G[(11 + i) * S + g] = gsh[i];
 }
 
 void launch_project_fwd(const ProjectArgs& a, int deg, cudaStream_t s) {
@@ -400,11 +456,12 @@ void launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t s) {
   const int threads = 128;
   const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
   switch (deg) {
-    case 0: project_bwd_kernel<0><<<blocks, threads, 0, s>>>(a); break;
-    case 1: project_bwd_kernel<1><<<blocks, threads, 0, s>>>(a); break;
-    case 2: project_bwd_kernel<2><<<blocks, threads, 0, s>>>(a); break;
-    default: project_bwd_kernel<3><<<blocks, threads, 0, s>>>(a); break;
+    case 0: project_bwd_color_kernel<0><<<blocks, threads, 0, s>>>(a); break;
+    case 1: project_bwd_color_kernel<1><<<blocks, threads, 0, s>>>(a); break;
+    case 2: project_bwd_color_kernel<2><<<blocks, threads, 0, s>>>(a); break;
+    default: project_bwd_color_kernel<3><<<blocks, threads, 0, s>>>(a); break;
   }
+  project_bwd_geom_kernel<<<blocks, threads, 0, s>>>(a);
 }
 
 }  // namespace gs

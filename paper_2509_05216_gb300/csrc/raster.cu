@@ -8,20 +8,18 @@
 // each pixel's last contributor towards the front, recovering T by division
 // and keeping the colour composited behind.
 //
-// Two launch shapes, selected per context (GS_OPT_RASTER_*):
-//  * block per tile (PPT = 1, 2, 4 pixels per thread): 256 / PPT threads;
-//    warp w covers an 8-pixel-wide band of 4 * PPT rows of the tile;
-//  * warp per tile (PPT = 8): lane l owns column l & 15 and 8 rows.
-// A staged Gaussian carries the half-extents of the ellipse on which
-// alpha = 1/255 (slightly widened); a warp whose pixel rectangle misses that
-// box skips the Gaussian with one uniform branch.  This removes only pairs
-// that the per-pixel test would skip, so the result is unchanged.
+// Launch shapes, selected per context (GS_OPT_RASTER_FWD / _BWD): PPT = 1, 2
+// or 4 pixels per thread with 8, 4 or 2 warps per tile (each warp an 8-pixel-
+// wide band), or PPT = 8 with one warp per 16x16 tile.  Every warp walks its
+// tile's list independently (no block barriers).  A record carries the
+// half-extents of the box around the ellipse where alpha >= 1/255 (slightly
+// widened); a warp whose pixel rectangle misses that box skips the Gaussian
+// with one uniform branch.  This removes only pairs that the per-pixel test
+// would skip, so the result is unchanged.
 #include "gs_internal.cuh"
 #include "launch.h"
 
 namespace gs {
-
-constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ int view_of_bin(const ViewRec* views, int B, int bin) {
   int lo = 0, hi = B - 1;
@@ -32,30 +30,16 @@ __device__ __forceinline__ int view_of_bin(const ViewRec* views, int B, int bin)
   return lo;
 }
 
-// Staged Gaussian (shared memory, three float4):
-//   s0 = (mu_x, mu_y, cA, cB), s1 = (cC, opacity, r, g), s2 = (b, hx, hy, -)
-// with p2 = cA dx^2 + cB dx dy + cC dy^2 = power * log2(e), dx = mu_x - x.
+// Staged Gaussian (shared memory, three float4), as written by the projection:
+//   s0 = (mu_x, mu_y, cA, cB), s1 = (cC, opacity, r, g), s2 = (b, hx, hy, depth)
+// with p2 = cA dx^2 + cB dx dy + cC dy^2 = power * log2(e), dx = mu_x - x,
+// and (hx, hy) the half-extents of the box around the alpha >= 1/255 ellipse.
 __device__ __forceinline__ void stage_one(const RasterArgs& a, int v, uint32_t g, float4& s0, float4& s1,
                                           float4& s2) {
   const int64_t o = (int64_t)v * a.stride + g;
-  const float4 r0 = a.rec0[o], r1 = a.rec1[o];
-  const float blue = a.rec2[o].x;
-  const float A = r0.z, B = r0.w, C = r1.x, op = r1.y;
-  // alpha >= 1/255  <=>  d^T K d <= tau = 2 ln(255 opacity); the ellipse's
-  // bounding box has half-extents sqrt(tau * (K^-1)_xx), sqrt(tau * (K^-1)_yy).
-  const float detK = A * C - B * B;
-  float hx = 3.0e38f, hy = 3.0e38f;
-  const float t = 255.f * op;
-  if (t <= 1.f) {
-    hx = hy = -3.0e38f;  // never reaches 1/255: no box is hit
-  } else if (detK > 0.f) {
-    const float tau = 2.f * __logf(t) * 1.001f + 1e-3f;
-    hx = sqrtf(tau * C / detK) * 1.001f + 0.01f;
-    hy = sqrtf(tau * A / detK) * 1.001f + 0.01f;
-  }
-  s0 = make_float4(r0.x, r0.y, -0.5f * kLog2e * A, -kLog2e * B);
-  s1 = make_float4(-0.5f * kLog2e * C, op, r1.z, r1.w);
-  s2 = make_float4(blue, hx, hy, 0.f);
+  s0 = a.rec0[o];
+  s1 = a.rec1[o];
+  s2 = a.rec2[o];
 }
 
 // Does the splat's alpha >= 1/255 box meet the pixel rectangle [x0,x1]x[y0,y1]?
@@ -100,15 +84,48 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
 }
 
 // Apply the warp's reduced gradient of one Gaussian: lanes 2q (q < 9) add
-// the total of value q.  Accumulators hold d/d(mu_x, mu_y) of p2 and raw
-// dx^2, dx dy, dy^2 sums; undo those scalings here.
-__device__ __forceinline__ void push_grad(float4* g2d, int64_t rec, float (&acc)[16], int lane) {
+// the total of value q to plane q.  Accumulators hold d/d(mu_x, mu_y) of p2
+// and raw dx^2, dx dy, dy^2 sums; undo those scalings here.
+__device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec, float (&acc)[16], int lane) {
   const float tot = warp_reduce_scatter16(acc, lane);
   const int q = lane >> 1;
   if ((lane & 1) == 0 && q < 9) {
     const float scale = q < 2 ? (1.f / kLog2e) : (q == 2 || q == 4) ? -0.5f : (q == 3 ? -1.f : 1.f);
-    atomicAdd(reinterpret_cast<float*>(g2d + rec * 3) + q, tot * scale);
+    atomicAdd(g2d + q * plane + rec, tot * scale);
   }
+}
+
+// Batched transpose-reduction of backward gradients.  A warp parks the
+// per-lane partial sums of up to kPend Gaussians in shared memory
+// (red[slot][value][lane], row pitch 33 so every access is conflict-free);
+// a flush has lane l sum rows l, l + 32, l + 64 (row = slot * 9 + value) over
+// the 32 lanes and add the total to its gradient plane: 18 shared-memory
+// operations per Gaussian instead of a 16-shuffle butterfly.
+constexpr int kPend = 8;
+constexpr int kRedPitch = 33;
+
+__device__ __forceinline__ void park_grad(float* red, int slot, const float (&acc)[16], int lane) {
+#pragma unroll
+  for (int q = 0; q < 9; q++) red[(slot * 9 + q) * kRedPitch + lane] = acc[q];
+}
+
+__device__ __forceinline__ void flush_grads(float* red, const uint32_t* pend_g, int npend, float* g2d, int64_t plane,
+                                            int64_t vbase, int lane) {
+  __syncwarp();
+#pragma unroll
+  for (int r0 = 0; r0 < kPend * 9; r0 += 32) {
+    const int row = r0 + lane;
+    if (row < npend * 9) {
+      const float* src = red + row * kRedPitch;
+      float t = 0.f;
+#pragma unroll 8
+      for (int l = 0; l < 32; l++) t += src[l];
+      const int slot = row / 9, q = row - slot * 9;
+      const float scale = q < 2 ? (1.f / kLog2e) : (q == 2 || q == 4) ? -0.5f : (q == 3 ? -1.f : 1.f);
+      atomicAdd(g2d + q * plane + vbase + pend_g[slot], t * scale);
+    }
+  }
+  __syncwarp();
 }
 
 // One backward (pixel, Gaussian) pair, branch-free so that the pixels of a
@@ -167,35 +184,69 @@ __device__ __forceinline__ void fwd_pair(const float4& q1, float blue, float a0,
   last = acc ? idx : last;
 }
 
-// ---------------------------------------------------------------- block per tile
-
+// ---------------------------------------------------------------- launch shapes
+//
+// PPT = pixels per thread.  A block holds TPB tiles; a warp owns a WR x HR
+// pixel rectangle of its tile (lane l: column l % CW, rows (l / CW) * PPT + k)
+// and walks the tile's list on its own: it stages 32 records at a time into
+// its own shared slots and never waits for the other warps of the block.
 template <int PPT>
-struct BlockShape {
-  static constexpr int NT = 256 / PPT;    // threads
-  static constexpr int NW = NT / 32;      // warps
-  static constexpr int BAND = 4 * PPT;    // rows per warp
-  // pixel of (warp, lane, k) inside the tile
-  __device__ static int col(int w, int lane) { return (w & 1) * 8 + (lane & 7); }
-  __device__ static int row(int w, int lane) { return (w >> 1) * BAND + (lane >> 3) * PPT; }
+struct Shape;
+template <>
+struct Shape<1> {  // 8 warps per tile, 8 x 4 pixels each
+  static constexpr int NW = 8, TPB = 1, CW = 8;
+};
+template <>
+struct Shape<2> {  // 4 warps per tile, 8 x 8 pixels each
+  static constexpr int NW = 4, TPB = 1, CW = 8;
+};
+template <>
+struct Shape<4> {  // 2 warps per tile, 8 x 16 pixels each
+  static constexpr int NW = 2, TPB = 1, CW = 8;
+};
+template <>
+struct Shape<8> {  // 1 warp per tile, 4 tiles per block
+  static constexpr int NW = 1, TPB = 4, CW = 16;
 };
 
 template <int PPT>
-__global__ void __launch_bounds__(256 / PPT) raster_fwd_kernel(RasterArgs a) {
-  using S = BlockShape<PPT>;
-  constexpr int NT = S::NT;
-  __shared__ float4 s0[NT], s1[NT], s2[NT];
-  const int bin = blockIdx.x;
+struct Geo {
+  static constexpr int NW = Shape<PPT>::NW, TPB = Shape<PPT>::TPB, CW = Shape<PPT>::CW;
+  static constexpr int THREADS = 32 * NW * TPB;
+  static constexpr int RW = CW, RH = (32 / CW) * PPT;  // warp rectangle
+  int64_t bin;
+  int v, px, py0;
+  float wx0, wx1, wy0, wy1;
+  __device__ bool init(const RasterArgs& a, int64_t bins, int warp, int lane) {
+    const int tile_in_block = warp / NW, sub = warp % NW;
+    bin = (int64_t)blockIdx.x * TPB + tile_in_block;
+    if (bin >= bins) return false;
+    v = view_of_bin(a.views, a.B, (int)bin);
+    const ViewRec& V = a.views[v];
+    const int tile = (int)bin - V.tile_offset;
+    const int tx = tile % V.gw, ty = tile / V.gw;
+    const int ox = (sub % (kTile / RW)) * RW, oy = (sub / (kTile / RW)) * RH;
+    px = tx * kTile + ox + (lane % CW);
+    py0 = ty * kTile + oy + (lane / CW) * PPT;
+    wx0 = (float)(tx * kTile + ox);
+    wx1 = wx0 + (float)(RW - 1);
+    wy0 = (float)(ty * kTile + oy);
+    wy1 = wy0 + (float)(RH - 1);
+    return true;
+  }
+};
+
+template <int PPT>
+__global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArgs a, int64_t bins) {
+  using G = Geo<PPT>;
+  constexpr int NWB = G::NW * G::TPB;  // warps per block
+  __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int v = view_of_bin(a.views, a.B, bin);
+  G geo;
+  if (!geo.init(a, bins, w, lane)) return;
+  const int v = geo.v, px = geo.px, py0 = geo.py0;
   const ViewRec& V = a.views[v];
-  const int tile = bin - V.tile_offset;
-  const int tx = tile % V.gw, ty = tile / V.gw;
-  const int px = tx * kTile + S::col(w, lane);
-  const int py0 = ty * kTile + S::row(w, lane);
-  // the warp's pixel rectangle
-  const float wx0 = (float)(tx * kTile + (w & 1) * 8), wx1 = wx0 + 7.f;
-  const float wy0 = (float)(ty * kTile + (w >> 1) * S::BAND), wy1 = wy0 + (float)(S::BAND - 1);
-  const uint2 rg = a.ranges[bin];
+  const uint2 rg = a.ranges[geo.bin];
   const int n = (int)(rg.y - rg.x);
 
   float T[PPT], C[PPT][3];
@@ -210,18 +261,18 @@ __global__ void __launch_bounds__(256 / PPT) raster_fwd_kernel(RasterArgs a) {
   }
   const uint32_t all_done = (1u << PPT) - 1u;
   const float fpx = (float)px, fpy = (float)py0;
-  for (int b0 = 0; b0 < n; b0 += NT) {
-    if (__syncthreads_count(done == all_done) == NT) break;
-    const int i = b0 + (int)threadIdx.x;
-    if (i < n) stage_one(a, v, a.vals[rg.x + i], s0[threadIdx.x], s1[threadIdx.x], s2[threadIdx.x]);
-    __syncthreads();
-    const int cnt = min(NT, n - b0);
-    bool warp_done = __all_sync(0xffffffffu, done == all_done);
-    for (int j = 0; j < cnt && !warp_done; j++) {
-      const float4 q0 = s0[j];
-      const float4 q2 = s2[j];
-      if (!box_hits(q0, q2, wx0, wx1, wy0, wy1)) continue;
-      const float4 q1 = s1[j];
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    if (__all_sync(0xffffffffu, done == all_done)) break;
+    const int i = b0 + lane;
+    __syncwarp();
+    if (i < n) stage_one(a, v, a.vals[rg.x + i], s0[w][lane], s1[w][lane], s2[w][lane]);
+    __syncwarp();
+    const int cnt = min(32, n - b0);
+    for (int j = 0; j < cnt; j++) {
+      const float4 q0 = s0[w][j];
+      const float4 q2 = s2[w][j];
+      if (!box_hits(q0, q2, geo.wx0, geo.wx1, geo.wy0, geo.wy1)) continue;
+      const float4 q1 = s1[w][j];
       const float dx = __fsub_rn(q0.x, fpx);
       const float a0 = __fmul_rn(q0.z, __fmul_rn(dx, dx));
       const float a1 = __fmul_rn(q0.w, dx);
@@ -229,9 +280,7 @@ __global__ void __launch_bounds__(256 / PPT) raster_fwd_kernel(RasterArgs a) {
       for (int k = 0; k < PPT; k++)
         fwd_pair(q1, q2.x, a0, a1, __fsub_rn(q0.y, fpy + (float)k), 1u << k, (uint32_t)(b0 + j + 1), done, T[k],
                  C[k], last[k]);
-      warp_done = __all_sync(0xffffffffu, done == all_done);
     }
-    __syncthreads();
   }
   const int64_t plane = (int64_t)V.W * V.H;
   float* img = a.image + 3 * V.pix_offset;
@@ -249,27 +298,27 @@ __global__ void __launch_bounds__(256 / PPT) raster_fwd_kernel(RasterArgs a) {
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterArgs a) {
-  using S = BlockShape<PPT>;
-  constexpr int NT = S::NT;
-  __shared__ float4 s0[NT], s1[NT], s2[NT];
-  __shared__ uint32_t sg[NT];
-  __shared__ uint32_t s_maxlast;
-  const int bin = blockIdx.x;
+__global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArgs a, int64_t bins) {
+  using G = Geo<PPT>;
+  constexpr int NWB = G::NW * G::TPB;
+  __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
+  __shared__ uint32_t sg[NWB][32];
+  __shared__ float red_s[NWB][kPend * 9 * kRedPitch];
+  __shared__ uint32_t pend_s[NWB][kPend];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int v = view_of_bin(a.views, a.B, bin);
+  G geo;
+  if (!geo.init(a, bins, w, lane)) return;
+  const int v = geo.v, px = geo.px, py0 = geo.py0;
   const ViewRec& V = a.views[v];
-  const int tile = bin - V.tile_offset;
-  const int tx = tile % V.gw, ty = tile / V.gw;
-  const int px = tx * kTile + S::col(w, lane);
-  const int py0 = ty * kTile + S::row(w, lane);
-  const float wx0 = (float)(tx * kTile + (w & 1) * 8), wx1 = wx0 + 7.f;
-  const float wy0 = (float)(ty * kTile + (w >> 1) * S::BAND), wy1 = wy0 + (float)(S::BAND - 1);
-  const uint2 rg = a.ranges[bin];
-  if (threadIdx.x == 0) s_maxlast = 0;
-
+  const uint2 rg = a.ranges[geo.bin];
   const int64_t plane = (int64_t)V.W * V.H;
   const float* dimg = a.dimage + 3 * V.pix_offset;
+  float* red = red_s[w];
+  uint32_t* pend = pend_s[w];
+  int npend = 0;
+
+  // per pixel: T (running, from T_final backwards), dL/dC, sum_c dC_c S_c
+  // (S = colour behind), T_final * sum_c dC_c bg_c, and n_last
   float T[PPT], dC[PPT][3], dCS[PPT], bgd[PPT];
   uint32_t nl[PPT];
   uint32_t mymax = 0;
@@ -286,27 +335,25 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterArgs a) {
     bgd[k] = T[k] * (dC[k][0] * V.bg[0] + dC[k][1] * V.bg[1] + dC[k][2] * V.bg[2]);
     mymax = max(mymax, nl[k]);
   }
-  const uint32_t warp_max = __reduce_max_sync(0xffffffffu, mymax);
-  __syncthreads();
-  if (lane == 0) atomicMax(&s_maxlast, warp_max);
-  __syncthreads();
-  const int total = (int)s_maxlast;
+  // this warp only walks the entries before its pixels' last contributors
+  const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
   const float fpx = (float)px, fpy = (float)py0;
-  for (int bend = total; bend > 0; bend -= NT) {
-    const int bstart = max(0, bend - NT);
-    const int i = bstart + (int)threadIdx.x;
+  const int64_t gplane = (int64_t)a.B * a.stride;
+  for (int bend = total; bend > 0; bend -= 32) {
+    const int bstart = max(0, bend - 32);
+    const int i = bstart + lane;
+    __syncwarp();
     if (i < bend) {
       const uint32_t g = a.vals[rg.x + i];
-      stage_one(a, v, g, s0[threadIdx.x], s1[threadIdx.x], s2[threadIdx.x]);
-      sg[threadIdx.x] = g;
+      stage_one(a, v, g, s0[w][lane], s1[w][lane], s2[w][lane]);
+      sg[w][lane] = g;
     }
-    __syncthreads();
-    const int jmax = min(bend - bstart, (int)warp_max - bstart);  // entries this warp needs
-    for (int j = jmax - 1; j >= 0; j--) {
-      const float4 q0 = s0[j];
-      const float4 q2 = s2[j];
-      if (!box_hits(q0, q2, wx0, wx1, wy0, wy1)) continue;
-      const float4 q1 = s1[j];
+    __syncwarp();
+    for (int j = bend - bstart - 1; j >= 0; j--) {
+      const float4 q0 = s0[w][j];
+      const float4 q2 = s2[w][j];
+      if (!box_hits(q0, q2, geo.wx0, geo.wx1, geo.wy0, geo.wy1)) continue;
+      const float4 q1 = s1[w][j];
       const uint32_t idx = (uint32_t)(bstart + j);
       const float rgb[3] = {q1.z, q1.w, q2.x};
       const float dx = __fsub_rn(q0.x, fpx);
@@ -323,168 +370,44 @@ __global__ void __launch_bounds__(256 / PPT) raster_bwd_kernel(RasterArgs a) {
       for (int k = 0; k < PPT; k++)
         any |= bwd_pair(idx < nl[k], q0, q1, rgb, a0, a1, __fsub_rn(q0.y, fpy + (float)k), dx, dx2, cA2dx, cBdx, T[k],
                         dCS[k], dC[k], bgd[k], acc);
-      if (__any_sync(0xffffffffu, any)) push_grad(a.g2d, (int64_t)v * a.stride + sg[j], acc, lane);
+      if (__any_sync(0xffffffffu, any)) {
+        park_grad(red, npend, acc, lane);
+        if (lane == 0) pend[npend] = sg[w][j];
+        if (++npend == kPend) {
+          flush_grads(red, pend, npend, a.g2d, gplane, (int64_t)v * a.stride, lane);
+          npend = 0;
+        }
+      }
     }
-    __syncthreads();
   }
+  if (npend) flush_grads(red, pend, npend, a.g2d, gplane, (int64_t)v * a.stride, lane);
 }
 
-// ---------------------------------------------------------------- warp per tile
-
-constexpr int kRows = 8;
-
-template <int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) raster_fwd_warp_kernel(RasterArgs a, int64_t bins) {
-  __shared__ float4 s0[WARPS][32], s1[WARPS][32], s2[WARPS][32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t bin = (int64_t)blockIdx.x * WARPS + w;
-  if (bin >= bins) return;
-  const int v = view_of_bin(a.views, a.B, (int)bin);
-  const ViewRec& V = a.views[v];
-  const int tile = (int)bin - V.tile_offset;
-  const int tx = tile % V.gw, ty = tile / V.gw;
-  const int px = tx * kTile + (lane & 15);
-  const int py0 = ty * kTile + (lane >> 4) * kRows;
-  const float wx0 = (float)(tx * kTile), wx1 = wx0 + 15.f, wy0 = (float)(ty * kTile), wy1 = wy0 + 15.f;
-  const uint2 rg = a.ranges[bin];
-  const int n = (int)(rg.y - rg.x);
-
-  float T[kRows], C[kRows][3];
-  uint32_t last[kRows];
-  uint32_t done = 0;
-#pragma unroll
-  for (int k = 0; k < kRows; k++) {
-    T[k] = 1.f;
-    C[k][0] = C[k][1] = C[k][2] = 0.f;
-    last[k] = 0;
-    if (!(px < V.W && py0 + k < V.H)) done |= 1u << k;
-  }
-  const float fpx = (float)px, fpy = (float)py0;
-  for (int b0 = 0; b0 < n; b0 += 32) {
-    if (__all_sync(0xffffffffu, done == (1u << kRows) - 1)) break;
-    const int i = b0 + lane;
-    __syncwarp();
-    if (i < n) stage_one(a, v, a.vals[rg.x + i], s0[w][lane], s1[w][lane], s2[w][lane]);
-    __syncwarp();
-    const int cnt = min(32, n - b0);
-    for (int j = 0; j < cnt; j++) {
-      const float4 q0 = s0[w][j];
-      const float4 q2 = s2[w][j];
-      if (!box_hits(q0, q2, wx0, wx1, wy0, wy1)) continue;
-      const float4 q1 = s1[w][j];
-      const float dx = __fsub_rn(q0.x, fpx);
-      const float a0 = __fmul_rn(q0.z, __fmul_rn(dx, dx));
-      const float a1 = __fmul_rn(q0.w, dx);
-#pragma unroll
-      for (int k = 0; k < kRows; k++)
-        fwd_pair(q1, q2.x, a0, a1, __fsub_rn(q0.y, fpy + (float)k), 1u << k, (uint32_t)(b0 + j + 1), done, T[k],
-                 C[k], last[k]);
-    }
-  }
-  const int64_t plane = (int64_t)V.W * V.H;
-  float* img = a.image + 3 * V.pix_offset;
-#pragma unroll
-  for (int k = 0; k < kRows; k++) {
-    const int py = py0 + k;
-    if (px >= V.W || py >= V.H) continue;
-    const int64_t p = (int64_t)py * V.W + px;
-    img[p] = fmaf(T[k], V.bg[0], C[k][0]);
-    img[plane + p] = fmaf(T[k], V.bg[1], C[k][1]);
-    img[2 * plane + p] = fmaf(T[k], V.bg[2], C[k][2]);
-    a.tfinal[V.pix_offset + p] = T[k];
-    a.nlast[V.pix_offset + p] = last[k];
-  }
-}
-
-template <int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) raster_bwd_warp_kernel(RasterArgs a, int64_t bins) {
-  __shared__ float4 s0[WARPS][32], s1[WARPS][32], s2[WARPS][32];
-  __shared__ uint32_t sg[WARPS][32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t bin = (int64_t)blockIdx.x * WARPS + w;
-  if (bin >= bins) return;
-  const int v = view_of_bin(a.views, a.B, (int)bin);
-  const ViewRec& V = a.views[v];
-  const int tile = (int)bin - V.tile_offset;
-  const int tx = tile % V.gw, ty = tile / V.gw;
-  const int px = tx * kTile + (lane & 15);
-  const int py0 = ty * kTile + (lane >> 4) * kRows;
-  const float wx0 = (float)(tx * kTile), wx1 = wx0 + 15.f, wy0 = (float)(ty * kTile), wy1 = wy0 + 15.f;
-  const uint2 rg = a.ranges[bin];
-  const int64_t plane = (int64_t)V.W * V.H;
-  const float* dimg = a.dimage + 3 * V.pix_offset;
-
-  float T[kRows], dC[kRows][3], dCS[kRows], bgd[kRows];
-  uint32_t nl[kRows];
-  uint32_t mymax = 0;
-#pragma unroll
-  for (int k = 0; k < kRows; k++) {
-    const int py = py0 + k;
-    const bool in = px < V.W && py < V.H;
-    const int64_t p = (int64_t)py * V.W + px;
-    T[k] = in ? a.tfinal[V.pix_offset + p] : 1.f;
-    nl[k] = in ? a.nlast[V.pix_offset + p] : 0u;
-#pragma unroll
-    for (int c = 0; c < 3; c++) dC[k][c] = in ? dimg[c * plane + p] : 0.f;
-    dCS[k] = 0.f;
-    bgd[k] = T[k] * (dC[k][0] * V.bg[0] + dC[k][1] * V.bg[1] + dC[k][2] * V.bg[2]);
-    mymax = max(mymax, nl[k]);
-  }
-  const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
-  const float fpx = (float)px, fpy = (float)py0;
-  for (int bend = total; bend > 0; bend -= 32) {
-    const int bstart = max(0, bend - 32);
-    const int i = bstart + lane;
-    __syncwarp();
-    if (i < bend) {
-      const uint32_t g = a.vals[rg.x + i];
-      stage_one(a, v, g, s0[w][lane], s1[w][lane], s2[w][lane]);
-      sg[w][lane] = g;
-    }
-    __syncwarp();
-    for (int j = bend - bstart - 1; j >= 0; j--) {
-      const float4 q0 = s0[w][j];
-      const float4 q2 = s2[w][j];
-      if (!box_hits(q0, q2, wx0, wx1, wy0, wy1)) continue;
-      const float4 q1 = s1[w][j];
-      const uint32_t idx = (uint32_t)(bstart + j);
-      const float rgb[3] = {q1.z, q1.w, q2.x};
-      const float dx = __fsub_rn(q0.x, fpx);
-      const float dx2 = __fmul_rn(dx, dx);
-      const float a0 = __fmul_rn(q0.z, dx2);
-      const float a1 = __fmul_rn(q0.w, dx);
-      const float cA2dx = 2.f * q0.z * dx;
-      const float cBdx = q0.w * dx;
-      float acc[16];
-#pragma unroll
-      for (int q = 0; q < 16; q++) acc[q] = 0.f;
-      bool any = false;
-#pragma unroll
-      for (int k = 0; k < kRows; k++)
-        any |= bwd_pair(idx < nl[k], q0, q1, rgb, a0, a1, __fsub_rn(q0.y, fpy + (float)k), dx, dx2, cA2dx, cBdx, T[k],
-                        dCS[k], dC[k], bgd[k], acc);
-      if (__any_sync(0xffffffffu, any)) push_grad(a.g2d, (int64_t)v * a.stride + sg[w][j], acc, lane);
-    }
-  }
+template <int PPT>
+void launch_shape(bool fwd, const RasterArgs& a, int64_t bins, cudaStream_t s) {
+  using G = Geo<PPT>;
+  const unsigned blocks = (unsigned)((bins + G::TPB - 1) / G::TPB);
+  if (fwd) raster_fwd_kernel<PPT><<<blocks, G::THREADS, 0, s>>>(a, bins);
+  else raster_bwd_kernel<PPT><<<blocks, G::THREADS, 0, s>>>(a, bins);
 }
 
 void launch_raster_fwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s) {
   if (bins == 0) return;
   switch (ppt) {
-    case 8: raster_fwd_warp_kernel<4><<<(unsigned)((bins + 3) / 4), 128, 0, s>>>(a, bins); break;
-    case 1: raster_fwd_kernel<1><<<(unsigned)bins, 256, 0, s>>>(a); break;
-    case 4: raster_fwd_kernel<4><<<(unsigned)bins, 64, 0, s>>>(a); break;
-    default: raster_fwd_kernel<2><<<(unsigned)bins, 128, 0, s>>>(a); break;
+    case 1: launch_shape<1>(true, a, bins, s); break;
+    case 4: launch_shape<4>(true, a, bins, s); break;
+    case 8: launch_shape<8>(true, a, bins, s); break;
+    default: launch_shape<2>(true, a, bins, s); break;
   }
 }
 
 void launch_raster_bwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s) {
   if (bins == 0) return;
   switch (ppt) {
-    case 8: raster_bwd_warp_kernel<4><<<(unsigned)((bins + 3) / 4), 128, 0, s>>>(a, bins); break;
-    case 1: raster_bwd_kernel<1><<<(unsigned)bins, 256, 0, s>>>(a); break;
-    case 4: raster_bwd_kernel<4><<<(unsigned)bins, 64, 0, s>>>(a); break;
-    default: raster_bwd_kernel<2><<<(unsigned)bins, 128, 0, s>>>(a); break;
+    case 1: launch_shape<1>(false, a, bins, s); break;
+    case 4: launch_shape<4>(false, a, bins, s); break;
+    case 8: launch_shape<8>(false, a, bins, s); break;
+    default: launch_shape<2>(false, a, bins, s); break;
   }
 }
 

@@ -345,7 +345,11 @@ gs_status gs_serve_poll(gs_server* s, uint64_t ticket, int64_t timeout_us, const
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return GS_EINVAL;
-  const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+  // negative or huge timeouts wait (practically) forever; cap to keep the
+  // deadline arithmetic in range
+  const int64_t cap_us = (int64_t)1 << 40;  // about 12 days
+  const int64_t wait_us = (timeout_us < 0 || timeout_us > cap_us) ? cap_us : timeout_us;
+  const auto deadline = Clock::now() + std::chrono::microseconds(wait_us);
   while (it->second.state != kDone) {
     if (timeout_us == 0) return GS_EAGAIN;
     if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && it->second.state != kDone)

@@ -22,7 +22,8 @@ _NAMES = ["GS_OK", "GS_EINVAL", "GS_ENOMEM", "GS_ECUDA", "GS_ECAPACITY", "GS_ETI
           "GS_EAGAIN", "GS_ESTATE"]
 
 (GS_BUF_REC0, GS_BUF_REC1, GS_BUF_REC2, GS_BUF_KEYS, GS_BUF_VALS, GS_BUF_RANGES, GS_BUF_TFINAL,
- GS_BUF_NLAST, GS_BUF_G2D) = range(9)
+ GS_BUF_NLAST, GS_BUF_G2D, GS_BUF_REC3) = range(10)
+LOG2E = 1.4426950408889634
 
 
 class GsError(RuntimeError):
@@ -260,7 +261,7 @@ class Context:
         n = cnt.value
         spec = {GS_BUF_REC0: ((n, 4), "<f4"), GS_BUF_REC1: ((n, 4), "<f4"), GS_BUF_REC2: ((n, 4), "<f4"),
                 GS_BUF_KEYS: ((n,), "<i8"), GS_BUF_VALS: ((n,), "<i4"), GS_BUF_RANGES: ((n, 2), "<i4"),
-                GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((n, 12), "<f4")}[which]
+                GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((9, n // 9), "<f4"), GS_BUF_REC3: ((n, 2), "<i4")}[which]
         if n == 0:
             return torch.empty(spec[0], device="cuda:%d" % self.device,
                                dtype={"<f4": torch.float32, "<i8": torch.int64, "<i4": torch.int32}[spec[1]])
@@ -327,7 +328,7 @@ class Server:
     def gs_serve_poll(self, ticket: int, timeout_us: int = -1):
         """Returns (status, image view or None); status GS_EAGAIN on timeout."""
         ptr, res = ctypes.c_void_p(), ctypes.c_int()
-        st = self.L.gs_serve_poll(self.h, ticket, int(timeout_us if timeout_us >= 0 else 1 << 60),
+        st = self.L.gs_serve_poll(self.h, ticket, int(timeout_us),
                                   ctypes.byref(ptr), ctypes.byref(res))
         if st == GS_EAGAIN:
             return GS_EAGAIN, None

@@ -35,7 +35,7 @@ def cpu_rect(mx, my, r, W, H):
     return x0, x1, y0, y1
 
 
-def expected_binning(rec0, rec2, cams, n, stride):
+def expected_binning(rec0, rec2, rec3, cams, n, stride):
     """Keys, values and ranges recomputed on the CPU from the GPU's projection."""
     B = len(cams)
     keys, vals = [], []
@@ -49,11 +49,11 @@ def expected_binning(rec0, rec2, cams, n, stride):
     for v, c in enumerate(cams):
         sl = slice(v * stride, v * stride + n)
         mx, my = rec0[sl, 0], rec0[sl, 1]
-        rad = rec2[sl, 2].view(np.int32).astype(np.int64)
-        tiles = rec2[sl, 3].view(np.uint32).astype(np.int64)
+        rad = rec3[sl, 0].astype(np.int64)
+        tiles = rec3[sl, 1].astype(np.int64)
         x0, x1, y0, y1 = cpu_rect(mx, my, rad, c["width"], c["height"])
         area = np.where(tiles > 0, (x1 - x0) * (y1 - y0), 0)
-        rects.append((x0, x1, y0, y1, area, rec2[sl, 1].view(np.uint32).astype(np.uint64)))
+        rects.append((x0, x1, y0, y1, area, np.ascontiguousarray(rec2[sl, 3]).view(np.uint32).astype(np.uint64)))
     # emission order: Gaussian, view, ty, tx
     for g in range(n):
         for v, c in enumerate(cams):

@@ -42,19 +42,21 @@ def test_projection_matches_oracle(ctx, oracle, name):
     scene, cams = SCENES[name]()
     run_forward(ctx, scene, cams)
     n, stride = scene["n"], scene["params"].shape[1]
-    r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
-    r1 = ctx.gs_get_buffer(gs.GS_BUF_REC1).cpu().numpy()
-    r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+    r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy().astype(np.float64)
+    r1 = ctx.gs_get_buffer(gs.GS_BUF_REC1).cpu().numpy().astype(np.float64)
+    r2f = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+    r2 = r2f.astype(np.float64)
+    r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
     for v, cam in enumerate(cams):
         sl = slice(v * stride, v * stride + n)
         pr = oracle.project(scene, cam)
         vis = (pr["flags"] & oracle.G_VISIBLE) != 0
-        tiles = r2[sl, 3].view(np.uint32)
+        tiles = r3[sl, 1]
         margin = (pr["flags"] & oracle.G_MARG_RECT) != 0
         # visibility and radius agree except on marginal rects
         bad = ((tiles > 0) != vis) & ~margin
         assert not bad.any(), ("visibility differs", np.nonzero(bad)[0][:8], pr["ext"][bad][:8])
-        rad = r2[sl, 2].view(np.int32)
+        rad = r3[sl, 0]
         both = vis & (tiles > 0)
         # the radius ceil itself may flip where 3 sqrt(lambda) is within FP32
         # reach of an integer (the rect usually does not change then)
@@ -63,17 +65,27 @@ def test_projection_matches_oracle(ctx, oracle, name):
         bad = both & ~margin & ~near_int & (rad != pr["radius"])
         assert not bad.any(), ("radius differs", rad[bad][:8], pr["radius"][bad][:8], pr["ext"][bad][:8])
         # depth: the same FP32 evaluation on both sides
-        dep = r2[sl, 1]
+        dep = r2f[sl, 3]
         assert np.array_equal(dep[both], pr["depth"][both].astype(np.float32))
         m = both
+        L = gs.LOG2E
+        conic = np.stack([r0[sl][m, 2] / (-0.5 * L), r0[sl][m, 3] / (-L), r1[sl][m, 0] / (-0.5 * L)], 1)
         np.testing.assert_allclose(r0[sl][m, 0:2], pr["mean2d"][m], rtol=0, atol=2e-3)
-        np.testing.assert_allclose(r0[sl][m, 2], pr["conic"][m, 0], rtol=1e-4, atol=1e-7)
-        np.testing.assert_allclose(r0[sl][m, 3], pr["conic"][m, 1], rtol=1e-4,
-                                   atol=1e-4 * np.abs(pr["conic"][m, 0:3]).max(axis=1).max())
-        np.testing.assert_allclose(r1[sl][m, 0], pr["conic"][m, 2], rtol=1e-4, atol=1e-7)
+        scale = np.abs(pr["conic"][m]).max(axis=1, keepdims=True)
+        assert np.all(np.abs(conic - pr["conic"][m]) <= 1e-4 * scale)
         np.testing.assert_allclose(r1[sl][m, 1], pr["opacity"][m], rtol=1e-6, atol=0)
         rgb = np.concatenate([r1[sl][m, 2:4], r2[sl][m, 0:1]], axis=1)
         np.testing.assert_allclose(rgb, pr["rgb"][m], rtol=0, atol=2e-5)
+        # the cull box contains the exact alpha >= 1/255 ellipse's box
+        A, B, C = pr["conic"][m].T
+        det = A * C - B * B
+        tau = 2.0 * np.log(np.maximum(255.0 * pr["opacity"][m], 1e-300))
+        reach = tau > 0
+        hx = np.sqrt(np.where(reach, tau, 0) * C / det)
+        hy = np.sqrt(np.where(reach, tau, 0) * A / det)
+        assert np.all(r2[sl][m, 1][reach] >= hx[reach])
+        assert np.all(r2[sl][m, 2][reach] >= hy[reach])
+        assert np.all(r2[sl][m, 1][~reach] < -1e30)
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -83,7 +95,8 @@ def test_binning_is_bit_exact(ctx, name):
     n, stride = scene["n"], scene["params"].shape[1]
     r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
     r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
-    keys, vals, ranges, per_view = expected_binning(r0, r2, cams, n, stride)
+    r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
+    keys, vals, ranges, per_view = expected_binning(r0, r2, r3, cams, n, stride)
     gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)
     gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64)
     gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
@@ -91,7 +104,7 @@ def test_binning_is_bit_exact(ctx, name):
     assert inst == keys.size == per_view.sum()
     # per-(view, Gaussian) tile counts equal the rect areas
     for v in range(len(cams)):
-        t = r2[v * stride: v * stride + n, 3].view(np.uint32)
+        t = r3[v * stride: v * stride + n, 1].astype(np.int64)
         assert int(t.sum()) == int(per_view[v])
     assert np.array_equal(gk, keys)
     assert np.array_equal(gv, vals)
@@ -153,9 +166,9 @@ def test_gradient_matches_oracle(ctx, oracle, name, fwd, bwd):
         r = ref[lo:hi, :n][:, keep]
         if np.linalg.norm(r) > 0:
             assert rel_l2(g[lo:hi, :n][:, keep], r) <= 1e-3, (lo, hi)
-    g2d = ctx.gs_get_buffer(gs.GS_BUF_G2D).cpu().numpy().astype(np.float64)
+    g2d = ctx.gs_get_buffer(gs.GS_BUF_G2D).cpu().numpy().astype(np.float64).T  # [B*stride][9]
     for v in range(len(cams)):
-        got = g2d[v * stride: v * stride + n, :9][keep]
+        got = g2d[v * stride: v * stride + n][keep]
         assert rel_l2(got, ref2d[v][keep]) <= 1e-3
 
 
