@@ -10,9 +10,14 @@ duplication, onesweep sort, ranges), forward compositing, L1 loss, backward
 compositing, projection backward and Adam, over a batch of B=16 views.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
+                    [--workload blobs4M|gyroid500k|noise18M] [--serve-sweep]
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-on the host cores instead (bounded sample of the same workload).
+on the host cores instead (bounded sample of the same workload).  The other
+workloads: gyroid500k = 500,000 Gaussians on the gyroid level set, 64 orbit
+cameras (radius 15) at 1024x1024, B=8; noise18M = 18,000,000 Gaussians on the
+zero level of 6-octave fractal noise, 4096x4096, B=4, with the device memory
+the training state holds reported beside the throughput.
 """
 from __future__ import annotations
 
@@ -41,46 +46,74 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
-    ap.add_argument("--n", type=int, default=4_000_000)
-    ap.add_argument("--res", type=int, default=2048)
-    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--workload", default="blobs4M", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="override the workload's Gaussian count")
+    ap.add_argument("--res", type=int, default=0, help="override the workload's resolution")
+    ap.add_argument("--batch", type=int, default=0, help="override the workload's views per step")
     ap.add_argument("--plain-views", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--serve-rate", type=float, default=100.0, help="render requests/s (0: skip serving)")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="sweep the request rate over 50..2000 req/s instead of one rate")
     ap.add_argument("--fwd-variant", type=int, default=0, help="force the forward compositing variant")
     ap.add_argument("--bwd-variant", type=int, default=0, help="force the backward compositing variant")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cache", default=os.environ.get("GS_SCENE_CACHE", "/tmp/gs_scene_cache"))
-    return ap.parse_args()
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    args.n = args.n or w["n"]
+    args.res = args.res or w["res"]
+    args.batch = args.batch or w["batch"]
+    return args
 
 
 # ---------------------------------------------------------------- workload
 
+# name -> scene builder, seed, sampling grid, Gaussians, resolution, views per
+# step, orbit grid (azimuths x elevations) and radius
+WORKLOADS = {
+    "blobs4M": dict(scene="blobs_scene", seed=4, grid=128, n=4_000_000, res=2048, batch=16, orbit=(16, 16),
+                    radius=4.0, title="blobs-isosurface-4M-2048sq-B16"),
+    "gyroid500k": dict(scene="gyroid_scene", seed=3, grid=96, n=500_000, res=1024, batch=8, orbit=(8, 8),
+                       radius=15.0, title="gyroid-isosurface-500k-1024sq-B8"),
+    "noise18M": dict(scene="noise_scene", seed=5, grid=256, n=18_000_000, res=4096, batch=4, orbit=(16, 16),
+                     radius=4.0, title="fractal-noise-isosurface-18M-4096sq-B4"),
+}
+
+
 def workload(args, device=None):
     from paper_2509_05216_gb300 import inputs
+    w = WORKLOADS[args.workload]
     os.makedirs(args.cache, exist_ok=True)
-    path = os.path.join(args.cache, "blobs_n%d_s4.npz" % args.n)
+    path = os.path.join(args.cache, "%s_n%d_s%d.npz" % (w["scene"], args.n, w["seed"]))
     if os.path.exists(path):
         z = np.load(path)
         scene = {"params": z["params"], "n": int(z["n"]), "deg": int(z["deg"])}
     else:
-        scene = inputs.blobs_scene(args.n, seed=4, deg=3, res=128, device=device)
+        scene = getattr(inputs, w["scene"])(args.n, seed=w["seed"], deg=3, res=w["grid"], device=device)
         tmp = path + ".%d.tmp.npz" % os.getpid()
         np.savez(tmp, params=scene["params"], n=scene["n"], deg=scene["deg"])
         os.replace(tmp, path)
-    cams = inputs.orbit_cameras(16, 16, 4.0, args.res, args.res)
-    trained = inputs.perturb(scene, 104)
+    cams = inputs.orbit_cameras(w["orbit"][0], w["orbit"][1], w["radius"], args.res, args.res)
+    trained = inputs.perturb(scene, 100 + w["seed"])
     return scene, trained, cams
 
 
 def config_dict(args, n_gpus):
-    return {"workload": "blobs-isosurface-4M-2048sq-B16", "gaussians": args.n, "sh_degree": 3,
-            "resolution": [args.res, args.res], "batch_views": args.batch, "orbit_cameras": 256,
+    w = WORKLOADS[args.workload]
+    title = w["title"]
+    if (args.n, args.res, args.batch) != (w["n"], w["res"], w["batch"]):
+        title += " (resized: n=%d res=%d B=%d)" % (args.n, args.res, args.batch)
+    P = 59
+    return {"workload": title, "gaussians": args.n, "sh_degree": 3,
+            "resolution": [args.res, args.res], "batch_views": args.batch,
+            "orbit_cameras": w["orbit"][0] * w["orbit"][1],
             "global_batch": args.batch * n_gpus, "parallelism": "replicas x%d" % n_gpus,
-            "l2": "inputs larger than L2 (944 MB parameters, 805 MB targets per step)"}
+            "l2": "inputs larger than L2 (%d MB parameters, %d MB targets per step)"
+                  % (args.n * P * 4 // 10**6, args.batch * 3 * args.res * args.res * 4 // 10**6)}
 
 
 # ---------------------------------------------------------------- clocks
@@ -158,20 +191,23 @@ class Trainer:
 
 
 def render_targets(ctx, scene, cams, B, nbatch, device):
+    """Target images of the first nbatch batches (renders of the reference
+    set) and the largest instance count seen."""
     import torch
     from paper_2509_05216_gb300 import gs
     p = torch.from_numpy(scene["params"]).to(device)
     _, total = gs.image_offsets(cams[:B])
-    out = []
+    out, most = [], 0
     for b in range(nbatch):
         cb = cams[b * B:(b + 1) * B]
         t = torch.empty(total, device=device)
         ctx.gs_project(p, scene["n"], scene["deg"], cb)
         ctx.gs_bin_sort()
         ctx.gs_raster_fwd(t)
+        most = max(most, ctx.gs_get_counts()[0])
         out.append(t)
     ctx.gs_sync()
-    return out
+    return out, most
 
 
 # Algorithmic work per launch (documented in DESIGN.md): bytes for the
@@ -216,12 +252,15 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    torch.zeros(1, device=dev)
+    free0, hbm_total = torch.cuda.mem_get_info(dev)
     scene, trained, cams = workload(args, device=dev)
+    torch.cuda.empty_cache()
     B = args.batch
     nbatch = len(cams) // B
     ctx = gs.Context(local)
     t0 = time.time()
-    targets = render_targets(ctx, scene, cams, B, min(nbatch, args.warmup + args.steps), dev)
+    targets, most = render_targets(ctx, scene, cams, B, min(nbatch, args.warmup + args.steps), dev)
     _, total = gs.image_offsets(cams[:B])
     img = torch.empty(total, device=dev)
     dimg = torch.empty(total, device=dev)
@@ -244,11 +283,28 @@ def gpu_arm(args):
         tuned = autotune.tune([ctx], lambda: tr.step(*batch(0), img, dimg), key,
                               use_cache=not args.retune)
     ctx.gs_sync()
-    # timed region: K batched steps
+    # the batched step captured once in a CUDA graph (fixed instance capacity)
+    torch.cuda.synchronize(dev)
+    free_g0, _ = torch.cuda.mem_get_info(dev)
+    gctx = gs.Context(local, instance_capacity=int(most * 1.3) + (1 << 20))
+    for opt, val in tuned.items():
+        gctx.gs_set_option(opt, val)
+    gctx.gs_train_graph_capture(tr.p, tr.g, tr.m, tr.v, tr.n, tr.deg, HP, batch(0)[0], batch(0)[1], img, dimg,
+                                tr.loss)
+    torch.cuda.synchronize(dev)
+    free_g1, _ = torch.cuda.mem_get_info(dev)
+
+    def graph_step(cb, tb):
+        tr.t += 1
+        gctx.gs_train_graph_launch(cb, tb, tr.t)
+
+    for i in range(2):
+        graph_step(*batch(i))
+    gctx.gs_sync()
+    gctx.profile_reset()
+    # timed region: K batched steps, each one graph launch
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ctx.profile_reset()
-    ctx.profile_enable(True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -256,16 +312,26 @@ def gpu_arm(args):
         torch.cuda.nvtx.range_push("timed_steps")
         ev0.record(stream)
         for i in range(args.steps):
-            tr.step(*batch(args.warmup + i), img, dimg)
+            graph_step(*batch(args.warmup + i))
         ev1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
-    ctx.profile_enable(False)
-    kstats = ctx.profile_read()
-    ctx.gs_sync()
+    gctx.gs_sync()  # raises on capacity overflow
+    free_t, _ = torch.cuda.mem_get_info(dev)
+    state_bytes = 4 * tr.p.numel() * 4
+    memory = {"device_used_gb": round((free0 - free_t) / 1e9, 2),
+              "training_state_gb": round(state_bytes / 1e9, 2),
+              "graph_context_workspace_gb": round((free_g0 - free_g1) / 1e9, 2),
+              "one_step_gb": round((state_bytes + (free_g0 - free_g1) + 3 * img.numel() * 4) / 1e9, 2),
+              "hbm_total_gb": round(hbm_total / 1e9, 1),
+              "note": "one_step = parameters, gradients and Adam moments + the graph context's workspace "
+                      "(records, keys, sort, per-pixel state) + image, image gradient and one target batch; "
+                      "device_used also holds the cached targets and the call-by-call context"}
+    gk = gctx.profile_read()
+    launches = sum(k["launches"] for k in gk)
     t_max = ms
     if world > 1:
         tt = torch.tensor([ms], device=dev)
@@ -274,12 +340,27 @@ def gpu_arm(args):
     views = args.steps * B * world
     value = views / (t_max / 1000.0)
 
+    # per-kernel times: the same K steps launched call by call with CUDA
+    # events around every kernel on the launching stream
+    ctx.profile_reset()
+    ctx.profile_enable(True)
+    torch.cuda.synchronize(dev)
+    ek0, ek1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ek0.record(stream)
+    for i in range(args.steps):
+        tr.step(*batch(args.warmup + i), img, dimg)
+    ek1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_calls = ek0.elapsed_time(ek1)
+    ctx.profile_enable(False)
+    kstats = ctx.profile_read()
+    ctx.gs_sync()
+
     # work counters of one batched step (for the roofline)
     inst, bins, pixels = ctx.gs_get_counts()
     nl = ctx.gs_get_buffer(gs.GS_BUF_NLAST)
     pairs = float(nl.to(torch.float64).sum().item())
     P = tr.p.shape[0]
-    launches = sum(k["launches"] for k in kstats)
     dom = max(kstats, key=lambda k: k["total_ms"])
     per_kernel = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
                               "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in kstats), 1e-9), 4)}
@@ -341,7 +422,7 @@ def gpu_arm(args):
     for i in range(args.e2e_steps):
         b = i % 2
         dev_t.copy_(host_t[b], non_blocking=True)
-        tr.step(cams[b * B:(b + 1) * B], dev_t, img, dimg)
+        graph_step(cams[b * B:(b + 1) * B], dev_t)
         loss_h.copy_(tr.loss, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize(dev)
@@ -357,10 +438,23 @@ def gpu_arm(args):
         "e2e": {"value": round(e2e, 3), "unit": "views/s", "h2d_bytes_per_step": total * 4,
                 "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
+        "graph": "each timed step is one CUDA-graph launch of the whole step; per-kernel times and the roofline "
+                 "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
         "instances_per_step": int(inst), "pairs_per_step": pairs, "kernels": per_kernel,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
+        "memory": memory,
     }
-    if args.serve_rate > 0:
+    if args.serve_sweep:
+        tr.ctx.gs_sync()
+        torch.cuda.synchronize(dev)
+        sweep = []
+        for rate in SERVE_RATES:
+            b = serve_run(tr.p, tr.n, tr.deg, local, rate, args.serve_seconds, 2, 16)
+            o = serve_run(tr.p, tr.n, tr.deg, local, rate, args.serve_seconds, 1, 1)
+            b["one_request_per_launch"] = {k: o[k] for k in ("p50_ms", "p99_ms", "frames_per_s")}
+            sweep.append(b)
+        out["render_sweep"] = sweep
+    elif args.serve_rate > 0:
         tr.ctx.gs_sync()
         torch.cuda.synchronize(dev)
         batched = serve_run(tr.p, tr.n, tr.deg, local, args.serve_rate, args.serve_seconds, 2, 16)
@@ -371,6 +465,7 @@ def gpu_arm(args):
                          "resolutions": ["%dx%d" % r for r in SERVE_RES]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene, trained, cams, args)
+    gctx.close()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
@@ -381,6 +476,7 @@ def gpu_arm(args):
 # ---------------------------------------------------------------- serving
 
 SERVE_RES = [(512, 512), (1024, 1024), (2048, 2048), (3840, 2160)]
+SERVE_RATES = [50.0, 100.0, 200.0, 500.0, 1000.0, 2000.0]
 
 
 def serve_run(params, n, deg, device, rate, duration_s, slots, max_batch, seed=6):
@@ -455,21 +551,29 @@ def cpu_sample(trained, scene, cams, args, budget_s):
     gw = (cam["width"] + 15) // 16
     ntiles = gw * ((cam["height"] + 15) // 16)
     rng = np.random.default_rng(0)
-    frac = 1.0 / 8.0
-    want = np.zeros(ntiles, np.uint8)
-    want[rng.choice(ntiles, max(1, int(ntiles * frac)), replace=False)] = 1
-    t0 = time.time()
-    img, _, _, _ = oracle.render(trained, cam, tile_want=want)
-    ref, _, _, _ = oracle.render(scene, cam, tile_want=want)
-    _, dimg = oracle.l1(img, ref)
-    dimg = dimg.reshape(img.shape)
-    oracle.render_grad(trained, [cam], [dimg])
-    dt = time.time() - t0
-    used = int(want.sum())
+    order = rng.permutation(ntiles)
+
+    def run(frac):
+        want = np.zeros(ntiles, np.uint8)
+        want[order[:max(1, int(round(ntiles * frac)))]] = 1
+        t0 = time.time()
+        img, _, _, _ = oracle.render(trained, cam, tile_want=want)
+        ref, _, _, _ = oracle.render(scene, cam, tile_want=want)
+        _, dimg = oracle.l1(img, ref)
+        oracle.render_grad(trained, [cam], [dimg.reshape(img.shape)])
+        return int(want.sum()), time.time() - t0
+
+    # a short calibration run sizes the sample to about budget_s of CPU time
+    used, dt = run(1.0 / 64.0)
+    frac = min(1.0, max(1.0 / 64.0, budget_s / max(dt * 64.0, 1e-3)))
+    if frac > 1.0 / 64.0:
+        used, dt = run(frac)
     return {"value": round((used / ntiles) / dt, 6), "unit": "views/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": "one 2048x2048 view: forward + gradient over %d of %d tiles (%.1f s), scaled by the tile "
-                      "fraction; projection of all %d Gaussians included" % (used, ntiles, dt, trained["n"])}
+            "sample": "one %dx%d view of the training workload: forward of the trained and the reference set, L1 "
+                      "gradient and backward over %d of %d tiles (%.1f s), scaled by the tile fraction; "
+                      "projection of all %d Gaussians included"
+                      % (cam["width"], cam["height"], used, ntiles, dt, trained["n"])}
 
 
 def cpu_baseline(scene, trained, cams, args):

@@ -211,6 +211,32 @@ gs_status gs_l1_loss_noalloc(const float* x, const float* y, int64_t count, floa
 gs_status gs_adam(gs_ctx* ctx, gs_params* p, const gs_params* g, gs_params* m, gs_params* v,
                   const gs_adam_hp* hp, int64_t step);
 
+/* ---------------------------------------------------------------- CUDA graph */
+
+/* Capture one whole training step (gs_project, gs_bin_sort, gs_raster_fwd,
+ * gs_l1_loss against `targets`, gs_raster_bwd, gs_adam) into a CUDA graph
+ * owned by the context, for replay with gs_train_graph_launch.  Needs a
+ * context created with a fixed instance_capacity (nothing in the step then
+ * reads the device on the host).  Runs the step once uncaptured first (no
+ * parameter update) to size every workspace; the capture itself uses a
+ * private stream.  Every pointer (parameters, gradients, moments, targets,
+ * images, dL/dimages, loss: device) is baked into the graph and must stay
+ * valid, except the targets, which each launch names.
+ * Errors: GS_EINVAL, GS_ENOMEM, GS_ECUDA, and those of the steps. */
+gs_status gs_train_graph_capture(gs_ctx* ctx, gs_params* params, gs_params* grads, gs_params* m, gs_params* v,
+                                 const gs_adam_hp* hp, const gs_camera* cams, int32_t B, const float* targets,
+                                 float* images, float* dL_dimages, float* loss);
+
+/* Replay the captured step on the context's stream for new cameras (same B
+ * and resolutions as captured), the batch's targets (device, image layout)
+ * and Adam step number `step` (>= 1).  Cameras, Adam constants and the
+ * targets pointer go through a pinned staging area that the graph copies at
+ * its start; the call waits (host) until the previous replay has made that
+ * copy.  Capacity overflow is reported by gs_sync.
+ * Errors: GS_ESTATE (nothing captured), GS_EINVAL (cameras differ, NULL
+ * targets), GS_ECUDA. */
+gs_status gs_train_graph_launch(gs_ctx* ctx, const gs_camera* cams, int32_t B, const float* targets, int64_t step);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Render server: the trained Gaussians stay resident and camera requests of

@@ -178,11 +178,13 @@ size_t sort_lookback_bytes(int64_t count) {
 
 // Digit counts of every pass in one read of the keys.  hist: [npass][256].
 __global__ void __launch_bounds__(256) digit_histogram_kernel(const uint64_t* __restrict__ keys,
-                                                               int64_t count, int npass,
+                                                               const uint64_t* __restrict__ count_ptr,
+                                                               int64_t capacity, int npass,
                                                                uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[8][kRadix];
   for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
+  const int64_t count = min((int64_t)*count_ptr, capacity);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = keys[i];
@@ -195,14 +197,11 @@ __global__ void __launch_bounds__(256) digit_histogram_kernel(const uint64_t* __
   }
 }
 
-void launch_digit_histogram(const uint64_t* keys, int64_t count, int npass, uint32_t* hist, cudaStream_t s) {
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t want = (count + 4095) / 4096;
-  const unsigned blocks = (unsigned)(want < 1 ? 1 : (want > (int64_t)sms * 8 ? (int64_t)sms * 8 : want));
-  digit_histogram_kernel<<<blocks, 256, 0, s>>>(keys, count, npass, hist);
-}
+// Passes whose digit histogram is a single bucket leave the order unchanged
+// and are skipped.  ctrl[p] (written once per sort by digit_scan_kernel):
+// bit 0 = which ping-pong buffer holds the keys before pass p (p == npass:
+// the sorted result), bit 1 = pass p is skipped.
+constexpr uint32_t kCtrlParity = 1u, kCtrlTrivial = 2u;
 
 // One LSD pass: rank keys of the partition by digit (stable), find the
 // partition's offset for each digit by decoupled look-back over the earlier
@@ -221,15 +220,24 @@ struct SortSmem {
   uint8_t dig[kSortTile];                  // digit of each tile-sorted position
 };
 
-__global__ void __launch_bounds__(kSortThreads, 4) onesweep_pass_kernel(
-    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, int64_t count, int shift, const uint32_t* __restrict__ hist_pass,
-    uint32_t* lookback, uint32_t* counter, int* status) {
+__global__ void __launch_bounds__(kSortThreads, 4) onesweep_pass_kernel(SortArgs a, int pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t count = min((int64_t)*a.count, a.capacity);
+  const uint32_t ctrl = a.ctrl[pass];
+  if (ctrl & kCtrlTrivial) return;  // whole block: this digit is the same for every key
+  const int par = (int)(ctrl & kCtrlParity);
+  const uint64_t* __restrict__ kin = a.keys[par];
+  const uint32_t* __restrict__ vin = a.vals[par];
+  uint64_t* __restrict__ kout = a.keys[par ^ 1];
+  uint32_t* __restrict__ vout = a.vals[par ^ 1];
+  const int shift = kRadixBits * pass;
+  const uint32_t* __restrict__ hist_pass = a.hist_scan + pass * kRadix;
+  uint32_t* lookback = a.lookback + (size_t)pass * a.lookback_stride;
+  int* status = a.status;
   if (tid == 0) {
-    sm.part = atomicAdd(counter, 1u);
+    sm.part = atomicAdd(a.counters + pass, 1u);
     sm.timed_out = 0;
   }
   for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&sm.warp_hist[0][0])[i] = 0;
@@ -371,57 +379,90 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_pass_kernel(
   }
 }
 
-void launch_onesweep_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
-                          int64_t count, int digit, const uint32_t* hist_pass, uint32_t* lookback,
-                          uint32_t* counter, int* status, cudaStream_t s) {
-  const int64_t parts = (count + kSortTile - 1) / kSortTile;
-  if (parts == 0) return;
+void launch_onesweep_pass(const SortArgs& a, int pass, int64_t grid, cudaStream_t s) {
+  if (grid <= 0) return;
   const size_t smem = sizeof(SortSmem);
-  // (idempotent; set on every call so that each device the library runs on gets it)
-  cudaFuncSetAttribute(onesweep_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  onesweep_pass_kernel<<<(unsigned)parts, kSortThreads, smem, s>>>(kin, vin, kout, vout, count,
-                                                                    kRadixBits * digit, hist_pass,
-                                                                    lookback, counter, status);
-}
-
-// Exclusive scan of a pass's 256 digit counts, in place (one block per pass).
-__global__ void digit_scan_kernel(uint32_t* hist) {
-  __shared__ uint32_t s[kRadix];
-  uint32_t* h = hist + blockIdx.x * kRadix;
-  s[threadIdx.x] = h[threadIdx.x];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int i = 0; i < kRadix; i++) {
-      const uint32_t c = s[i];
-      s[i] = run;
-      run += c;
-    }
+  // once per device (the attribute is per device; not repeated inside a graph capture)
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    cudaFuncSetAttribute(onesweep_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  __syncthreads();
-  h[threadIdx.x] = s[threadIdx.x];
+  onesweep_pass_kernel<<<(unsigned)grid, kSortThreads, smem, s>>>(a, pass);
 }
 
-void launch_digit_scan(uint32_t* hist, int npass, cudaStream_t s) {
-  digit_scan_kernel<<<npass, kRadix, 0, s>>>(hist);
+int64_t sort_partitions(int64_t count) { return (count + kSortTile - 1) / kSortTile; }
+
+// Exclusive scan of each pass's 256 digit counts, and the pass control
+// words (one block of 256 threads, passes in order).
+__global__ void __launch_bounds__(kRadix) digit_scan_kernel(const uint32_t* __restrict__ hist,
+                                                             const uint64_t* __restrict__ count_ptr,
+                                                             int64_t capacity, int npass,
+                                                             uint32_t* __restrict__ scanned,
+                                                             uint32_t* __restrict__ ctrl) {
+  __shared__ uint32_t wsum[kRadix / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t count = (uint32_t)min((int64_t)*count_ptr, capacity);
+  uint32_t parity = 0;
+  for (int p = 0; p < npass; p++) {
+    const uint32_t c = hist[p * kRadix + tid];
+    const bool trivial = __syncthreads_or(c == count) != 0;
+    uint32_t inc = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < wid; w++) pre += wsum[w];
+    scanned[p * kRadix + tid] = pre + inc - c;
+    if (tid == 0) ctrl[p] = parity | (trivial ? kCtrlTrivial : 0u);
+    if (!trivial) parity ^= 1u;
+    __syncthreads();
+  }
+  if (tid == 0) ctrl[npass] = parity;
+}
+
+void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, cudaStream_t s) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t want = (grid_hint + 4095) / 4096;
+  const unsigned blocks = (unsigned)(want < 1 ? 1 : (want > (int64_t)sms * 8 ? (int64_t)sms * 8 : want));
+  digit_histogram_kernel<<<blocks, 256, 0, s>>>(a.keys[0], a.count, a.capacity, a.npass, a.hist);
+  digit_scan_kernel<<<1, kRadix, 0, s>>>(a.hist, a.count, a.capacity, a.npass, a.hist_scan, a.ctrl);
 }
 
 // ---------------------------------------------------------------- tile ranges
 
-__global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, int64_t count, uint2* __restrict__ ranges) {
+// ranges[bin] = [first, last + 1) of the bin in the sorted keys; block 0
+// also records which buffers hold the sorted list.
+__global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __restrict__ ranges) {
+  const int64_t count = min((int64_t)*a.count, a.capacity);
+  const int par = (int)(a.ctrl[a.npass] & kCtrlParity);
+  const uint64_t* __restrict__ keys = a.keys[par];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.sorted_keys = a.keys[par];
+    *a.sorted_vals = a.vals[par];
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t bin = (uint32_t)(keys[i] >> 32);
+    if ((int64_t)bin >= a.bins) continue;  // only after a capacity overflow (reported by the status)
     if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != bin) ranges[bin].x = (uint32_t)i;
     if (i == count - 1 || (uint32_t)(keys[i + 1] >> 32) != bin) ranges[bin].y = (uint32_t)(i + 1);
   }
 }
 
-void launch_tile_ranges(const uint64_t* keys, int64_t count, uint2* ranges, cudaStream_t s) {
-  if (count == 0) return;
-  int64_t blocks = (count + 255) / 256;
+void launch_tile_ranges(const SortArgs& a, int64_t grid_hint, uint2* ranges, cudaStream_t s) {
+  int64_t blocks = (grid_hint + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  tile_ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, count, ranges);
+  if (blocks < 1) blocks = 1;
+  tile_ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, ranges);
 }
 
 }  // namespace gs

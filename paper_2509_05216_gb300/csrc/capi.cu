@@ -11,13 +11,14 @@
 #include "gs_internal.cuh"
 #include "launch.h"
 
-namespace gs {
-void launch_digit_scan(uint32_t* hist, int npass, cudaStream_t s);
-}
-
 using namespace gs;
 
 namespace {
+
+constexpr size_t kViewStagingBytes = sizeof(ViewRec) * kMaxViews;
+constexpr size_t kAdamStagingOff = kViewStagingBytes;
+constexpr size_t kTargetStagingOff = kViewStagingBytes + 72 * sizeof(float);  // 8-byte aligned
+constexpr size_t kStagingBytes = kTargetStagingOff + sizeof(void*);
 
 struct DevBuf {
   void* p = nullptr;
@@ -34,18 +35,30 @@ struct gs_ctx {
   int* status_d = nullptr;
   int* status_h = nullptr;     // pinned
   uint64_t* pinned = nullptr;  // pinned scratch for small read-backs (16 KB)
+  // pinned staging of the per-step constants (cameras, Adam constants) read by
+  // the copies of a captured training graph
+  unsigned char* staging = nullptr;
+  bool capturing = false;
+  cudaStream_t graph_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t staged_ev = nullptr;  // the graph's staging copies have run
+  int graph_B = 0;
+  std::vector<int> graph_res;        // W, H per view of the captured batch
+  gs_adam_hp graph_hp{};
+  int64_t graph_kernels = 0;         // kernels per replay
+  int graph_planes = 0;
   int raster_fwd = 2;  // compositing variants (pixels per thread; 8 = one warp per tile)
-  int raster_bwd = 8;
+  int raster_bwd = 2;
 
   // last batch
   int B = 0, deg = 0;
   int64_t n = 0, stride = 0, bins = 0, pixels = 0, instances = 0, nblocks = 0;
   bool projected = false, sorted = false, rastered = false;
-  int sorted_in = 0;  // which ping-pong buffer holds the sorted list
   std::vector<ViewRec> views_h;
 
   DevBuf views, rec0, rec1, rec2, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
-      hist, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial;
+      hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
+      target_slot;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -78,9 +91,11 @@ gs_status fail(gs_ctx* c, gs_status st, const char* fmt, ...) {
 #define GS_CUDA(ctx, call)                                                                  \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \
-    if (e_ != cudaSuccess)                                                                  \
+    if (e_ != cudaSuccess) {                                                                \
+      (void)cudaGetLastError(); /* do not leave it for the next launch check */             \
       return fail(ctx, GS_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
                   __LINE__);                                                                \
+    }                                                                                       \
   } while (0)
 
 #define GS_CHECK_LAUNCH(ctx)                                                                    \
@@ -158,6 +173,10 @@ struct LaunchScope {
   int k;
   cudaEvent_t a = nullptr;
   LaunchScope(gs_ctx* ctx, const char* name, int kernels = 1) : c(ctx), k(kernel_index(ctx, name)) {
+    if (c->capturing) {  // counted per replay instead
+      c->graph_kernels += kernels;
+      return;
+    }
     c->kstats[k].launches += kernels;
     if (c->profiling) {
       a = take_event(c);
@@ -175,86 +194,9 @@ struct LaunchScope {
 
 void set_device(gs_ctx* c) { cudaSetDevice(c->device); }
 
-}  // namespace
-
-extern "C" {
-
-gs_status gs_create(gs_ctx** out, int device, const gs_config* cfg) {
-  if (!out) return GS_EINVAL;
-  *out = nullptr;
-  gs_config conf{};
-  if (cfg) conf = *cfg;
-  if (conf.max_views == 0) conf.max_views = kMaxViews;
-  if (conf.max_views < 0 || conf.max_views > kMaxViews) return GS_EINVAL;
-  if (conf.max_gaussians < 0 || conf.instance_capacity < 0) return GS_EINVAL;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
-    (void)cudaGetLastError();
-    return GS_ECUDA;
-  }
-  gs_ctx* c = new gs_ctx();
-  c->device = device;
-  c->cfg = conf;
-  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&c->status_d, sizeof(int)) != cudaSuccess ||
-      cudaMemset(c->status_d, 0, sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&c->status_h, sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&c->pinned, 16384) != cudaSuccess) {
-    (void)cudaGetLastError();
-    gs_destroy(c);
-    return GS_ECUDA;
-  }
-  *out = c;
-  return GS_OK;
-}
-
-void gs_destroy(gs_ctx* c) {
-  if (!c) return;
-  cudaSetDevice(c->device);
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  else cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->views, &c->rec0, &c->rec1, &c->rec2, &c->rec3, &c->tiles, &c->block_sums, &c->block_offsets,
-                    &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->lookback,
-                    &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial};
-  for (DevBuf* b : bufs)
-    if (b->p) cudaFree(b->p);
-  for (const auto& p : c->pending) {
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
-  }
-  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
-  if (c->status_d) cudaFree(c->status_d);
-  if (c->status_h) cudaFreeHost(c->status_h);
-  if (c->pinned) cudaFreeHost(c->pinned);
-  delete c;
-}
-
-const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null context"; }
-
-gs_status gs_set_stream(gs_ctx* c, void* stream) {
-  if (!c) return GS_EINVAL;
-  c->stream = reinterpret_cast<cudaStream_t>(stream);
-  return GS_OK;
-}
-
-gs_status gs_sync(gs_ctx* c) {
-  if (!c) return GS_EINVAL;
-  set_device(c);
-  GS_CUDA(c, cudaMemcpyAsync(c->status_h, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  GS_CUDA(c, cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
-  GS_CUDA(c, cudaStreamSynchronize(c->stream));
-  const int st = *c->status_h;
-  if (st & kStatusTimeout) return fail(c, GS_ETIMEOUT, "a bounded device-side wait ran out");
-  if (st & kStatusCapacity) return fail(c, GS_ECAPACITY, "instance capacity exceeded");
-  return GS_OK;
-}
-
-gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, int32_t B) {
-  if (!c) return GS_EINVAL;
-  GS_TRY(check_params(c, params, "params"));
-  if (!cams) return fail(c, GS_EINVAL, "cams is NULL");
-  if (B < 1 || B > c->cfg.max_views) return fail(c, GS_EINVAL, "B must be in 1..%d", c->cfg.max_views);
-  set_device(c);
-  c->projected = c->sorted = c->rastered = false;
+// Per-view records of a batch (host side), with each view's first tile bin
+// and first pixel.
+gs_status build_views(gs_ctx* c, const gs_camera* cams, int B, int64_t* tiles_out, int64_t* pixels_out) {
   c->views_h.assign(B, ViewRec{});
   int64_t tile_off = 0, pix_off = 0;
   for (int v = 0; v < B; v++) {
@@ -285,6 +227,120 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
     tile_off += (int64_t)r.gw * r.gh;
     pix_off += (int64_t)k.width * k.height;
   }
+  *tiles_out = tile_off;
+  *pixels_out = pix_off;
+  return GS_OK;
+}
+
+// Per-plane learning rate divided by the first-moment bias correction, and
+// 1 / sqrt(second-moment bias correction) in slot 64.
+void adam_constants(const gs_adam_hp* hp, int planes, int64_t step, float* out) {
+  const double bc1 = 1.0 - std::pow((double)hp->beta1, (double)step);
+  const double bc2 = 1.0 - std::pow((double)hp->beta2, (double)step);
+  for (int pl = 0; pl < 64; pl++) {
+    double lr = 0.0;
+    if (pl < planes) {
+      if (pl < 3) lr = hp->lr_mean;
+      else if (pl < 6) lr = hp->lr_scale;
+      else if (pl < 10) lr = hp->lr_quat;
+      else if (pl < 11) lr = hp->lr_opacity;
+      else if (pl < 14) lr = hp->lr_sh_dc;
+      else lr = hp->lr_sh_rest;
+    }
+    out[pl] = (float)(lr / bc1);
+  }
+  out[64] = (float)(1.0 / std::sqrt(bc2));
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_create(gs_ctx** out, int device, const gs_config* cfg) {
+  if (!out) return GS_EINVAL;
+  *out = nullptr;
+  gs_config conf{};
+  if (cfg) conf = *cfg;
+  if (conf.max_views == 0) conf.max_views = kMaxViews;
+  if (conf.max_views < 0 || conf.max_views > kMaxViews) return GS_EINVAL;
+  if (conf.max_gaussians < 0 || conf.instance_capacity < 0) return GS_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    (void)cudaGetLastError();
+    return GS_ECUDA;
+  }
+  gs_ctx* c = new gs_ctx();
+  c->device = device;
+  c->cfg = conf;
+  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&c->status_d, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->status_d, 0, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->status_h, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->pinned, 16384) != cudaSuccess ||
+      cudaMallocHost(&c->staging, kStagingBytes) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->staged_ev, cudaEventDisableTiming) != cudaSuccess) {
+    (void)cudaGetLastError();
+    gs_destroy(c);
+    return GS_ECUDA;
+  }
+  *out = c;
+  return GS_OK;
+}
+
+void gs_destroy(gs_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  DevBuf* bufs[] = {&c->views, &c->rec0, &c->rec1, &c->rec2, &c->rec3, &c->tiles, &c->block_sums, &c->block_offsets,
+                    &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->hist_scan,
+                    &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
+                    &c->sorted_slots, &c->adam_consts, &c->target_slot};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  for (const auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  if (c->status_d) cudaFree(c->status_d);
+  if (c->status_h) cudaFreeHost(c->status_h);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->staging) cudaFreeHost(c->staging);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
+  if (c->staged_ev) cudaEventDestroy(c->staged_ev);
+  delete c;
+}
+
+const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+gs_status gs_set_stream(gs_ctx* c, void* stream) {
+  if (!c) return GS_EINVAL;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  return GS_OK;
+}
+
+gs_status gs_sync(gs_ctx* c) {
+  if (!c) return GS_EINVAL;
+  set_device(c);
+  GS_CUDA(c, cudaMemcpyAsync(c->status_h, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int st = *c->status_h;
+  if (st & kStatusTimeout) return fail(c, GS_ETIMEOUT, "a bounded device-side wait ran out");
+  if (st & kStatusCapacity) return fail(c, GS_ECAPACITY, "instance capacity exceeded");
+  return GS_OK;
+}
+
+gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, int32_t B) {
+  if (!c) return GS_EINVAL;
+  GS_TRY(check_params(c, params, "params"));
+  if (!cams) return fail(c, GS_EINVAL, "cams is NULL");
+  if (B < 1 || B > c->cfg.max_views) return fail(c, GS_EINVAL, "B must be in 1..%d", c->cfg.max_views);
+  set_device(c);
+  c->projected = c->sorted = c->rastered = false;
+  int64_t tile_off = 0, pix_off = 0;
+  GS_TRY(build_views(c, cams, B, &tile_off, &pix_off));
   if (tile_off >= ((int64_t)1 << 31)) return fail(c, GS_EINVAL, "too many tiles in the batch");
   const int64_t n = params->n, stride = params->stride;
   const int64_t nb = (n + project_fwd_block() - 1) / project_fwd_block();
@@ -295,8 +351,12 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   GS_TRY(ensure(c, c->rec3, sizeof(int2) * B * stride));
   GS_TRY(ensure(c, c->tiles, sizeof(uint32_t) * B * stride));
   GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * nb));
-  GS_CUDA(c, cudaMemcpyAsync(c->views.p, c->views_h.data(), sizeof(ViewRec) * B, cudaMemcpyHostToDevice,
-                             c->stream));
+  if (c->capturing) {
+    // a captured step copies the cameras from the pinned staging area at its start
+  } else {
+    GS_CUDA(c, cudaMemcpyAsync(c->views.p, c->views_h.data(), sizeof(ViewRec) * B, cudaMemcpyHostToDevice,
+                               c->stream));
+  }
   ProjectArgs a{};
   a.params = params->data;
   a.n = n;
@@ -338,20 +398,35 @@ gs_status gs_bin_sort(gs_ctx* c) {
                            P<uint64_t>(c->total), c->stream);
   }
   GS_CHECK_LAUNCH(c);
-  int64_t I;
+  // capacity: the exact count (grow-on-demand contexts read it, one stream
+  // synchronisation) or the context's fixed capacity (no host read, so the
+  // sequence can be captured in a CUDA graph; overflow -> GS_ECAPACITY)
+  int64_t cap;
   if (c->cfg.instance_capacity > 0) {
-    return fail(c, GS_EINVAL, "fixed instance capacity is not supported by gs_bin_sort yet");
+    cap = c->cfg.instance_capacity;
+    c->instances = -1;
+  } else {
+    GS_CUDA(c, cudaMemcpyAsync(c->pinned, c->total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    cap = (int64_t)c->pinned[0];
+    c->instances = cap;
   }
-  GS_CUDA(c, cudaMemcpyAsync(c->pinned, c->total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
-  GS_CUDA(c, cudaStreamSynchronize(c->stream));
-  I = (int64_t)c->pinned[0];
-  if (I >= ((int64_t)1 << 30) - 1) return fail(c, GS_ECAPACITY, "%lld instances exceed 2^30", (long long)I);
-  c->instances = I;
-  GS_TRY(ensure(c, c->keys0, sizeof(uint64_t) * I));
-  GS_TRY(ensure(c, c->keys1, sizeof(uint64_t) * I));
-  GS_TRY(ensure(c, c->vals0, sizeof(uint32_t) * I));
-  GS_TRY(ensure(c, c->vals1, sizeof(uint32_t) * I));
+  if (cap >= ((int64_t)1 << 30) - 1) return fail(c, GS_ECAPACITY, "%lld instances exceed 2^30", (long long)cap);
+  GS_TRY(ensure(c, c->keys0, sizeof(uint64_t) * cap));
+  GS_TRY(ensure(c, c->keys1, sizeof(uint64_t) * cap));
+  GS_TRY(ensure(c, c->vals0, sizeof(uint32_t) * cap));
+  GS_TRY(ensure(c, c->vals1, sizeof(uint32_t) * cap));
   GS_TRY(ensure(c, c->ranges, sizeof(uint2) * c->bins));
+  int bin_bits = 0;
+  while (((int64_t)1 << bin_bits) < c->bins) bin_bits++;
+  const int npass = (32 + bin_bits + 7) / 8;  // the 32 depth bits and the bin bits
+  const size_t lb = sort_lookback_bytes(cap);
+  GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
+  GS_TRY(ensure(c, c->hist_scan, sizeof(uint32_t) * (8 * 256 + 16)));
+  GS_TRY(ensure(c, c->lookback, lb * npass));
+  GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
+  GS_TRY(ensure(c, c->sorted_slots, 2 * sizeof(void*)));
+
   DuplicateArgs d{};
   d.n = c->n;
   d.stride = c->stride;
@@ -364,73 +439,51 @@ gs_status gs_bin_sort(gs_ctx* c) {
   d.block_offsets = P<uint32_t>(c->block_offsets);
   d.keys = P<uint64_t>(c->keys0);
   d.vals = P<uint32_t>(c->vals0);
-  d.capacity = I;
+  d.capacity = cap;
   d.status = c->status_d;
-  if (I > 0) {
+  {
     LaunchScope ls(c, "duplicate");
     launch_duplicate(d, c->stream);
   }
   GS_CHECK_LAUNCH(c);
 
-  // radix passes over the 32 depth bits and the bits of the largest bin
-  int bin_bits = 0;
-  while (((int64_t)1 << bin_bits) < c->bins) bin_bits++;
-  const int npass = (32 + bin_bits + 7) / 8;
-  int cur = 0;
-  if (I > 1) {
-    GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
-    GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * 8 * 256, c->stream));
-    {
-      LaunchScope ls(c, "digit_histogram");
-      launch_digit_histogram(P<uint64_t>(c->keys0), I, npass, P<uint32_t>(c->hist), c->stream);
-    }
-    GS_CHECK_LAUNCH(c);
-    uint32_t* h_host = reinterpret_cast<uint32_t*>(c->pinned);
-    GS_CUDA(c, cudaMemcpyAsync(h_host, c->hist.p, sizeof(uint32_t) * npass * 256, cudaMemcpyDeviceToHost,
-                               c->stream));
-    GS_CUDA(c, cudaStreamSynchronize(c->stream));
-    std::vector<int> passes;
-    for (int p = 0; p < npass; p++) {
-      bool trivial = false;
-      for (int d = 0; d < 256; d++)
-        if ((int64_t)h_host[p * 256 + d] == I) trivial = true;
-      if (!trivial) passes.push_back(p);
-    }
-    {
-      LaunchScope ls(c, "digit_scan");
-      launch_digit_scan(P<uint32_t>(c->hist), npass, c->stream);
-    }
-    GS_CHECK_LAUNCH(c);
-    const size_t lb = sort_lookback_bytes(I);
-    if (!passes.empty()) {
-      GS_TRY(ensure(c, c->lookback, lb * passes.size()));
-      GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
-      GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * passes.size(), c->stream));
-      GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * 8, c->stream));
-    }
-    for (size_t q = 0; q < passes.size(); q++) {
-      const int p = passes[q];
-      const uint64_t* kin = P<uint64_t>(cur ? c->keys1 : c->keys0);
-      const uint32_t* vin = P<uint32_t>(cur ? c->vals1 : c->vals0);
-      uint64_t* kout = P<uint64_t>(cur ? c->keys0 : c->keys1);
-      uint32_t* vout = P<uint32_t>(cur ? c->vals0 : c->vals1);
-      {
-        LaunchScope ls(c, "onesweep_pass");
-        launch_onesweep_pass(kin, vin, kout, vout, I, p, P<uint32_t>(c->hist) + p * 256,
-                             reinterpret_cast<uint32_t*>(P<unsigned char>(c->lookback) + lb * q),
-                             P<uint32_t>(c->counters) + q, c->status_d, c->stream);
-      }
-      GS_CHECK_LAUNCH(c);
-      cur ^= 1;
-    }
-  }
-  GS_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * c->bins, c->stream));
-  if (I > 0) {
-    LaunchScope ls(c, "tile_ranges");
-    launch_tile_ranges(P<uint64_t>(cur ? c->keys1 : c->keys0), I, P<uint2>(c->ranges), c->stream);
+  SortArgs sa{};
+  sa.keys[0] = P<uint64_t>(c->keys0);
+  sa.keys[1] = P<uint64_t>(c->keys1);
+  sa.vals[0] = P<uint32_t>(c->vals0);
+  sa.vals[1] = P<uint32_t>(c->vals1);
+  sa.count = P<uint64_t>(c->total);
+  sa.capacity = cap;
+  sa.bins = c->bins;
+  sa.hist = P<uint32_t>(c->hist);
+  sa.hist_scan = P<uint32_t>(c->hist_scan);
+  sa.ctrl = P<uint32_t>(c->hist_scan) + 8 * 256;
+  sa.lookback = P<uint32_t>(c->lookback);
+  sa.lookback_stride = lb / sizeof(uint32_t);
+  sa.counters = P<uint32_t>(c->counters);
+  sa.npass = npass;
+  sa.status = c->status_d;
+  sa.sorted_keys = reinterpret_cast<const uint64_t**>(c->sorted_slots.p);
+  sa.sorted_vals = reinterpret_cast<const uint32_t**>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
+  GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * 8 * 256, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * 8, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * npass, c->stream));
+  {
+    LaunchScope ls(c, "digit_histogram", 2);
+    launch_digit_histogram(sa, cap, c->stream);
   }
   GS_CHECK_LAUNCH(c);
-  c->sorted_in = cur;
+  for (int p = 0; p < npass; p++) {
+    LaunchScope ls(c, "onesweep_pass");
+    launch_onesweep_pass(sa, p, sort_partitions(cap), c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  GS_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * c->bins, c->stream));
+  {
+    LaunchScope ls(c, "tile_ranges");
+    launch_tile_ranges(sa, cap, P<uint2>(c->ranges), c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
   c->sorted = true;
   return GS_OK;
 }
@@ -439,9 +492,10 @@ static RasterArgs raster_args(gs_ctx* c) {
   RasterArgs r{};
   r.views = P<ViewRec>(c->views);
   r.B = c->B;
+  r.n = c->n;
   r.stride = c->stride;
   r.ranges = P<uint2>(c->ranges);
-  r.vals = P<uint32_t>(c->sorted_in ? c->vals1 : c->vals0);
+  r.vals = reinterpret_cast<const uint32_t* const*>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
   r.rec0 = P<float4>(c->rec0);
   r.rec1 = P<float4>(c->rec1);
   r.rec2 = P<float4>(c->rec2);
@@ -519,7 +573,9 @@ gs_status gs_l1_loss(gs_ctx* c, const float* x, const float* y, int64_t count, f
   GS_TRY(ensure(c, c->l1_partial, sizeof(float) * parts));
   {
     LaunchScope ls(c, "l1_loss", loss ? 2 : 1);
-    launch_l1(x, y, count, P<float>(c->l1_partial), parts, loss, dL_dx, c->stream);
+    // inside a captured step the targets are read through the device slot
+    const float* const* slot = c->capturing ? reinterpret_cast<const float* const*>(c->target_slot.p) : nullptr;
+    launch_l1(x, y, slot, count, P<float>(c->l1_partial), parts, loss, dL_dx, c->stream);
   }
   GS_CHECK_LAUNCH(c);
   return GS_OK;
@@ -546,22 +602,18 @@ gs_status gs_adam(gs_ctx* c, gs_params* p, const gs_params* g, gs_params* m, gs_
   a.v = v->data;
   a.stride = p->stride;
   a.planes = n_planes(p->sh_degree);
-  const double bc1 = 1.0 - std::pow((double)hp->beta1, (double)step);
-  const double bc2 = 1.0 - std::pow((double)hp->beta2, (double)step);
-  for (int pl = 0; pl < a.planes; pl++) {
-    double lr;
-    if (pl < 3) lr = hp->lr_mean;
-    else if (pl < 6) lr = hp->lr_scale;
-    else if (pl < 10) lr = hp->lr_quat;
-    else if (pl < 11) lr = hp->lr_opacity;
-    else if (pl < 14) lr = hp->lr_sh_dc;
-    else lr = hp->lr_sh_rest;
-    a.lr[pl] = (float)(lr / bc1);
+  float consts[65];
+  adam_constants(hp, a.planes, step, consts);
+  GS_TRY(ensure(c, c->adam_consts, sizeof(consts)));
+  if (c->capturing) {
+    // a captured step copies the constants from the pinned staging area at its start
+  } else {
+    GS_CUDA(c, cudaMemcpyAsync(c->adam_consts.p, consts, sizeof(consts), cudaMemcpyHostToDevice, c->stream));
   }
+  a.consts = P<float>(c->adam_consts);
   a.beta1 = hp->beta1;
   a.beta2 = hp->beta2;
   a.eps = hp->eps;
-  a.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
   {
     LaunchScope ls(c, "adam");
     launch_adam(a, c->stream);
@@ -578,8 +630,18 @@ gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
     case GS_BUF_REC1: if (!c->projected) return GS_ESTATE; *ptr = c->rec1.p; *count = bn; break;
     case GS_BUF_REC2: if (!c->projected) return GS_ESTATE; *ptr = c->rec2.p; *count = bn; break;
     case GS_BUF_REC3: if (!c->projected) return GS_ESTATE; *ptr = c->rec3.p; *count = bn; break;
-    case GS_BUF_KEYS: if (!c->sorted) return GS_ESTATE; *ptr = c->sorted_in ? c->keys1.p : c->keys0.p; *count = c->instances; break;
-    case GS_BUF_VALS: if (!c->sorted) return GS_ESTATE; *ptr = c->sorted_in ? c->vals1.p : c->vals0.p; *count = c->instances; break;
+    case GS_BUF_KEYS:
+    case GS_BUF_VALS: {
+      if (!c->sorted) return GS_ESTATE;
+      void* slots[2] = {nullptr, nullptr};
+      uint64_t cnt = 0;
+      GS_CUDA(c, cudaMemcpyAsync(slots, c->sorted_slots.p, sizeof(slots), cudaMemcpyDeviceToHost, c->stream));
+      GS_CUDA(c, cudaMemcpyAsync(&cnt, c->total.p, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+      GS_CUDA(c, cudaStreamSynchronize(c->stream));
+      *ptr = slots[which == GS_BUF_KEYS ? 0 : 1];
+      *count = (int64_t)cnt;
+      break;
+    }
     case GS_BUF_RANGES: if (!c->sorted) return GS_ESTATE; *ptr = c->ranges.p; *count = c->bins; break;
     case GS_BUF_TFINAL: if (!c->rastered) return GS_ESTATE; *ptr = c->tfinal.p; *count = c->pixels; break;
     case GS_BUF_NLAST: if (!c->rastered) return GS_ESTATE; *ptr = c->nlast.p; *count = c->pixels; break;
@@ -593,8 +655,10 @@ gs_status gs_get_counts(gs_ctx* c, int64_t* instances, int64_t* bins, int64_t* p
   if (!c) return GS_EINVAL;
   if (!c->projected) return fail(c, GS_ESTATE, "no batch projected");
   set_device(c);
+  uint64_t cnt = 0;
+  if (c->sorted) GS_CUDA(c, cudaMemcpyAsync(&cnt, c->total.p, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   GS_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (instances) *instances = c->sorted ? c->instances : -1;
+  if (instances) *instances = c->sorted ? (int64_t)cnt : -1;
   if (bins) *bins = c->bins;
   if (pixels) *pixels = c->pixels;
   return GS_OK;
@@ -621,6 +685,104 @@ gs_status gs_get_option(gs_ctx* c, int32_t option, int64_t* value) {
     case GS_OPT_RASTER_BWD: *value = c->raster_bwd; return GS_OK;
     default: return fail(c, GS_EINVAL, "unknown option %d", option);
   }
+}
+
+gs_status gs_train_graph_capture(gs_ctx* c, gs_params* p, gs_params* g, gs_params* m, gs_params* v,
+                                 const gs_adam_hp* hp, const gs_camera* cams, int32_t B, const float* targets,
+                                 float* images, float* dL_dimages, float* loss) {
+  if (!c) return GS_EINVAL;
+  if (c->cfg.instance_capacity <= 0)
+    return fail(c, GS_EINVAL, "graph capture needs a context with a fixed instance capacity");
+  if (!hp || !cams || !targets || !images || !dL_dimages || !loss)
+    return fail(c, GS_EINVAL, "NULL argument");
+  set_device(c);
+  // 1. one uncaptured pass (no parameter update) sizes every workspace
+  GS_TRY(gs_project(c, p, cams, B));
+  GS_TRY(gs_bin_sort(c));
+  GS_TRY(gs_raster_fwd(c, images));
+  const int64_t count = 3 * c->pixels;
+  GS_TRY(gs_l1_loss(c, images, targets, count, loss, dL_dimages));
+  GS_TRY(gs_raster_bwd(c, p, dL_dimages, g));
+  GS_TRY(ensure(c, c->adam_consts, 65 * sizeof(float)));
+  GS_TRY(ensure(c, c->target_slot, sizeof(void*)));
+  GS_TRY(gs_sync(c));
+  // 2. capture on a private stream
+  if (!c->graph_stream) GS_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+  if (c->gexec) {
+    GS_CUDA(c, cudaGraphExecDestroy(c->gexec));
+    c->gexec = nullptr;
+  }
+  cudaStream_t user = c->stream;
+  c->stream = c->graph_stream;
+  c->capturing = true;
+  c->graph_kernels = 0;
+  gs_status st = GS_OK;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    // per-step constants: staging area -> device, then the step
+    e = cudaMemcpyAsync(c->views.p, c->staging, sizeof(ViewRec) * B, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->adam_consts.p, c->staging + kAdamStagingOff, 65 * sizeof(float),
+                          cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->target_slot.p, c->staging + kTargetStagingOff, sizeof(void*), cudaMemcpyHostToDevice,
+                          c->stream);
+    // an external record: the event is recorded at every replay, so the host
+    // can wait on it before rewriting the staging area
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->staged_ev, c->stream, cudaEventRecordExternal);
+    if (e == cudaSuccess) st = gs_project(c, p, cams, B);
+    if (e == cudaSuccess && st == GS_OK) st = gs_bin_sort(c);
+    if (e == cudaSuccess && st == GS_OK) st = gs_raster_fwd(c, images);
+    if (e == cudaSuccess && st == GS_OK) st = gs_l1_loss(c, images, targets, count, loss, dL_dimages);
+    if (e == cudaSuccess && st == GS_OK) st = gs_raster_bwd(c, p, dL_dimages, g);
+    if (e == cudaSuccess && st == GS_OK) st = gs_adam(c, p, g, m, v, hp, 1);
+    const cudaError_t e2 = cudaStreamEndCapture(c->graph_stream, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  c->capturing = false;
+  c->stream = user;
+  if (e == cudaSuccess && st == GS_OK) e = cudaGraphInstantiate(&c->gexec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (st != GS_OK) return st;
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    c->gexec = nullptr;
+    return fail(c, GS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  }
+  c->graph_B = B;
+  c->graph_res.clear();
+  for (int i = 0; i < B; i++) {
+    c->graph_res.push_back(cams[i].width);
+    c->graph_res.push_back(cams[i].height);
+  }
+  c->graph_hp = *hp;
+  c->graph_planes = n_planes(p->sh_degree);
+  return GS_OK;
+}
+
+gs_status gs_train_graph_launch(gs_ctx* c, const gs_camera* cams, int32_t B, const float* targets, int64_t step) {
+  if (!c) return GS_EINVAL;
+  if (!c->gexec) return fail(c, GS_ESTATE, "no captured training graph");
+  if (!cams || !targets || B != c->graph_B || step < 1)
+    return fail(c, GS_EINVAL, "cameras must match the captured batch; targets must not be NULL");
+  for (int i = 0; i < B; i++)
+    if (cams[i].width != c->graph_res[2 * i] || cams[i].height != c->graph_res[2 * i + 1])
+      return fail(c, GS_EINVAL, "camera %d: resolution differs from the captured batch", i);
+  set_device(c);
+  int64_t tiles = 0, pixels = 0;
+  GS_TRY(build_views(c, cams, B, &tiles, &pixels));
+  // the previous replay must have read the staging area before it is rewritten
+  GS_CUDA(c, cudaEventSynchronize(c->staged_ev));
+  memcpy(c->staging, c->views_h.data(), sizeof(ViewRec) * B);
+  adam_constants(&c->graph_hp, c->graph_planes, step, reinterpret_cast<float*>(c->staging + kAdamStagingOff));
+  memcpy(c->staging + kTargetStagingOff, &targets, sizeof(void*));
+  {
+    LaunchScope ls(c, "train_graph", (int)c->graph_kernels);
+    GS_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+  }
+  c->projected = c->sorted = c->rastered = true;
+  return GS_OK;
 }
 
 gs_status gs_profile_enable(gs_ctx* c, int32_t enable) {

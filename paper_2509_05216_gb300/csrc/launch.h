@@ -49,8 +49,9 @@ struct RasterArgs {
   const ViewRec* views;
   int B;
   int64_t stride;       // view stride of the records
+  int64_t n;            // Gaussians (indices at or above are ignored)
   const uint2* ranges;  // [bins]
-  const uint32_t* vals; // sorted Gaussian indices
+  const uint32_t* const* vals;  // device slot holding the sorted Gaussian indices
   const float4* rec0;
   const float4* rec1;
   const float4* rec2;
@@ -69,21 +70,40 @@ void launch_scan_block_sums(const uint32_t* sums, int64_t nb, uint32_t* offsets,
                             cudaStream_t s);
 void launch_duplicate(const DuplicateArgs& a, cudaStream_t s);
 
-// Radix sort of (key, value) pairs on key bits [0, 8 * npass_max) with the
-// passes `pass_list` (digit positions, ascending).  Buffers ping-pong; returns
-// 0 if the sorted result ends in (keys0, vals0), 1 if in (keys1, vals1).
+// LSD radix sort of (key, value) pairs on key bits [0, 8 npass), ping-pong
+// between keys[0]/vals[0] (input) and keys[1]/vals[1].  Everything that
+// depends on the data (instance count, skipped passes, which buffer ends up
+// sorted) is decided on the device, so the sequence can be captured in a
+// CUDA graph.
+struct SortArgs {
+  uint64_t* keys[2];
+  uint32_t* vals[2];
+  const uint64_t* count;     // device: number of pairs (clamped to capacity)
+  int64_t capacity;          // pairs the buffers hold
+  int64_t bins;              // valid bin ids are [0, bins)
+  uint32_t* hist;            // [8][256] digit counts
+  uint32_t* hist_scan;       // [8][256] exclusive digit offsets
+  uint32_t* ctrl;            // [npass + 1] pass control: source buffer, skipped
+  uint32_t* lookback;        // [npass][lookback_stride]
+  size_t lookback_stride;    // uint32 per pass (sort_lookback_bytes / 4)
+  uint32_t* counters;        // [8] partition tickets
+  int npass;
+  int* status;
+  const uint64_t** sorted_keys;  // device slots: where the sorted list ends up
+  const uint32_t** sorted_vals;
+};
+
 size_t sort_lookback_bytes(int64_t count);
-void launch_digit_histogram(const uint64_t* keys, int64_t count, int npass, uint32_t* hist, cudaStream_t s);
-void launch_onesweep_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
-                          int64_t count, int digit, const uint32_t* hist_pass, uint32_t* lookback,
-                          uint32_t* counter, int* status, cudaStream_t s);
-void launch_tile_ranges(const uint64_t* keys, int64_t count, uint2* ranges, cudaStream_t s);
+int64_t sort_partitions(int64_t count);
+void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, cudaStream_t s);
+void launch_onesweep_pass(const SortArgs& a, int pass, int64_t grid, cudaStream_t s);
+void launch_tile_ranges(const SortArgs& a, int64_t grid_hint, uint2* ranges, cudaStream_t s);
 
 void launch_raster_fwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s);
 void launch_raster_bwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s);
 
-void launch_l1(const float* x, const float* y, int64_t count, float* partial, int nparts, float* loss,
-               float* grad, cudaStream_t s);
+void launch_l1(const float* x, const float* y, const float* const* y_slot, int64_t count, float* partial,
+               int nparts, float* loss, float* grad, cudaStream_t s);
 int l1_parts(int64_t count);
 
 struct AdamArgs {
@@ -93,9 +113,8 @@ struct AdamArgs {
   float* v;
   int64_t stride;
   int planes;
-  float lr[64];  // per plane, already multiplied by 1 / (1 - beta1^t)
+  const float* consts;  // device: [64] per-plane lr / (1 - beta1^t), [64] = 1 / sqrt(1 - beta2^t)
   float beta1, beta2, eps;
-  float inv_sqrt_bc2;  // 1 / sqrt(1 - beta2^t)
 };
 void launch_adam(const AdamArgs& a, cudaStream_t s);
 

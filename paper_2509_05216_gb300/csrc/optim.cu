@@ -18,9 +18,12 @@ int l1_parts(int64_t count) {
   return (int)parts;
 }
 
-__global__ void __launch_bounds__(kL1Threads) l1_kernel(const float* __restrict__ x, const float* __restrict__ y,
-                                                        int64_t count, float inv_count, float* __restrict__ grad,
-                                                        float* __restrict__ partial) {
+__global__ void __launch_bounds__(kL1Threads) l1_kernel(const float* __restrict__ x, const float* y_arg,
+                                                        const float* const* y_slot, int64_t count, float inv_count,
+                                                        float* __restrict__ grad, float* __restrict__ partial) {
+  // the target pointer comes from device memory when given through a slot
+  // (a captured training step reads each batch's targets there)
+  const float* __restrict__ y = y_slot ? *y_slot : y_arg;
   float s = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const float d = x[i] - y[i];
@@ -47,16 +50,24 @@ __global__ void l1_finish_kernel(const float* __restrict__ partial, int nparts, 
   }
 }
 
-void launch_l1(const float* x, const float* y, int64_t count, float* partial, int nparts, float* loss,
-               float* grad, cudaStream_t s) {
+void launch_l1(const float* x, const float* y, const float* const* y_slot, int64_t count, float* partial,
+               int nparts, float* loss, float* grad, cudaStream_t s) {
   const float inv = (float)(1.0 / (double)count);
-  l1_kernel<<<nparts, kL1Threads, 0, s>>>(x, y, count, inv, grad, partial);
+  l1_kernel<<<nparts, kL1Threads, 0, s>>>(x, y, y_slot, count, inv, grad, partial);
   if (loss) l1_finish_kernel<<<1, 32, 0, s>>>(partial, nparts, 1.0 / (double)count, loss);
 }
 
 // Adam over [planes][stride] float planes, float4 at a time (stride % 4 == 0,
 // so a vector never straddles two planes).
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
+  // step-dependent constants come from device memory, so the launch can be
+  // captured once and replayed for any step
+  __shared__ float lr_s[64];
+  __shared__ float isb2_s;
+  if (threadIdx.x < 64) lr_s[threadIdx.x] = a.consts[threadIdx.x];
+  if (threadIdx.x == 0) isb2_s = a.consts[64];
+  __syncthreads();
+  const float inv_sqrt_bc2 = isb2_s;
   const int64_t n4 = (int64_t)a.planes * a.stride / 4;
   const int64_t per_plane4 = a.stride / 4;
   float4* p4 = reinterpret_cast<float4*>(a.p);
@@ -65,13 +76,13 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   float4* v4 = reinterpret_cast<float4*>(a.v);
   const float b1 = a.beta1, b2 = a.beta2, c1 = 1.f - a.beta1, c2 = 1.f - a.beta2;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-    const float lr = a.lr[i / per_plane4];
+    const float lr = lr_s[i / per_plane4];
     const float4 g = g4[i];
     float4 m = m4[i], v = v4[i], p = p4[i];
 #define ADAM_LANE(f)                                                  \
   m.f = fmaf(b1, m.f, c1 * g.f);                                      \
   v.f = fmaf(b2, v.f, c2 * g.f * g.f);                                \
-  p.f -= lr * m.f / fmaf(sqrtf(v.f), a.inv_sqrt_bc2, a.eps);
+  p.f -= lr * m.f / fmaf(sqrtf(v.f), inv_sqrt_bc2, a.eps);
     ADAM_LANE(x) ADAM_LANE(y) ADAM_LANE(z) ADAM_LANE(w)
 #undef ADAM_LANE
     m4[i] = m;

@@ -36,6 +36,12 @@ __device__ __forceinline__ int view_of_bin(const ViewRec* views, int B, int bin)
 // and (hx, hy) the half-extents of the box around the alpha >= 1/255 ellipse.
 __device__ __forceinline__ void stage_one(const RasterArgs& a, int v, uint32_t g, float4& s0, float4& s1,
                                           float4& s2) {
+  if ((int64_t)g >= a.n) {  // only after a capacity overflow: a box nothing hits
+    s0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    s1 = s0;
+    s2 = make_float4(0.f, -3.0e38f, -3.0e38f, 0.f);
+    return;
+  }
   const int64_t o = (int64_t)v * a.stride + g;
   s0 = a.rec0[o];
   s1 = a.rec1[o];
@@ -93,39 +99,6 @@ __device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec
     const float scale = q < 2 ? (1.f / kLog2e) : (q == 2 || q == 4) ? -0.5f : (q == 3 ? -1.f : 1.f);
     atomicAdd(g2d + q * plane + rec, tot * scale);
   }
-}
-
-// Batched transpose-reduction of backward gradients.  A warp parks the
-// per-lane partial sums of up to kPend Gaussians in shared memory
-// (red[slot][value][lane], row pitch 33 so every access is conflict-free);
-// a flush has lane l sum rows l, l + 32, l + 64 (row = slot * 9 + value) over
-// the 32 lanes and add the total to its gradient plane: 18 shared-memory
-// operations per Gaussian instead of a 16-shuffle butterfly.
-constexpr int kPend = 8;
-constexpr int kRedPitch = 33;
-
-__device__ __forceinline__ void park_grad(float* red, int slot, const float (&acc)[16], int lane) {
-#pragma unroll
-  for (int q = 0; q < 9; q++) red[(slot * 9 + q) * kRedPitch + lane] = acc[q];
-}
-
-__device__ __forceinline__ void flush_grads(float* red, const uint32_t* pend_g, int npend, float* g2d, int64_t plane,
-                                            int64_t vbase, int lane) {
-  __syncwarp();
-#pragma unroll
-  for (int r0 = 0; r0 < kPend * 9; r0 += 32) {
-    const int row = r0 + lane;
-    if (row < npend * 9) {
-      const float* src = red + row * kRedPitch;
-      float t = 0.f;
-#pragma unroll 8
-      for (int l = 0; l < 32; l++) t += src[l];
-      const int slot = row / 9, q = row - slot * 9;
-      const float scale = q < 2 ? (1.f / kLog2e) : (q == 2 || q == 4) ? -0.5f : (q == 3 ? -1.f : 1.f);
-      atomicAdd(g2d + q * plane + vbase + pend_g[slot], t * scale);
-    }
-  }
-  __syncwarp();
 }
 
 // One backward (pixel, Gaussian) pair, branch-free so that the pixels of a
@@ -248,6 +221,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   const ViewRec& V = a.views[v];
   const uint2 rg = a.ranges[geo.bin];
   const int n = (int)(rg.y - rg.x);
+  const uint32_t* __restrict__ vals = *a.vals;
 
   float T[PPT], C[PPT][3];
   uint32_t last[PPT];
@@ -265,7 +239,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     if (__all_sync(0xffffffffu, done == all_done)) break;
     const int i = b0 + lane;
     __syncwarp();
-    if (i < n) stage_one(a, v, a.vals[rg.x + i], s0[w][lane], s1[w][lane], s2[w][lane]);
+    if (i < n) stage_one(a, v, vals[rg.x + i], s0[w][lane], s1[w][lane], s2[w][lane]);
     __syncwarp();
     const int cnt = min(32, n - b0);
     for (int j = 0; j < cnt; j++) {
@@ -303,19 +277,15 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
   constexpr int NWB = G::NW * G::TPB;
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
   __shared__ uint32_t sg[NWB][32];
-  __shared__ float red_s[NWB][kPend * 9 * kRedPitch];
-  __shared__ uint32_t pend_s[NWB][kPend];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   G geo;
   if (!geo.init(a, bins, w, lane)) return;
   const int v = geo.v, px = geo.px, py0 = geo.py0;
   const ViewRec& V = a.views[v];
   const uint2 rg = a.ranges[geo.bin];
+  const uint32_t* __restrict__ vals = *a.vals;
   const int64_t plane = (int64_t)V.W * V.H;
   const float* dimg = a.dimage + 3 * V.pix_offset;
-  float* red = red_s[w];
-  uint32_t* pend = pend_s[w];
-  int npend = 0;
 
   // per pixel: T (running, from T_final backwards), dL/dC, sum_c dC_c S_c
   // (S = colour behind), T_final * sum_c dC_c bg_c, and n_last
@@ -344,7 +314,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
     const int i = bstart + lane;
     __syncwarp();
     if (i < bend) {
-      const uint32_t g = a.vals[rg.x + i];
+      const uint32_t g = vals[rg.x + i];
       stage_one(a, v, g, s0[w][lane], s1[w][lane], s2[w][lane]);
       sg[w][lane] = g;
     }
@@ -370,17 +340,9 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
       for (int k = 0; k < PPT; k++)
         any |= bwd_pair(idx < nl[k], q0, q1, rgb, a0, a1, __fsub_rn(q0.y, fpy + (float)k), dx, dx2, cA2dx, cBdx, T[k],
                         dCS[k], dC[k], bgd[k], acc);
-      if (__any_sync(0xffffffffu, any)) {
-        park_grad(red, npend, acc, lane);
-        if (lane == 0) pend[npend] = sg[w][j];
-        if (++npend == kPend) {
-          flush_grads(red, pend, npend, a.g2d, gplane, (int64_t)v * a.stride, lane);
-          npend = 0;
-        }
-      }
+      if (__any_sync(0xffffffffu, any)) push_grad(a.g2d, gplane, (int64_t)v * a.stride + sg[w][j], acc, lane);
     }
   }
-  if (npend) flush_grads(red, pend, npend, a.g2d, gplane, (int64_t)v * a.stride, lane);
 }
 
 template <int PPT>

@@ -66,7 +66,7 @@ class gs_serve_cfg(ctypes.Structure):
                 ("output_pool_bytes", ctypes.c_int64)]
 
 
-EXPORTS = ["gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
+EXPORTS = ["gs_train_graph_capture", "gs_train_graph_launch", "gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
            "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
            "gs_get_counts"]
@@ -96,6 +96,9 @@ def load(path: str | None = None):
     L.gs_adam.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), P(gs_params), P(gs_adam_hp), i64]
     L.gs_get_buffer.argtypes = [vp, i32, P(vp), P(i64)]
     L.gs_get_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
+    L.gs_train_graph_capture.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), P(gs_params), P(gs_adam_hp),
+                                         P(gs_camera), i32, vp, vp, vp, vp]
+    L.gs_train_graph_launch.argtypes = [vp, P(gs_camera), i32, vp, i64]
     L.gs_serve_create.argtypes = [P(vp), ctypes.c_int, P(gs_params), P(gs_serve_cfg)]
     L.gs_serve_destroy.argtypes = [vp]
     L.gs_serve_destroy.restype = None
@@ -220,6 +223,26 @@ class Context:
                        hp["lr_sh_rest"], hp.get("beta1", 0.9), hp.get("beta2", 0.999), hp.get("eps", 1e-15))
         self._check(self.L.gs_adam(self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv),
                                    ctypes.byref(h), int(step)), "gs_adam")
+
+    def gs_train_graph_capture(self, p, g, m, v, n, deg, hp: dict, cams, targets, images, dimages, loss):
+        """Capture one training step (needs instance_capacity > 0).  Keep every
+        tensor alive and in place while the graph is used."""
+        self._bind_stream()
+        sp, sg, sm, sv = (params_struct(t, n, deg) for t in (p, g, m, v))
+        h = gs_adam_hp(hp["lr_mean"], hp["lr_scale"], hp["lr_quat"], hp["lr_opacity"], hp["lr_sh_dc"],
+                       hp["lr_sh_rest"], hp.get("beta1", 0.9), hp.get("beta2", 0.999), hp.get("eps", 1e-15))
+        arr = (gs_camera * len(cams))(*[camera_struct(c) for c in cams])
+        self._graph_keep = (sp, sg, sm, sv, h, p, g, m, v, targets, images, dimages, loss)
+        self._check(self.L.gs_train_graph_capture(
+            self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv), ctypes.byref(h), arr,
+            len(cams), ctypes.c_void_p(targets.data_ptr()), ctypes.c_void_p(images.data_ptr()),
+            ctypes.c_void_p(dimages.data_ptr()), ctypes.c_void_p(loss.data_ptr())), "gs_train_graph_capture")
+
+    def gs_train_graph_launch(self, cams, targets: torch.Tensor, step: int):
+        self._bind_stream()
+        arr = (gs_camera * len(cams))(*[camera_struct(c) for c in cams])
+        self._check(self.L.gs_train_graph_launch(self.h, arr, len(cams), ctypes.c_void_p(targets.data_ptr()),
+                                                 int(step)), "gs_train_graph_launch")
 
     def gs_sync(self):
         self._check(self.L.gs_sync(self.h), "gs_sync")

@@ -377,6 +377,69 @@ def blobs_scene(n=4_000_000, seed=4, deg=3, res=128, iso=0.5, device=None):
     return _surface_scene(pts, nrm, deg, seed)
 
 
+# ---------------------------------------------------------------- config 4
+
+class NoiseField:
+    """Fractal value noise: f(x) = sum_{o<6} 0.5^o n(4 * 2^o * (x + 1) / 2),
+    n = trilinear interpolation (smoothstep weights) of seeded lattice values
+    in [-1, 1]; the [-1,1]^3 box stands for the 1024^3 volume."""
+
+    def __init__(self, seed=5, octaves=6, base=4.0, lacunarity=2.0, gain=0.5):
+        self.seed, self.octaves, self.base, self.lac, self.gain = seed, octaves, base, lacunarity, gain
+
+    def _lattice(self, ix, iy, iz, o):
+        import torch
+        h = (ix * 73856093) ^ (iy * 19349663) ^ (iz * 83492791) ^ ((self.seed * 2654435761 + o * 97) & 0x7FFFFFFF)
+        h = (h ^ (h >> 13)) * 1274126177
+        h = h ^ (h >> 16)
+        return (h & 0xFFFFFF).to(torch.float64) / float(0x7FFFFF) - 1.0
+
+    def fg(self, x):
+        import torch
+        f = torch.zeros(x.shape[0], dtype=torch.float64, device=x.device)
+        g = torch.zeros_like(x)
+        for o in range(self.octaves):
+            freq = self.base * self.lac ** o
+            amp = self.gain ** o
+            u = (x + 1.0) * 0.5 * freq
+            i0 = torch.floor(u)
+            t = u - i0
+            w = t * t * (3.0 - 2.0 * t)
+            dw = 6.0 * t * (1.0 - t) * 0.5 * freq
+            ii = i0.to(torch.int64)
+            val = torch.zeros_like(f)
+            dval = torch.zeros_like(g)
+            for cx in (0, 1):
+                for cy in (0, 1):
+                    for cz in (0, 1):
+                        lv = self._lattice(ii[:, 0] + cx, ii[:, 1] + cy, ii[:, 2] + cz, o)
+                        wx = w[:, 0] if cx else 1.0 - w[:, 0]
+                        wy = w[:, 1] if cy else 1.0 - w[:, 1]
+                        wz = w[:, 2] if cz else 1.0 - w[:, 2]
+                        sx = 1.0 if cx else -1.0
+                        sy = 1.0 if cy else -1.0
+                        sz = 1.0 if cz else -1.0
+                        val = val + lv * wx * wy * wz
+                        dval[:, 0] += lv * sx * dw[:, 0] * wy * wz
+                        dval[:, 1] += lv * sy * dw[:, 1] * wx * wz
+                        dval[:, 2] += lv * sz * dw[:, 2] * wx * wy
+            f = f + amp * val
+            g = g + amp * dval
+        return f, g
+
+
+def noise_scene(n=18_000_000, seed=5, deg=3, res=256, device=None):
+    """Gaussians on the zero level of 6-octave fractal value noise (Miranda-scale stand-in)."""
+    import torch
+    fld = NoiseField(seed)
+    fg = lambda x: _chunked(fld.fg, x, 1 << 20)
+    pts = _sample_isosurface(fg, -1.0, 1.0, 0.0, n, seed, res=res, device=device)
+    _, g = fg(torch.from_numpy(pts).to(_device(device)))
+    g = g.cpu().numpy()
+    nrm = g / np.linalg.norm(g, axis=1, keepdims=True)
+    return _surface_scene(pts, nrm, deg, seed)
+
+
 # ---------------------------------------------------------------- generic small scenes
 
 def random_scene(n, deg, seed, extent=1.0, log_scale=(-3.5, -2.0), opacity=(-2.0, 3.0)):

@@ -36,37 +36,40 @@ def cpu_rect(mx, my, r, W, H):
 
 
 def expected_binning(rec0, rec2, rec3, cams, n, stride):
-    """Keys, values and ranges recomputed on the CPU from the GPU's projection."""
-    B = len(cams)
-    keys, vals = [], []
-    tile_off = []
-    t = 0
+    """Keys, values and ranges recomputed on the CPU from the GPU's projection
+    (vectorised: one entry per (view, Gaussian, tile), stable sort by key, so
+    equal keys stay in Gaussian order)."""
+    tile_off, t = [], 0
     for c in cams:
         tile_off.append(t)
         t += ((c["width"] + 15) // 16) * ((c["height"] + 15) // 16)
     bins = t
-    rects = []
+    all_keys, all_vals, per_view = [], [], []
     for v, c in enumerate(cams):
         sl = slice(v * stride, v * stride + n)
         mx, my = rec0[sl, 0], rec0[sl, 1]
         rad = rec3[sl, 0].astype(np.int64)
         tiles = rec3[sl, 1].astype(np.int64)
         x0, x1, y0, y1 = cpu_rect(mx, my, rad, c["width"], c["height"])
-        area = np.where(tiles > 0, (x1 - x0) * (y1 - y0), 0)
-        rects.append((x0, x1, y0, y1, area, np.ascontiguousarray(rec2[sl, 3]).view(np.uint32).astype(np.uint64)))
-    # emission order: Gaussian, view, ty, tx
-    for g in range(n):
-        for v, c in enumerate(cams):
-            x0, x1, y0, y1, area, dbits = rects[v]
-            if area[g] == 0:
-                continue
-            gw = (c["width"] + 15) // 16
-            for ty in range(y0[g], y1[g]):
-                for tx in range(x0[g], x1[g]):
-                    keys.append(((tile_off[v] + ty * gw + tx) << 32) | int(dbits[g]))
-                    vals.append(g)
-    keys = np.array(keys, dtype=np.uint64)
-    vals = np.array(vals, dtype=np.int64)
+        w = np.where(tiles > 0, x1 - x0, 0)
+        h = np.where(tiles > 0, y1 - y0, 0)
+        area = w * h
+        per_view.append(int(area.sum()))
+        g = np.repeat(np.arange(n, dtype=np.int64), area)
+        start = np.repeat(np.cumsum(area) - area, area)
+        local = np.arange(area.sum(), dtype=np.int64) - start
+        wg = np.maximum(w[g], 1)
+        tx = x0[g] + local % wg
+        ty = y0[g] + local // wg
+        gw = (c["width"] + 15) // 16
+        dbits = np.ascontiguousarray(rec2[sl, 3]).view(np.uint32).astype(np.uint64)[g]
+        keys = ((tile_off[v] + ty * gw + tx).astype(np.uint64) << np.uint64(32)) | dbits
+        all_keys.append(keys)
+        all_vals.append(g)
+    keys = np.concatenate(all_keys) if all_keys else np.zeros(0, np.uint64)
+    vals = np.concatenate(all_vals) if all_vals else np.zeros(0, np.int64)
+    # emission order (Gaussian-major across views) does not matter after a
+    # stable sort: within a bin (one view) the order is by Gaussian index
     order = np.argsort(keys, kind="stable")
     keys, vals = keys[order], vals[order]
     ranges = np.zeros((bins, 2), dtype=np.int64)
@@ -76,7 +79,7 @@ def expected_binning(rec0, rec2, rec3, cams, n, stride):
         ends = np.r_[starts[1:], keys.size]
         ranges[b[starts], 0] = starts
         ranges[b[starts], 1] = ends
-    return keys, vals, ranges, np.array([int(r[4].sum()) for r in rects])
+    return keys, vals, ranges, np.array(per_view)
 
 
 def rel_l2(a, b):

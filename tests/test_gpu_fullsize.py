@@ -1,0 +1,126 @@
+"""Parity at the benchmark's full size (GPU only): 4,000,000 Gaussians on the
+blob isosurface, SH degree 3, B = 16 views of 2048 x 2048 in one launch, the
+launch configuration the benchmark times.  The oracle cannot render whole
+views at this size in test time, so the checks are sampled: binning
+bit-exact for two whole views, sampled pixels against the oracle, and the
+gradient of a loss supported on a few tiles against the oracle's gradient of
+the same loss (which only walks those tiles)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_05216_gb300 import gs, inputs
+from tests.gpu_helpers import expected_binning, rel_l2, to_dev_images
+
+pytestmark = pytest.mark.gpu
+
+N = 4_000_000
+B = 16
+RES = 2048
+
+
+@pytest.fixture(scope="module")
+def c3():
+    cache = os.environ.get("GS_SCENE_CACHE", "/tmp/gs_scene_cache")
+    os.makedirs(cache, exist_ok=True)
+    path = os.path.join(cache, "blobs_scene_n%d_s4.npz" % N)
+    if os.path.exists(path):
+        z = np.load(path)
+        scene = {"params": z["params"], "n": int(z["n"]), "deg": int(z["deg"])}
+    else:
+        scene = inputs.blobs_scene(N, seed=4, deg=3, res=128)
+        tmp = path + ".%d.tmp.npz" % os.getpid()
+        np.savez(tmp, params=scene["params"], n=scene["n"], deg=scene["deg"])
+        os.replace(tmp, path)
+    trained = inputs.perturb(scene, 104)
+    cams = inputs.orbit_cameras(16, 16, 4.0, RES, RES)[5 * B:6 * B]
+    ctx = gs.Context(0)
+    p = torch.from_numpy(trained["params"]).cuda()
+    ctx.gs_project(p, trained["n"], trained["deg"], cams)
+    ctx.gs_bin_sort()
+    _, total = gs.image_offsets(cams)
+    img = torch.empty(total, device="cuda")
+    ctx.gs_raster_fwd(img)
+    ctx.gs_sync()
+    yield {"scene": trained, "cams": cams, "ctx": ctx, "p": p, "img": img}
+    ctx.close()
+
+
+def test_fullsize_binning_bit_exact_on_two_views(c3):
+    ctx, cams, n = c3["ctx"], c3["cams"], c3["scene"]["n"]
+    stride = c3["scene"]["params"].shape[1]
+    r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
+    r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+    r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
+    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)
+    gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64)
+    gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
+    tiles_per_view = (RES // 16) ** 2
+    for v in (0, 11):
+        # a view's records and bins, as if it were a batch of one at bin offset v * tiles
+        sub = slice(v * stride, (v + 1) * stride)
+        keys, vals, ranges, per_view = expected_binning(r0[sub], r2[sub], r3[sub], [cams[v]], n, stride)
+        keys = keys + (np.uint64(v * tiles_per_view) << np.uint64(32))
+        lo, hi = v * tiles_per_view, (v + 1) * tiles_per_view
+        starts = gr[lo:hi, 0][gr[lo:hi, 1] > gr[lo:hi, 0]]
+        first = int(starts.min())
+        assert np.array_equal(gk[first:first + keys.size], keys)
+        assert np.array_equal(gv[first:first + keys.size], vals)
+        exp_r = np.where(ranges[:, 1:] > ranges[:, :1], ranges + first, 0)
+        assert np.array_equal(gr[lo:hi], exp_r)
+
+
+def test_fullsize_sampled_pixels_match_oracle(c3, oracle):
+    rng = np.random.default_rng(9)
+    views = gs.split_images(c3["img"], c3["cams"])
+    checked = 0
+    for v in range(0, B, 3):
+        cam = c3["cams"][v]
+        xs = rng.integers(0, RES, size=12)
+        ys = rng.integers(0, RES, size=12)
+        ref, _, marg = oracle.render_pixels(c3["scene"], cam, xs, ys)
+        got = views[v][:, ys, xs].T.cpu().numpy()
+        ok = ~marg
+        assert np.abs(got - ref)[ok].max() <= 1e-4
+        checked += int(ok.sum())
+    assert checked >= 60
+
+
+def test_fullsize_sampled_gradient_matches_oracle(c3, oracle):
+    """Loss supported on 3 tiles of each of two views: the GPU backward runs
+    on the whole B = 16 batch, the oracle walks only those tiles."""
+    ctx, cams, scene, p = c3["ctx"], c3["cams"], c3["scene"], c3["p"]
+    rng = np.random.default_rng(10)
+    dimgs = [np.zeros((3, RES, RES)) for _ in cams]
+    used = [2, 9]
+    for v in used:
+        for _ in range(3):
+            ty, tx = rng.integers(40, 88, size=2)  # tiles near the image centre
+            ys, xs = slice(16 * ty, 16 * ty + 16), slice(16 * tx, 16 * tx + 16)
+            dimgs[v][:, ys, xs] = rng.normal(size=(3, 16, 16))
+    # leave out pixels whose own decisions are marginal
+    for v in used:
+        cam = cams[v]
+        yy, xx = np.nonzero(np.abs(dimgs[v]).sum(0) > 0)
+        _, _, mg = oracle.render_pixels(scene, cam, xx, yy)
+        dimgs[v][:, yy[mg], xx[mg]] = 0.0
+    grads = torch.zeros_like(p)
+    ctx.gs_raster_bwd(p, scene["n"], scene["deg"], to_dev_images(dimgs), grads)
+    ctx.gs_sync()
+    ref = oracle.render_grad(scene, [cams[v] for v in used], [dimgs[v] for v in used])
+    n = scene["n"]
+    g = grads.cpu().numpy().astype(np.float64)
+    touched = np.nonzero(np.abs(ref[:, :n]).sum(0) > 0)[0]
+    assert touched.size > 50
+    keep = np.ones(touched.size, bool)
+    for v in used:
+        f = oracle.gaussian_flags({"params": scene["params"][:, touched], "n": touched.size, "deg": 3}, cams[v])
+        keep &= (f & oracle.G_MARG_ANY_GRAD) == 0
+    sel = touched[keep]
+    assert rel_l2(g[:, sel], ref[:, sel]) <= 1e-3
+    # Gaussians the loss does not reach get exactly zero
+    others = np.ones(n, bool)
+    others[touched] = False
+    assert np.abs(g[:, :n][:, others]).max() == 0.0
