@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--res", type=int, default=0, help="override the workload's resolution")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's views per step")
     ap.add_argument("--plain-views", type=int, default=16)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--serve-rate", type=float, default=100.0, help="render requests/s (0: skip serving)")
@@ -60,6 +60,8 @@ def parse():
                     help="sweep the request rate over 50..2000 req/s instead of one rate")
     ap.add_argument("--fwd-variant", type=int, default=0, help="force the forward compositing variant")
     ap.add_argument("--bwd-variant", type=int, default=0, help="force the backward compositing variant")
+    ap.add_argument("--bwd-direct", type=int, default=-1,
+                    help="force the backward's direct-atomic lane limit (with forced variants)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cache", default=os.environ.get("GS_SCENE_CACHE", "/tmp/gs_scene_cache"))
     args = ap.parse_args()
@@ -108,12 +110,14 @@ def config_dict(args, n_gpus):
     if (args.n, args.res, args.batch) != (w["n"], w["res"], w["batch"]):
         title += " (resized: n=%d res=%d B=%d)" % (args.n, args.res, args.batch)
     P = 59
+    state = 4 * args.n * P * 4 // 10**6          # parameters, gradients, Adam moments
+    images = 3 * args.batch * 3 * args.res * args.res * 4 // 10**6  # targets, image, image gradient
     return {"workload": title, "gaussians": args.n, "sh_degree": 3,
             "resolution": [args.res, args.res], "batch_views": args.batch,
             "orbit_cameras": w["orbit"][0] * w["orbit"][1],
             "global_batch": args.batch * n_gpus, "parallelism": "replicas x%d" % n_gpus,
-            "l2": "inputs larger than L2 (%d MB parameters, %d MB targets per step)"
-                  % (args.n * P * 4 // 10**6, args.batch * 3 * args.res * args.res * 4 // 10**6)}
+            "l2": "no flush: every step streams a working set larger than the 129 MB L2 (%d MB training "
+                  "state, %d MB of images, plus records and sort buffers)" % (state, images)}
 
 
 # ---------------------------------------------------------------- clocks
@@ -190,15 +194,32 @@ class Trainer:
         c.gs_adam(self.p, self.g, self.m, self.v, self.n, self.deg, HP, self.t)
 
 
-def render_targets(ctx, scene, cams, B, nbatch, device):
-    """Target images of the first nbatch batches (renders of the reference
+def replica_batches(rank, world, nbatch, count):
+    """Camera batches of one replica: rank r takes batches r, r + world, ...
+    (modulo the orbit), so the replicas train on disjoint views."""
+    return [(rank + i * world) % nbatch for i in range(count)]
+
+
+def max_over_ranks(x, world, device=None):
+    """Largest value of x over all ranks (the job's time is its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def render_targets(ctx, scene, cams, B, batches, device):
+    """Target images of the given camera batches (renders of the reference
     set) and the largest instance count seen."""
     import torch
     from paper_2509_05216_gb300 import gs
     p = torch.from_numpy(scene["params"]).to(device)
     _, total = gs.image_offsets(cams[:B])
     out, most = [], 0
-    for b in range(nbatch):
+    for b in batches:
         cb = cams[b * B:(b + 1) * B]
         t = torch.empty(total, device=device)
         ctx.gs_project(p, scene["n"], scene["deg"], cb)
@@ -260,15 +281,17 @@ def gpu_arm(args):
     nbatch = len(cams) // B
     ctx = gs.Context(local)
     t0 = time.time()
-    targets, most = render_targets(ctx, scene, cams, B, min(nbatch, args.warmup + args.steps), dev)
+    order = replica_batches(rank, world, nbatch, min(nbatch, args.warmup + args.steps))
+    targets, most = render_targets(ctx, scene, cams, B, order, dev)
     _, total = gs.image_offsets(cams[:B])
     img = torch.empty(total, device=dev)
     dimg = torch.empty(total, device=dev)
     tr = Trainer(ctx, trained, dev)
 
     def batch(i):
-        b = i % len(targets)
-        return cams[b * B:(b + 1) * B], targets[b]
+        k = i % len(order)
+        b = order[k]
+        return cams[b * B:(b + 1) * B], targets[k]
 
     for i in range(args.warmup):
         tr.step(*batch(i), img, dimg)
@@ -276,7 +299,8 @@ def gpu_arm(args):
     # launch options picked by the autotuner (timed on this workload, cached)
     key = autotune.workload_key(tr.n, cams[:B], B)
     if args.fwd_variant or args.bwd_variant:
-        tuned = {gs.GS_OPT_RASTER_FWD: args.fwd_variant or 2, gs.GS_OPT_RASTER_BWD: args.bwd_variant or 8}
+        tuned = {gs.GS_OPT_RASTER_FWD: args.fwd_variant or 2, gs.GS_OPT_RASTER_BWD: args.bwd_variant or 2,
+                 gs.GS_OPT_BWD_DIRECT: args.bwd_direct if args.bwd_direct >= 0 else 2}
         for opt, val in tuned.items():
             ctx.gs_set_option(opt, val)
     else:
@@ -332,11 +356,7 @@ def gpu_arm(args):
                       "device_used also holds the cached targets and the call-by-call context"}
     gk = gctx.profile_read()
     launches = sum(k["launches"] for k in gk)
-    t_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms, world, dev)
     views = args.steps * B * world
     value = views / (t_max / 1000.0)
 
@@ -397,36 +417,41 @@ def gpu_arm(args):
         for opt, val in tuned.items():
             ctx2.gs_set_option(opt, val)
     else:
-        autotune.tune([ctx2], lambda: tr2.step([cams[0]], one_t, one_img, one_dimg),
+        autotune.tune([ctx2], lambda: tr2.step([batch(0)[0][0]], one_t, one_img, one_dimg),
                       autotune.workload_key(tr2.n, cams[:1], 1), use_cache=not args.retune)
     for i in range(2):
-        tr2.step([cams[i]], targets[0][i * one_img.numel():(i + 1) * one_img.numel()], one_img, one_dimg)
+        tr2.step([batch(0)[0][i]], targets[0][i * one_img.numel():(i + 1) * one_img.numel()], one_img, one_dimg)
     ctx2.gs_sync()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.plain_views):
         b = i % B
-        tr2.step([cams[b]], targets[0][b * one_img.numel():(b + 1) * one_img.numel()], one_img, one_dimg)
+        tr2.step([batch(0)[0][b]], targets[0][b * one_img.numel():(b + 1) * one_img.numel()], one_img, one_dimg)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plain = args.plain_views / (e0.elapsed_time(e1) / 1000.0)
     ctx2.close()
 
-    # end to end: targets from pinned host memory, loss read back each step
+    # end to end through the host-buffer entry point: every step uploads its
+    # targets from pinned host memory (overlapped with the previous step on
+    # the library's copy stream) and reads its loss back to pinned memory
     host_t = [t.cpu().pin_memory() for t in targets[:2]]
-    dev_t = torch.empty(total, device=dev)
-    loss_h = torch.empty(1, pin_memory=True)
+    loss_h = [torch.empty(1, pin_memory=True) for _ in range(args.e2e_steps)]
+    gctx.gs_sync()
     torch.cuda.synchronize(dev)
+    t_e0 = time.perf_counter()
     e0.record(stream)
     for i in range(args.e2e_steps):
         b = i % 2
-        dev_t.copy_(host_t[b], non_blocking=True)
-        graph_step(cams[b * B:(b + 1) * B], dev_t)
-        loss_h.copy_(tr.loss, non_blocking=True)
+        tr.t += 1
+        gctx.gs_train_graph_launch_host(batch(b)[0], host_t[b], tr.t, loss_h[i])
     e1.record(stream)
+    gctx.gs_sync()
     torch.cuda.synchronize(dev)
-    e2e = args.e2e_steps * B * world / (e0.elapsed_time(e1) / 1000.0)
+    e2e_wall = time.perf_counter() - t_e0
+    e2e = args.e2e_steps * B * world / max(e0.elapsed_time(e1) / 1000.0, e2e_wall)
+    assert all(np.isfinite(float(x)) for x in loss_h)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "views/s", "n_gpus": world, "steps": args.steps,
@@ -563,10 +588,14 @@ def cpu_sample(trained, scene, cams, args, budget_s):
         oracle.render_grad(trained, [cam], [dimg.reshape(img.shape)])
         return int(want.sum()), time.time() - t0
 
-    # a short calibration run sizes the sample to about budget_s of CPU time
-    used, dt = run(1.0 / 64.0)
-    frac = min(1.0, max(1.0 / 64.0, budget_s / max(dt * 64.0, 1e-3)))
-    if frac > 1.0 / 64.0:
+    # grow the sample until it takes about budget_s of CPU time (the
+    # projection of every Gaussian is a fixed cost, so extrapolate twice)
+    frac = 1.0 / 64.0
+    used, dt = run(frac)
+    for _ in range(2):
+        if frac >= 1.0 or dt >= 0.6 * budget_s:
+            break
+        frac = min(1.0, frac * budget_s / max(dt, 1e-3))
         used, dt = run(frac)
     return {"value": round((used / ntiles) / dt, 6), "unit": "views/s", "cores": oracle.num_threads(),
             "kind": "oracle",

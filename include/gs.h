@@ -87,11 +87,17 @@ typedef struct {
   int32_t reserved;
 } gs_params;
 
-/* Adam hyper-parameters: one learning rate per parameter group. */
+/* Adam hyper-parameters: one learning rate per parameter group.  flags:
+ * GS_ADAM_SQRT_BATCH_LR multiplies every learning rate by sqrt(B), B = views
+ * of the context's last projected batch (the learning-rate scaling batched
+ * 3D-GS trainers such as Grendel-GS apply; off by default). */
 typedef struct {
   float lr_mean, lr_scale, lr_quat, lr_opacity, lr_sh_dc, lr_sh_rest;
   float beta1, beta2, eps;
+  int32_t flags;
 } gs_adam_hp;
+
+enum { GS_ADAM_SQRT_BATCH_LR = 1 };
 
 /* ---------------------------------------------------------------- context */
 
@@ -121,7 +127,12 @@ typedef enum {
                             thread with one block per tile, 8 = one warp per
                             tile.  All variants give the same result up to
                             FP32 rounding. */
-  GS_OPT_RASTER_BWD = 1  /* backward compositing kernel, same values */
+  GS_OPT_RASTER_BWD = 1, /* backward compositing kernel, same values */
+  GS_OPT_BWD_DIRECT = 2  /* backward: a warp whose pixels meet a Gaussian in at
+                            most this many lanes (0..32, default 2) adds the
+                            lanes' gradients with per-lane atomics instead of
+                            a warp reduction.  Same result up to FP32
+                            summation order. */
 } gs_option;
 
 /* Set / read an option.  Errors: GS_EINVAL (unknown option, bad value). */
@@ -236,6 +247,18 @@ gs_status gs_train_graph_capture(gs_ctx* ctx, gs_params* params, gs_params* grad
  * Errors: GS_ESTATE (nothing captured), GS_EINVAL (cameras differ, NULL
  * targets), GS_ECUDA. */
 gs_status gs_train_graph_launch(gs_ctx* ctx, const gs_camera* cams, int32_t B, const float* targets, int64_t step);
+
+/* gs_train_graph_launch with the batch's targets in HOST memory (image
+ * layout, float32) and the loss read back to host memory: the targets are
+ * uploaded on the context's own copy stream into one of two device buffers,
+ * so the upload for the next call overlaps this replay (overlap needs
+ * page-locked host memory; pageable memory works but copies synchronously).
+ * The host buffers must stay valid and unchanged until the step has run
+ * (gs_sync); *host_loss (may be NULL; page-locked for an asynchronous read)
+ * holds the step's loss after gs_sync.
+ * Errors: those of gs_train_graph_launch, GS_ENOMEM, GS_ECUDA. */
+gs_status gs_train_graph_launch_host(gs_ctx* ctx, const gs_camera* cams, int32_t B, const float* host_targets,
+                                     int64_t step, float* host_loss);
 
 /* ---------------------------------------------------------------- serving */
 

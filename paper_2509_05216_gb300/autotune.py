@@ -15,7 +15,8 @@ import torch
 
 from . import gs
 
-CANDIDATES = {gs.GS_OPT_RASTER_FWD: [2, 8, 4, 1], gs.GS_OPT_RASTER_BWD: [8, 2, 4, 1]}
+CANDIDATES = {gs.GS_OPT_RASTER_FWD: [2, 8, 4, 1], gs.GS_OPT_RASTER_BWD: [2, 4, 8, 1],
+              gs.GS_OPT_BWD_DIRECT: [2, 0, 4, 8]}
 
 
 def workload_key(n, cams, batch):
@@ -49,20 +50,26 @@ def _save(db):
         pass
 
 
-def time_step(step, reps=2):
+def time_step(step, reps=3):
+    """Shortest of `reps` single-step times (ms) after one warm-up step: the
+    minimum is the least disturbed by clock or power-state drift."""
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step()
     torch.cuda.synchronize()
-    ev0.record()
+    best = float("inf")
     for _ in range(reps):
+        ev0.record()
         step()
-    ev1.record()
-    torch.cuda.synchronize()
-    return ev0.elapsed_time(ev1) / reps
+        ev1.record()
+        torch.cuda.synchronize()
+        best = min(best, ev0.elapsed_time(ev1))
+    return best
 
 
-def tune(ctxs, step, key, candidates=None, reps=2, use_cache=True):
-    """Pick option values for `ctxs` (contexts the step uses) by timing `step`.
+def tune(ctxs, step, key, candidates=None, reps=3, rounds=2, use_cache=True):
+    """Pick option values for `ctxs` (contexts the step uses) by timing `step`,
+    one option at a time (the others at their current values).  Each
+    candidate is timed in `rounds` interleaved rounds and keeps its best time.
 
     Returns {option: value} and leaves the chosen values set."""
     candidates = candidates or CANDIDATES
@@ -72,14 +79,17 @@ def tune(ctxs, step, key, candidates=None, reps=2, use_cache=True):
     else:
         chosen, report = {}, {}
         for opt, values in candidates.items():
-            best, best_ms = None, float("inf")
+            times = {v: float("inf") for v in values}
+            for _ in range(rounds):
+                for v in values:
+                    for c in ctxs:
+                        c.gs_set_option(opt, v)
+                    times[v] = min(times[v], time_step(step, reps))
+            best = min(values, key=lambda v: times[v])
             for v in values:
-                for c in ctxs:
-                    c.gs_set_option(opt, v)
-                ms = time_step(step, reps)
-                report["%d=%d" % (opt, v)] = round(ms, 3)
-                if ms < best_ms:
-                    best, best_ms = v, ms
+                report["%d=%d" % (opt, v)] = round(times[v], 3)
+            for c in ctxs:
+                c.gs_set_option(opt, best)
             chosen[opt] = best
         db[key] = {"options": {str(k): v for k, v in chosen.items()}, "ms": report}
         if use_cache:

@@ -47,8 +47,17 @@ struct gs_ctx {
   gs_adam_hp graph_hp{};
   int64_t graph_kernels = 0;         // kernels per replay
   int graph_planes = 0;
+  float* graph_loss = nullptr;       // device loss the graph writes
+  int64_t graph_count = 0;           // image elements per step
+  // host-target replays: targets uploaded on a copy stream into two device
+  // buffers, so the upload of step k + 1 overlaps step k
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t tgt_copied[2] = {nullptr, nullptr};
+  cudaEvent_t tgt_free[2] = {nullptr, nullptr};
+  int64_t host_launches = 0;
   int raster_fwd = 2;  // compositing variants (pixels per thread; 8 = one warp per tile)
   int raster_bwd = 2;
+  int bwd_direct = 2;  // per-lane gradient atomics when at most this many lanes contribute
 
   // last batch
   int B = 0, deg = 0;
@@ -58,7 +67,7 @@ struct gs_ctx {
 
   DevBuf views, rec0, rec1, rec2, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
-      target_slot;
+      target_slot, host_tgt0, host_tgt1;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -234,9 +243,10 @@ gs_status build_views(gs_ctx* c, const gs_camera* cams, int B, int64_t* tiles_ou
 
 // Per-plane learning rate divided by the first-moment bias correction, and
 // 1 / sqrt(second-moment bias correction) in slot 64.
-void adam_constants(const gs_adam_hp* hp, int planes, int64_t step, float* out) {
+void adam_constants(const gs_adam_hp* hp, int planes, int64_t step, int B, float* out) {
   const double bc1 = 1.0 - std::pow((double)hp->beta1, (double)step);
   const double bc2 = 1.0 - std::pow((double)hp->beta2, (double)step);
+  const double lr_mul = (hp->flags & GS_ADAM_SQRT_BATCH_LR) ? std::sqrt((double)(B > 0 ? B : 1)) : 1.0;
   for (int pl = 0; pl < 64; pl++) {
     double lr = 0.0;
     if (pl < planes) {
@@ -247,7 +257,7 @@ void adam_constants(const gs_adam_hp* hp, int planes, int64_t step, float* out) 
       else if (pl < 14) lr = hp->lr_sh_dc;
       else lr = hp->lr_sh_rest;
     }
-    out[pl] = (float)(lr / bc1);
+    out[pl] = (float)(lr * lr_mul / bc1);
   }
   out[64] = (float)(1.0 / std::sqrt(bc2));
 }
@@ -294,7 +304,7 @@ void gs_destroy(gs_ctx* c) {
   DevBuf* bufs[] = {&c->views, &c->rec0, &c->rec1, &c->rec2, &c->rec3, &c->tiles, &c->block_sums, &c->block_offsets,
                     &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->hist_scan,
                     &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
-                    &c->sorted_slots, &c->adam_consts, &c->target_slot};
+                    &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -309,6 +319,14 @@ void gs_destroy(gs_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
   if (c->staged_ev) cudaEventDestroy(c->staged_ev);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (int i = 0; i < 2; i++) {
+    if (c->tgt_copied[i]) cudaEventDestroy(c->tgt_copied[i]);
+    if (c->tgt_free[i]) cudaEventDestroy(c->tgt_free[i]);
+  }
   delete c;
 }
 
@@ -539,6 +557,7 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   RasterArgs r = raster_args(c);
   r.dimage = dL_dimages;
   r.g2d = P<float>(c->g2d);
+  r.direct_max = c->bwd_direct;
   {
     LaunchScope ls(c, "raster_bwd");
     launch_raster_bwd(r, c->bins, c->raster_bwd, c->stream);
@@ -603,7 +622,7 @@ gs_status gs_adam(gs_ctx* c, gs_params* p, const gs_params* g, gs_params* m, gs_
   a.stride = p->stride;
   a.planes = n_planes(p->sh_degree);
   float consts[65];
-  adam_constants(hp, a.planes, step, consts);
+  adam_constants(hp, a.planes, step, c->B, consts);
   GS_TRY(ensure(c, c->adam_consts, sizeof(consts)));
   if (c->capturing) {
     // a captured step copies the constants from the pinned staging area at its start
@@ -673,6 +692,10 @@ gs_status gs_set_option(gs_ctx* c, int32_t option, int64_t value) {
         return fail(c, GS_EINVAL, "raster variant must be 1, 2, 4 or 8");
       (option == GS_OPT_RASTER_FWD ? c->raster_fwd : c->raster_bwd) = (int)value;
       return GS_OK;
+    case GS_OPT_BWD_DIRECT:
+      if (value < 0 || value > 32) return fail(c, GS_EINVAL, "direct-atomic lane limit must be 0..32");
+      c->bwd_direct = (int)value;
+      return GS_OK;
     default:
       return fail(c, GS_EINVAL, "unknown option %d", option);
   }
@@ -683,6 +706,7 @@ gs_status gs_get_option(gs_ctx* c, int32_t option, int64_t* value) {
   switch (option) {
     case GS_OPT_RASTER_FWD: *value = c->raster_fwd; return GS_OK;
     case GS_OPT_RASTER_BWD: *value = c->raster_bwd; return GS_OK;
+    case GS_OPT_BWD_DIRECT: *value = c->bwd_direct; return GS_OK;
     default: return fail(c, GS_EINVAL, "unknown option %d", option);
   }
 }
@@ -758,6 +782,8 @@ gs_status gs_train_graph_capture(gs_ctx* c, gs_params* p, gs_params* g, gs_param
   }
   c->graph_hp = *hp;
   c->graph_planes = n_planes(p->sh_degree);
+  c->graph_loss = loss;
+  c->graph_count = count;
   return GS_OK;
 }
 
@@ -775,13 +801,44 @@ gs_status gs_train_graph_launch(gs_ctx* c, const gs_camera* cams, int32_t B, con
   // the previous replay must have read the staging area before it is rewritten
   GS_CUDA(c, cudaEventSynchronize(c->staged_ev));
   memcpy(c->staging, c->views_h.data(), sizeof(ViewRec) * B);
-  adam_constants(&c->graph_hp, c->graph_planes, step, reinterpret_cast<float*>(c->staging + kAdamStagingOff));
+  adam_constants(&c->graph_hp, c->graph_planes, step, c->graph_B,
+                 reinterpret_cast<float*>(c->staging + kAdamStagingOff));
   memcpy(c->staging + kTargetStagingOff, &targets, sizeof(void*));
   {
     LaunchScope ls(c, "train_graph", (int)c->graph_kernels);
     GS_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
   }
   c->projected = c->sorted = c->rastered = true;
+  return GS_OK;
+}
+
+gs_status gs_train_graph_launch_host(gs_ctx* c, const gs_camera* cams, int32_t B, const float* host_targets,
+                                     int64_t step, float* host_loss) {
+  if (!c) return GS_EINVAL;
+  if (!c->gexec) return fail(c, GS_ESTATE, "no captured training graph");
+  if (!host_targets) return fail(c, GS_EINVAL, "targets must not be NULL");
+  set_device(c);
+  if (!c->copy_stream) {
+    GS_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; i++) {
+      GS_CUDA(c, cudaEventCreateWithFlags(&c->tgt_copied[i], cudaEventDisableTiming));
+      GS_CUDA(c, cudaEventCreateWithFlags(&c->tgt_free[i], cudaEventDisableTiming));
+    }
+  }
+  const int slot = (int)(c->host_launches & 1);
+  DevBuf& buf = slot ? c->host_tgt1 : c->host_tgt0;
+  const size_t bytes = sizeof(float) * (size_t)c->graph_count;
+  GS_TRY(ensure(c, buf, bytes));
+  // the buffer is rewritten once the replay that read it (two calls ago) is done
+  GS_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->tgt_free[slot], 0));
+  GS_CUDA(c, cudaMemcpyAsync(buf.p, host_targets, bytes, cudaMemcpyHostToDevice, c->copy_stream));
+  GS_CUDA(c, cudaEventRecord(c->tgt_copied[slot], c->copy_stream));
+  GS_CUDA(c, cudaStreamWaitEvent(c->stream, c->tgt_copied[slot], 0));
+  GS_TRY(gs_train_graph_launch(c, cams, B, P<float>(buf), step));
+  GS_CUDA(c, cudaEventRecord(c->tgt_free[slot], c->stream));
+  if (host_loss)
+    GS_CUDA(c, cudaMemcpyAsync(host_loss, c->graph_loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  c->host_launches++;
   return GS_OK;
 }
 

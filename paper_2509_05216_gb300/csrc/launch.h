@@ -60,6 +60,7 @@ struct RasterArgs {
   uint32_t* nlast;      // [pixels]
   const float* dimage;  // backward only
   float* g2d;           // backward only: 9 planes of [B][stride]
+  int direct_max;       // backward only: at most this many contributing lanes -> per-lane atomics
 };
 
 int project_fwd_block();

@@ -11,11 +11,11 @@
 // Launch shapes, selected per context (GS_OPT_RASTER_FWD / _BWD): PPT = 1, 2
 // or 4 pixels per thread with 8, 4 or 2 warps per tile (each warp an 8-pixel-
 // wide band), or PPT = 8 with one warp per 16x16 tile.  Every warp walks its
-// tile's list independently (no block barriers).  A record carries the
-// half-extents of the box around the ellipse where alpha >= 1/255 (slightly
-// widened); a warp whose pixel rectangle misses that box skips the Gaussian
-// with one uniform branch.  This removes only pairs that the per-pixel test
-// would skip, so the result is unchanged.
+// tile's list independently (no block barriers).  It stages 32 records at a
+// time, one per lane; each lane tests its record's alpha >= 1/255 ellipse
+// (with a rounding margin) against the warp's pixel rectangle, and the warp
+// walks only the survivors (a ballot mask).  This removes only pairs that
+// the per-pixel test would skip, so the result is unchanged.
 #include "gs_internal.cuh"
 #include "launch.h"
 
@@ -54,6 +54,40 @@ __device__ __forceinline__ bool box_hits(const float4& s0, const float4& s2, flo
   return s0.x + s2.y >= x0 && s0.x - s2.y <= x1 && s0.y + s2.z >= y0 && s0.y - s2.z <= y1;
 }
 
+// Can any pixel of the rectangle [x0,x1]x[y0,y1] pass the alpha >= 1/255
+// test?  p2(u, w) = cA u^2 + cB u w + cC w^2 (u = mu_x - x, w = mu_y - y) is
+// concave, so its maximum over the rectangle is 0 when the mean lies inside
+// and otherwise lies on an edge, where it is the 1-D maximum at the clamped
+// stationary point.  A pixel passes only if opacity * 2^p2 >= 1/255, i.e.
+// p2 >= -log2(255 opacity); the threshold is lowered by a margin that covers
+// the rounding of the per-pixel FP32 evaluation (relative to the largest term
+// magnitude over the rectangle) and of ex2.approx, so the test only removes
+// pairs the per-pixel test would skip.
+__device__ __forceinline__ bool ellipse_hits(const float4& r0, const float4& r1, const float4& r2, float x0,
+                                             float x1, float y0, float y1) {
+  if (!box_hits(r0, r2, x0, x1, y0, y1)) return false;
+  const float u0 = r0.x - x1, u1 = r0.x - x0, w0 = r0.y - y1, w1 = r0.y - y0;
+  if (u0 <= 0.f && u1 >= 0.f && w0 <= 0.f && w1 >= 0.f) return true;
+  const float cA = r0.z, cB = r0.w, cC = r1.x;
+  // stationary w for a fixed u and u for a fixed w (an approximate quotient
+  // only moves the evaluation point, which changes p2 to second order)
+  const float kw = __fdividef(-0.5f * cB, cC), ku = __fdividef(-0.5f * cB, cA);
+  float best = -3.0e38f;
+#pragma unroll
+  for (int e = 0; e < 2; e++) {
+    const float u = e ? u1 : u0;
+    const float w = fminf(fmaxf(kw * u, w0), w1);
+    best = fmaxf(best, fmaf(cA * u, u, fmaf(cB * u, w, cC * w * w)));
+    const float w2 = e ? w1 : w0;
+    const float u2 = fminf(fmaxf(ku * w2, u0), u1);
+    best = fmaxf(best, fmaf(cA * u2, u2, fmaf(cB * u2, w2, cC * w2 * w2)));
+  }
+  const float U = fmaxf(fabsf(u0), fabsf(u1)), W = fmaxf(fabsf(w0), fabsf(w1));
+  const float mag = fabsf(cA) * U * U + fabsf(cB) * U * W + fabsf(cC) * W * W;
+  const float thr = -__log2f(255.f * r1.y);
+  return best >= thr - (1e-3f + 1e-3f * fabsf(thr) + 1e-5f * mag);
+}
+
 // p2 at row offset dy = mu_y - y for a lane with column coefficients
 // a0 = cA dx^2, a1 = cB dx.  Every kernel variant, forward and backward,
 // evaluates it with the same instructions on the same operands for a given
@@ -89,16 +123,34 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// Apply the warp's reduced gradient of one Gaussian: lanes 2q (q < 9) add
-// the total of value q to plane q.  Accumulators hold d/d(mu_x, mu_y) of p2
-// and raw dx^2, dx dy, dy^2 sums; undo those scalings here.
-__device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec, float (&acc)[16], int lane) {
+// Accumulators hold d/d(mu_x, mu_y) of p2 and raw dx^2, dx dy, dy^2 sums;
+// the scale of value q undoes those scalings.
+__device__ __forceinline__ float grad_scale(int q) {
+  return q < 2 ? (1.f / kLog2e) : (q == 2 || q == 4) ? -0.5f : (q == 3 ? -1.f : 1.f);
+}
+
+// Apply a warp's gradient of one Gaussian.  `contrib`: ballot of the lanes
+// whose pixels contributed.  With few such lanes each adds its own 9 values
+// (9 atomic instructions for the warp); otherwise a reduce-scatter leaves
+// the total of value q in lanes 2q, 2q+1 and lane 2q adds it (16 shuffles).
+__device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec, float (&acc)[16], int lane,
+                                          uint32_t contrib, int direct_max) {
+  if (__popc(contrib) <= direct_max) {
+    if (contrib & (1u << lane)) {
+#pragma unroll
+      for (int q = 0; q < 9; q++) atomicAdd(g2d + q * plane + rec, acc[q] * grad_scale(q));
+    }
+    return;
+  }
   const float tot = warp_reduce_scatter16(acc, lane);
   const int q = lane >> 1;
-  if ((lane & 1) == 0 && q < 9) {
-    const float scale = q < 2 ? (1.f / kLog2e) : (q == 2 || q == 4) ? -0.5f : (q == 3 ? -1.f : 1.f);
-    atomicAdd(g2d + q * plane + rec, tot * scale);
-  }
+  if ((lane & 1) == 0 && q < 9) atomicAdd(g2d + q * plane + rec, tot * grad_scale(q));
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // One backward (pixel, Gaussian) pair, branch-free so that the pixels of a
@@ -115,7 +167,9 @@ __device__ __forceinline__ bool bwd_pair(bool live, const float4& q0, const floa
   const float alpha = splat_alpha2(q1.y, p2, G);
   const bool on = live && !(p2 > 0.f) && !(alpha < kAlphaSkip);
   const float ae = on ? alpha : 0.f;
-  const float inv_om = __frcp_rn(1.f - ae);
+  // 1 - ae is in [0.01, 1]: the approximate reciprocal (relative error
+  // below 2^-22) keeps the recovered T within FP32 rounding of the division
+  const float inv_om = rcp_approx(1.f - ae);
   const float Ti = T * inv_om;
   const float wgt = ae * Ti;
   const float dcr = dC[0] * rgb[0] + dC[1] * rgb[1] + dC[2] * rgb[2];
@@ -238,14 +292,24 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   for (int b0 = 0; b0 < n; b0 += 32) {
     if (__all_sync(0xffffffffu, done == all_done)) break;
     const int i = b0 + lane;
+    bool hit = false;
     __syncwarp();
-    if (i < n) stage_one(a, v, vals[rg.x + i], s0[w][lane], s1[w][lane], s2[w][lane]);
+    if (i < n) {
+      float4 r0, r1, r2;
+      stage_one(a, v, vals[rg.x + i], r0, r1, r2);
+      s0[w][lane] = r0;
+      s1[w][lane] = r1;
+      s2[w][lane] = r2;
+      hit = ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
+    }
+    // each lane culls its own record; the warp walks the survivors in order
+    uint32_t mask = __ballot_sync(0xffffffffu, hit);
     __syncwarp();
-    const int cnt = min(32, n - b0);
-    for (int j = 0; j < cnt; j++) {
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1u;
       const float4 q0 = s0[w][j];
       const float4 q2 = s2[w][j];
-      if (!box_hits(q0, q2, geo.wx0, geo.wx1, geo.wy0, geo.wy1)) continue;
       const float4 q1 = s1[w][j];
       const float dx = __fsub_rn(q0.x, fpx);
       const float a0 = __fmul_rn(q0.z, __fmul_rn(dx, dx));
@@ -312,17 +376,25 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
   for (int bend = total; bend > 0; bend -= 32) {
     const int bstart = max(0, bend - 32);
     const int i = bstart + lane;
+    bool hit = false;
     __syncwarp();
     if (i < bend) {
       const uint32_t g = vals[rg.x + i];
-      stage_one(a, v, g, s0[w][lane], s1[w][lane], s2[w][lane]);
+      float4 r0, r1, r2;
+      stage_one(a, v, g, r0, r1, r2);
+      s0[w][lane] = r0;
+      s1[w][lane] = r1;
+      s2[w][lane] = r2;
       sg[w][lane] = g;
+      hit = ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
     }
+    uint32_t mask = __ballot_sync(0xffffffffu, hit);
     __syncwarp();
-    for (int j = bend - bstart - 1; j >= 0; j--) {
+    while (mask) {  // back to front
+      const int j = 31 - __clz(mask);
+      mask ^= 1u << j;
       const float4 q0 = s0[w][j];
       const float4 q2 = s2[w][j];
-      if (!box_hits(q0, q2, geo.wx0, geo.wx1, geo.wy0, geo.wy1)) continue;
       const float4 q1 = s1[w][j];
       const uint32_t idx = (uint32_t)(bstart + j);
       const float rgb[3] = {q1.z, q1.w, q2.x};
@@ -340,7 +412,8 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
       for (int k = 0; k < PPT; k++)
         any |= bwd_pair(idx < nl[k], q0, q1, rgb, a0, a1, __fsub_rn(q0.y, fpy + (float)k), dx, dx2, cA2dx, cBdx, T[k],
                         dCS[k], dC[k], bgd[k], acc);
-      if (__any_sync(0xffffffffu, any)) push_grad(a.g2d, gplane, (int64_t)v * a.stride + sg[w][j], acc, lane);
+      const uint32_t contrib = __ballot_sync(0xffffffffu, any);
+      if (contrib) push_grad(a.g2d, gplane, (int64_t)v * a.stride + sg[w][j], acc, lane, contrib, a.direct_max);
     }
   }
 }

@@ -51,14 +51,27 @@ class gs_params(ctypes.Structure):
 class gs_adam_hp(ctypes.Structure):
     _fields_ = [("lr_mean", ctypes.c_float), ("lr_scale", ctypes.c_float), ("lr_quat", ctypes.c_float),
                 ("lr_opacity", ctypes.c_float), ("lr_sh_dc", ctypes.c_float), ("lr_sh_rest", ctypes.c_float),
-                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("flags", ctypes.c_int32)]
+
+
+GS_ADAM_SQRT_BATCH_LR = 1
+
+
+def adam_hp_struct(hp: dict) -> gs_adam_hp:
+    """hp: lr_mean, lr_scale, lr_quat, lr_opacity, lr_sh_dc, lr_sh_rest, and
+    optionally beta1, beta2, eps and sqrt_batch_lr (scale the rates by
+    sqrt(views per batch))."""
+    return gs_adam_hp(hp["lr_mean"], hp["lr_scale"], hp["lr_quat"], hp["lr_opacity"], hp["lr_sh_dc"],
+                      hp["lr_sh_rest"], hp.get("beta1", 0.9), hp.get("beta2", 0.999), hp.get("eps", 1e-15),
+                      GS_ADAM_SQRT_BATCH_LR if hp.get("sqrt_batch_lr", False) else 0)
 
 
 class gs_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
-GS_OPT_RASTER_FWD, GS_OPT_RASTER_BWD = 0, 1
+GS_OPT_RASTER_FWD, GS_OPT_RASTER_BWD, GS_OPT_BWD_DIRECT = 0, 1, 2
 
 class gs_serve_cfg(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch_views", ctypes.c_int32), ("max_queue", ctypes.c_int32),
@@ -66,7 +79,7 @@ class gs_serve_cfg(ctypes.Structure):
                 ("output_pool_bytes", ctypes.c_int64)]
 
 
-EXPORTS = ["gs_train_graph_capture", "gs_train_graph_launch", "gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
+EXPORTS = ["gs_train_graph_capture", "gs_train_graph_launch", "gs_train_graph_launch_host", "gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
            "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
            "gs_get_counts"]
@@ -99,6 +112,7 @@ def load(path: str | None = None):
     L.gs_train_graph_capture.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), P(gs_params), P(gs_adam_hp),
                                          P(gs_camera), i32, vp, vp, vp, vp]
     L.gs_train_graph_launch.argtypes = [vp, P(gs_camera), i32, vp, i64]
+    L.gs_train_graph_launch_host.argtypes = [vp, P(gs_camera), i32, vp, i64, vp]
     L.gs_serve_create.argtypes = [P(vp), ctypes.c_int, P(gs_params), P(gs_serve_cfg)]
     L.gs_serve_destroy.argtypes = [vp]
     L.gs_serve_destroy.restype = None
@@ -219,8 +233,7 @@ class Context:
     def gs_adam(self, p, g, m, v, n, deg, hp: dict, step: int):
         self._bind_stream()
         sp, sg, sm, sv = (params_struct(t, n, deg) for t in (p, g, m, v))
-        h = gs_adam_hp(hp["lr_mean"], hp["lr_scale"], hp["lr_quat"], hp["lr_opacity"], hp["lr_sh_dc"],
-                       hp["lr_sh_rest"], hp.get("beta1", 0.9), hp.get("beta2", 0.999), hp.get("eps", 1e-15))
+        h = adam_hp_struct(hp)
         self._check(self.L.gs_adam(self.h, ctypes.byref(sp), ctypes.byref(sg), ctypes.byref(sm), ctypes.byref(sv),
                                    ctypes.byref(h), int(step)), "gs_adam")
 
@@ -229,8 +242,7 @@ class Context:
         tensor alive and in place while the graph is used."""
         self._bind_stream()
         sp, sg, sm, sv = (params_struct(t, n, deg) for t in (p, g, m, v))
-        h = gs_adam_hp(hp["lr_mean"], hp["lr_scale"], hp["lr_quat"], hp["lr_opacity"], hp["lr_sh_dc"],
-                       hp["lr_sh_rest"], hp.get("beta1", 0.9), hp.get("beta2", 0.999), hp.get("eps", 1e-15))
+        h = adam_hp_struct(hp)
         arr = (gs_camera * len(cams))(*[camera_struct(c) for c in cams])
         self._graph_keep = (sp, sg, sm, sv, h, p, g, m, v, targets, images, dimages, loss)
         self._check(self.L.gs_train_graph_capture(
@@ -243,6 +255,21 @@ class Context:
         arr = (gs_camera * len(cams))(*[camera_struct(c) for c in cams])
         self._check(self.L.gs_train_graph_launch(self.h, arr, len(cams), ctypes.c_void_p(targets.data_ptr()),
                                                  int(step)), "gs_train_graph_launch")
+
+    def gs_train_graph_launch_host(self, cams, host_targets: torch.Tensor, step: int, host_loss=None):
+        """Replay with targets in host memory (pinned for overlap) and the loss
+        read back into `host_loss` (a 1-element CPU float32 tensor, or None).
+        Keep both alive and unchanged until gs_sync."""
+        self._bind_stream()
+        assert host_targets.device.type == "cpu" and host_targets.dtype == torch.float32
+        assert host_targets.is_contiguous()
+        lp = None
+        if host_loss is not None:
+            assert host_loss.device.type == "cpu" and host_loss.dtype == torch.float32
+            lp = ctypes.c_void_p(host_loss.data_ptr())
+        arr = (gs_camera * len(cams))(*[camera_struct(c) for c in cams])
+        self._check(self.L.gs_train_graph_launch_host(self.h, arr, len(cams), ctypes.c_void_p(host_targets.data_ptr()),
+                                                      int(step), lp), "gs_train_graph_launch_host")
 
     def gs_sync(self):
         self._check(self.L.gs_sync(self.h), "gs_sync")

@@ -83,6 +83,49 @@ def test_graph_step_matches_call_by_call():
     gctx.close()
 
 
+def test_graph_host_targets_match_device_targets():
+    """gs_train_graph_launch_host (targets uploaded from pinned host memory on
+    the copy stream, loss read back) against device-target replays."""
+    ref, cur, cams = setup()
+    n, deg = cur["n"], cur["deg"]
+    plain = gs.Context(0)
+    targets = render(plain, ref, cams)
+    inst, _, _ = plain.gs_get_counts()
+    _, total = gs.image_offsets(cams)
+    host_t = targets.cpu().pin_memory()
+    runs = []
+    for host in (False, True):
+        st = State(cur)
+        img, d = torch.empty(total, device="cuda"), torch.empty(total, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        g = gs.Context(0, instance_capacity=2 * inst + 1024)
+        g.gs_train_graph_capture(st.p, st.g, st.m, st.v, n, deg, HP, cams, targets, img, d, loss)
+        losses = []
+        for step in range(1, 5):
+            if host:
+                lh = torch.full((1,), float("nan"), pin_memory=True)
+                g.gs_train_graph_launch_host(cams, host_t, step, lh)
+                g.gs_sync()
+                losses.append(float(lh))
+            else:
+                g.gs_train_graph_launch(cams, targets, step)
+                g.gs_sync()
+                losses.append(float(loss.item()))
+            if step == 1:
+                first_img = img.clone()
+        torch.cuda.synchronize()
+        runs.append((st, losses, first_img, g))
+    (a, la, ia, ga), (b, lb, ib, gb) = runs
+    assert torch.equal(ia, ib)
+    assert abs(la[0] - lb[0]) <= 1e-6 * la[0]
+    for x, y in zip(la, lb):
+        assert abs(x - y) <= 1e-4 * x
+    assert (a.p - b.p).abs().max().item() <= 4 * 5e-2
+    for g in (ga, gb):
+        g.close()
+    plain.close()
+
+
 def test_graph_capacity_overflow_is_reported():
     ref, cur, cams = setup()
     n, deg = cur["n"], cur["deg"]

@@ -34,6 +34,10 @@ SCENES = {
     "random_deg3_mixed": lambda: (inputs.random_scene(20000, 3, 11, extent=0.8), mixed_cams()),
     "random_deg1_one": lambda: (inputs.random_scene(5001, 1, 12, extent=0.6, log_scale=(-4, -1.5)),
                                 [inputs.pinhole(inputs.look_at((0.1, 0.2, 2.4)), 130, 70)]),
+    # strongly anisotropic splats at random angles: the per-warp ellipse cull
+    # is tested where the ellipse and its bounding box differ most
+    "needles_deg0": lambda: (inputs.random_scene(4000, 0, 13, extent=0.7, log_scale=(-6.0, -1.5)),
+                             [inputs.pinhole(inputs.look_at((1.9, -1.6, 1.3)), 192, 160)]),
 }
 
 
@@ -194,6 +198,36 @@ def test_options_reject_bad_values(ctx):
         ctx.gs_set_option(99, 1)
     assert ctx.gs_get_option(gs.GS_OPT_RASTER_FWD) in VARIANTS
     assert ctx.gs_get_option(gs.GS_OPT_RASTER_BWD) in VARIANTS
+    with pytest.raises(gs.GsError):
+        ctx.gs_set_option(gs.GS_OPT_BWD_DIRECT, 33)
+    with pytest.raises(gs.GsError):
+        ctx.gs_set_option(gs.GS_OPT_BWD_DIRECT, -1)
+    assert 0 <= ctx.gs_get_option(gs.GS_OPT_BWD_DIRECT) <= 32
+
+
+@pytest.mark.parametrize("direct", [0, 3, 32])
+@pytest.mark.parametrize("bwd", [2, 8])
+def test_gradient_direct_atomics_match_oracle(ctx, oracle, bwd, direct):
+    """Backward with the per-lane atomic path never (0), for up to 3
+    contributing lanes, and always (32)."""
+    scene, cams = SCENES["random_deg3_mixed"]()
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, 2)
+    ctx.gs_set_option(gs.GS_OPT_RASTER_BWD, bwd)
+    ctx.gs_set_option(gs.GS_OPT_BWD_DIRECT, direct)
+    p, _ = run_forward(ctx, scene, cams)
+    rng = np.random.default_rng(8)
+    dimgs = [rng.normal(size=(3, c["height"], c["width"])) * (~oracle.render(scene, c)[2]) for c in cams]
+    grads = torch.zeros_like(p)
+    ctx.gs_raster_bwd(p, scene["n"], scene["deg"], to_dev_images(dimgs), grads)
+    ctx.gs_sync()
+    ctx.gs_set_option(gs.GS_OPT_BWD_DIRECT, 2)
+    ref = oracle.render_grad(scene, cams, dimgs)
+    n = scene["n"]
+    keep = np.ones(n, bool)
+    for cam in cams:
+        keep &= (oracle.gaussian_flags(scene, cam) & oracle.G_MARG_ANY_GRAD) == 0
+    g = grads.cpu().numpy().astype(np.float64)
+    assert rel_l2(g[:, :n][:, keep], ref[:, :n][:, keep]) <= 1e-3
 
 
 def test_batched_forward_equals_single_views(ctx):
@@ -262,6 +296,30 @@ def test_adam_matches_oracle(ctx, oracle):
     ctx.gs_sync()
     np.testing.assert_allclose(p.cpu().numpy(), p64, rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(m.cpu().numpy(), m64, rtol=1e-5, atol=1e-7)
+
+
+def test_adam_sqrt_batch_lr_scaling(ctx, oracle):
+    """The optional sqrt(B) learning-rate scaling of batched training: after a
+    3-view projection the step equals plain Adam with the rates times sqrt 3."""
+    rng = np.random.default_rng(6)
+    scene = inputs.random_scene(777, 1, 3)
+    P, stride = scene["params"].shape
+    n = scene["n"]
+    p = torch.from_numpy(scene["params"]).cuda()
+    ctx.gs_project(p, n, 1, mixed_cams())
+    hp = dict(lr_mean=1e-3, lr_scale=2e-3, lr_quat=3e-3, lr_opacity=4e-2, lr_sh_dc=5e-3, lr_sh_rest=6e-4,
+              sqrt_batch_lr=True)
+    lr_planes = np.sqrt(3.0) * np.array([hp["lr_mean"]] * 3 + [hp["lr_scale"]] * 3 + [hp["lr_quat"]] * 4
+                                        + [hp["lr_opacity"]] + [hp["lr_sh_dc"]] * 3 + [hp["lr_sh_rest"]] * (P - 14))
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    p64, m64, v64 = scene["params"].astype(np.float64), np.zeros((P, stride)), np.zeros((P, stride))
+    for step in (1, 2):
+        g = rng.normal(size=(P, stride)).astype(np.float32)
+        g[:, n:] = 0
+        ctx.gs_adam(p, torch.from_numpy(g).cuda(), m, v, n, 1, hp, step)
+        oracle.adam(p64, g.astype(np.float64), m64, v64, lr_planes, step)
+    ctx.gs_sync()
+    np.testing.assert_allclose(p.cpu().numpy(), p64, rtol=1e-6, atol=1e-7)
 
 
 def test_invalid_arguments_are_rejected(ctx):
