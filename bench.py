@@ -237,19 +237,21 @@ RASTER_OPS_FWD = 24   # FP32 ops per evaluated (pixel, Gaussian) pair, forward
 RASTER_OPS_BWD = 60   # FP32 ops per evaluated pair, backward
 
 
-def algorithmic_work(name, n, P, B, I, pairs, pixels, passes):
+def algorithmic_work(name, n, P, B, I, pairs, pixels):
+    """(bound, work per launch scope): bytes for the HBM-bound kernels, FP32
+    operations for the compositing kernels.  I = tile instances."""
     if name == "project_fwd":
         return "hbm", n * (4 * P + B * 60.0)
     if name == "project_bwd":
         return "hbm", n * (8 * P + B * 36.0)
     if name == "adam":
         return "hbm", 28.0 * P * n
-    if name == "onesweep_pass":
-        return "hbm", 24.0 * I
-    if name == "digit_histogram":
-        return "hbm", 8.0 * I
     if name == "duplicate":
         return "hbm", n * B * 4.0 + 12.0 * I
+    if name == "digit_histogram":
+        return "hbm", 8.0 * I
+    if name == "onesweep_pass":
+        return "hbm", 24.0 * I
     if name == "tile_ranges":
         return "hbm", 8.0 * I
     if name == "l1_loss":
@@ -385,8 +387,23 @@ def gpu_arm(args):
     per_kernel = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
                               "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in kstats), 1e-9), 4)}
                   for k in kstats}
-    passes = next((k["launches"] for k in kstats if k["name"] == "onesweep_pass"), 0) / max(args.steps, 1)
-    kind, work = algorithmic_work(dom["name"], tr.n, P, B, inst, pairs, pixels, passes)
+    ctrl = ctx.gs_get_buffer(gs.GS_BUF_SORT_CTRL).cpu().numpy()
+    executed = {"onesweep_pass": int(sum((ctrl[p] & 2) == 0 for p in range(ctrl.size - 1)))}
+    peak_hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    for k in kstats:
+        kk, w = algorithmic_work(k["name"], tr.n, P, B, inst, pairs, pixels)
+        if kk is None or k["total_ms"] <= 0:
+            continue
+        runs = executed.get(k["name"], 1) * args.steps  # one launch scope per step, sort passes as executed
+        rate = w * runs / (k["total_ms"] / 1e3)
+        e = per_kernel[k["name"]]
+        if kk == "hbm":
+            e["GB_s"] = round(rate / 1e9, 1)
+            e["frac_hbm"] = round(rate / 1e9 / peak_hbm, 3)
+        else:
+            e["TFLOP_s"] = round(rate / 1e12, 2)
+    kind, work = algorithmic_work(dom["name"], tr.n, P, B, inst, pairs, pixels)
     avg_ms = dom["total_ms"] / max(dom["launches"], 1)
     peaks = {}
     try:
@@ -465,7 +482,8 @@ def gpu_arm(args):
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
         "graph": "each timed step is one CUDA-graph launch of the whole step; per-kernel times and the roofline "
                  "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
-        "instances_per_step": int(inst), "pairs_per_step": pairs, "kernels": per_kernel,
+        "instances_per_step": int(inst), "pairs_per_step": pairs, "sort_passes_executed": executed,
+        "kernels": per_kernel,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
         "memory": memory,
     }

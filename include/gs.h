@@ -325,7 +325,10 @@ typedef enum {
   GS_BUF_TFINAL = 6, /* float [pixels]: transmittance after the last contributor */
   GS_BUF_NLAST = 7,  /* uint32 [pixels]: 1 + list position of the last contributor */
   GS_BUF_G2D = 8,    /* float [9][B][N] planes: dL/d(mu_x, mu_y, A, B, C, opacity, r, g, b) */
-  GS_BUF_REC3 = 9    /* int2 [B][N]: radius, tiles touched (0: culled) */
+  GS_BUF_REC3 = 9,   /* int2 [B][N]: radius, tiles touched (0: culled) */
+  GS_BUF_SORT_CTRL = 10 /* uint32 [npass + 1]: control word of each sort pass; bit 1
+                        set = pass skipped (its digit is the same for every key),
+                        bit 0 = source buffer */
 } gs_buffer;
 
 /* *ptr = device pointer of the buffer, *count = number of elements (of the

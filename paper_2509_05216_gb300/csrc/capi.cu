@@ -58,6 +58,7 @@ struct gs_ctx {
   int raster_fwd = 2;  // compositing variants (pixels per thread; 8 = one warp per tile)
   int raster_bwd = 2;
   int bwd_direct = 2;  // per-lane gradient atomics when at most this many lanes contribute
+  int sort_passes = 0;  // LSD passes of the last sort
 
   // last batch
   int B = 0, deg = 0;
@@ -438,6 +439,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   int bin_bits = 0;
   while (((int64_t)1 << bin_bits) < c->bins) bin_bits++;
   const int npass = (32 + bin_bits + 7) / 8;  // the 32 depth bits and the bin bits
+  c->sort_passes = npass;
   const size_t lb = sort_lookback_bytes(cap);
   GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
   GS_TRY(ensure(c, c->hist_scan, sizeof(uint32_t) * (8 * 256 + 16)));
@@ -665,6 +667,11 @@ gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
     case GS_BUF_TFINAL: if (!c->rastered) return GS_ESTATE; *ptr = c->tfinal.p; *count = c->pixels; break;
     case GS_BUF_NLAST: if (!c->rastered) return GS_ESTATE; *ptr = c->nlast.p; *count = c->pixels; break;
     case GS_BUF_G2D: if (!c->g2d.p) return GS_ESTATE; *ptr = c->g2d.p; *count = 9 * bn; break;
+    case GS_BUF_SORT_CTRL:
+      if (!c->sorted) return GS_ESTATE;
+      *ptr = P<uint32_t>(c->hist_scan) + 8 * 256;
+      *count = c->sort_passes + 1;
+      break;
     default: return fail(c, GS_EINVAL, "unknown buffer %d", which);
   }
   return GS_OK;

@@ -211,6 +211,85 @@ __device__ __forceinline__ void fwd_pair(const float4& q1, float blue, float a0,
   last = acc ? idx : last;
 }
 
+// ---------------------------------------------------------------- pixel pairs
+//
+// With two or more pixels per thread, the pixels of a pair (rows k and k + 1
+// of one column: same dx, different dy) go through the packed FP32x2
+// instructions of sm_100-class GPUs, one instruction for both.  Each element
+// is rounded exactly like the scalar operation it replaces (dy = mu_y - y is
+// computed as mu_y + (-y), which IEEE defines identically), so every skip and
+// stop decision equals the one-pixel variant's.
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// Forward of one pixel pair (bits bitx, bitx << 1 of `done`).
+__device__ __forceinline__ void fwd_pair2(const float2& cC, const float2& a1, const float2& a0, const float2& op,
+                                          const float2& r, const float2& g, const float2& b, float2 dy,
+                                          uint32_t bitx, uint32_t idx, uint32_t& done, float2& T, float2 (&C)[3],
+                                          uint32_t& lastx, uint32_t& lasty) {
+  const float2 p2 = __ffma2_rn(__ffma2_rn(cC, dy, a1), dy, a0);
+  const float2 raw = __fmul2_rn(op, make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
+  const float ax = fminf(kAlphaClamp, raw.x), ay = fminf(kAlphaClamp, raw.y);
+  const uint32_t bity = bitx << 1;
+  const bool okx = !(done & bitx) && !(p2.x > 0.f) && !(ax < kAlphaSkip);
+  const bool oky = !(done & bity) && !(p2.y > 0.f) && !(ay < kAlphaSkip);
+  const float2 Tn = __fmul2_rn(T, __fadd2_rn(bc2(1.f), make_float2(-ax, -ay)));
+  const bool stx = okx && Tn.x < kTStop, sty = oky && Tn.y < kTStop;
+  done |= (stx ? bitx : 0u) | (sty ? bity : 0u);
+  const bool accx = okx && !stx, accy = oky && !sty;
+  const float2 aT = __fmul2_rn(make_float2(ax, ay), T);
+  const float2 w = make_float2(accx ? aT.x : 0.f, accy ? aT.y : 0.f);
+  C[0] = __ffma2_rn(r, w, C[0]);
+  C[1] = __ffma2_rn(g, w, C[1]);
+  C[2] = __ffma2_rn(b, w, C[2]);
+  T = make_float2(accx ? Tn.x : T.x, accy ? Tn.y : T.y);
+  lastx = accx ? idx : lastx;
+  lasty = accy ? idx : lasty;
+}
+
+// Backward of one pixel pair.  Per (thread, Gaussian) it accumulates the
+// colour and opacity gradients and three moments of dL/dp2 over the pixels
+// (S0 = sum dp, S1 = sum dp dy, S2 = sum dp dy^2), from which the mean and
+// conic gradients follow once per Gaussian.  Returns whether a pixel of the
+// pair contributed.
+__device__ __forceinline__ bool bwd_pair2(bool livex, bool livey, const float2& cC, const float2& a1,
+                                          const float2& a0, const float2& op, const float2& r, const float2& g,
+                                          const float2& b, float2 dy, float2& T, float2& dCS, const float2 (&dC)[3],
+                                          const float2& bgd, float2 (&racc)[3], float2& oacc, float2& S0,
+                                          float2& S1, float2& S2) {
+  const float2 p2 = __ffma2_rn(__ffma2_rn(cC, dy, a1), dy, a0);
+  const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
+  const float2 raw = __fmul2_rn(op, G);
+  const float ax = fminf(kAlphaClamp, raw.x), ay = fminf(kAlphaClamp, raw.y);
+  const bool onx = livex && !(p2.x > 0.f) && !(ax < kAlphaSkip);
+  const bool ony = livey && !(p2.y > 0.f) && !(ay < kAlphaSkip);
+  const float2 ae = make_float2(onx ? ax : 0.f, ony ? ay : 0.f);
+  const float2 om = __fadd2_rn(bc2(1.f), make_float2(-ae.x, -ae.y));
+  // 1 - ae is in [0.01, 1]: the approximate reciprocal (relative error
+  // below 2^-22) keeps the recovered T within FP32 rounding of the division
+  const float2 inv = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+  const float2 Ti = __fmul2_rn(T, inv);
+  const float2 w = __fmul2_rn(ae, Ti);
+  const float2 dcr = __ffma2_rn(dC[2], b, __ffma2_rn(dC[1], g, __fmul2_rn(dC[0], r)));
+  // dL/dalpha = T_i (dC . rgb) - (bg T_final + S) . dC / (1 - alpha)
+  const float2 dLda = __ffma2_rn(Ti, dcr, __fmul2_rn(make_float2(-inv.x, -inv.y), __fadd2_rn(bgd, dCS)));
+  racc[0] = __ffma2_rn(dC[0], w, racc[0]);
+  racc[1] = __ffma2_rn(dC[1], w, racc[1]);
+  racc[2] = __ffma2_rn(dC[2], w, racc[2]);
+  dCS = __ffma2_rn(w, dcr, dCS);
+  T = Ti;
+  // zero through a clamped alpha (opacity G > 0.99)
+  const float2 dLg = make_float2((onx && raw.x <= kAlphaClamp) ? dLda.x : 0.f,
+                                 (ony && raw.y <= kAlphaClamp) ? dLda.y : 0.f);
+  oacc = __ffma2_rn(dLg, G, oacc);
+  const float2 dp = __fmul2_rn(dLg, make_float2(ax, ay));  // dL/dpower
+  S0 = __fadd2_rn(S0, dp);
+  const float2 t = __fmul2_rn(dp, dy);
+  S1 = __fadd2_rn(S1, t);
+  S2 = __ffma2_rn(t, dy, S2);
+  return onx || ony;
+}
+
 // ---------------------------------------------------------------- launch shapes
 //
 // PPT = pixels per thread.  A block holds TPB tiles; a warp owns a WR x HR
@@ -267,6 +346,7 @@ template <int PPT>
 __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArgs a, int64_t bins) {
   using G = Geo<PPT>;
   constexpr int NWB = G::NW * G::TPB;  // warps per block
+  constexpr int NP = PPT / 2;          // pixel pairs per thread
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   G geo;
@@ -277,7 +357,10 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   const int n = (int)(rg.y - rg.x);
   const uint32_t* __restrict__ vals = *a.vals;
 
+  // PPT == 1: scalar state; otherwise pixel pairs (pixel k = pair k / 2,
+  // element k % 2)
   float T[PPT], C[PPT][3];
+  float2 T2[NP > 0 ? NP : 1], C2[NP > 0 ? NP : 1][3], nfy[NP > 0 ? NP : 1];
   uint32_t last[PPT];
   uint32_t done = 0;
 #pragma unroll
@@ -286,6 +369,12 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     C[k][0] = C[k][1] = C[k][2] = 0.f;
     last[k] = 0;
     if (!(px < V.W && py0 + k < V.H)) done |= 1u << k;
+  }
+#pragma unroll
+  for (int j = 0; j < NP; j++) {
+    T2[j] = bc2(1.f);
+    C2[j][0] = C2[j][1] = C2[j][2] = bc2(0.f);
+    nfy[j] = make_float2(-((float)py0 + (float)(2 * j)), -((float)py0 + (float)(2 * j + 1)));
   }
   const uint32_t all_done = (1u << PPT) - 1u;
   const float fpx = (float)px, fpy = (float)py0;
@@ -314,10 +403,31 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
       const float dx = __fsub_rn(q0.x, fpx);
       const float a0 = __fmul_rn(q0.z, __fmul_rn(dx, dx));
       const float a1 = __fmul_rn(q0.w, dx);
+      const uint32_t idx = (uint32_t)(b0 + j + 1);
+      if constexpr (NP == 0) {
 #pragma unroll
-      for (int k = 0; k < PPT; k++)
-        fwd_pair(q1, q2.x, a0, a1, __fsub_rn(q0.y, fpy + (float)k), 1u << k, (uint32_t)(b0 + j + 1), done, T[k],
-                 C[k], last[k]);
+        for (int k = 0; k < PPT; k++)
+          fwd_pair(q1, q2.x, a0, a1, __fsub_rn(q0.y, fpy + (float)k), 1u << k, idx, done, T[k], C[k], last[k]);
+      } else {
+        const float2 cC = bc2(q1.x), A1 = bc2(a1), A0 = bc2(a0), op = bc2(q1.y);
+        const float2 r = bc2(q1.z), g = bc2(q1.w), b = bc2(q2.x), qy = bc2(q0.y);
+#pragma unroll
+        for (int jp = 0; jp < NP; jp++)
+          fwd_pair2(cC, A1, A0, op, r, g, b, __fadd2_rn(qy, nfy[jp]), 1u << (2 * jp), idx, done, T2[jp], C2[jp],
+                    last[2 * jp], last[2 * jp + 1]);
+      }
+    }
+  }
+  if constexpr (NP > 0) {
+#pragma unroll
+    for (int jp = 0; jp < NP; jp++) {
+      T[2 * jp] = T2[jp].x;
+      T[2 * jp + 1] = T2[jp].y;
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        C[2 * jp][c] = C2[jp][c].x;
+        C[2 * jp + 1][c] = C2[jp][c].y;
+      }
     }
   }
   const int64_t plane = (int64_t)V.W * V.H;
@@ -339,6 +449,8 @@ template <int PPT>
 __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArgs a, int64_t bins) {
   using G = Geo<PPT>;
   constexpr int NWB = G::NW * G::TPB;
+  constexpr int NP = PPT / 2;  // pixel pairs per thread (0: the scalar one-pixel path)
+  constexpr int NS = NP > 0 ? NP : 1;
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
   __shared__ uint32_t sg[NWB][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -369,6 +481,17 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
     bgd[k] = T[k] * (dC[k][0] * V.bg[0] + dC[k][1] * V.bg[1] + dC[k][2] * V.bg[2]);
     mymax = max(mymax, nl[k]);
   }
+  // the same state as pixel pairs
+  float2 T2[NS], dC2[NS][3], dCS2[NS], bgd2[NS], nfy[NS];
+#pragma unroll
+  for (int j = 0; j < NP; j++) {
+    T2[j] = make_float2(T[2 * j], T[2 * j + 1]);
+#pragma unroll
+    for (int c = 0; c < 3; c++) dC2[j][c] = make_float2(dC[2 * j][c], dC[2 * j + 1][c]);
+    dCS2[j] = bc2(0.f);
+    bgd2[j] = make_float2(bgd[2 * j], bgd[2 * j + 1]);
+    nfy[j] = make_float2(-((float)py0 + (float)(2 * j)), -((float)py0 + (float)(2 * j + 1)));
+  }
   // this warp only walks the entries before its pixels' last contributors
   const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
   const float fpx = (float)px, fpy = (float)py0;
@@ -397,7 +520,6 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
       const float4 q2 = s2[w][j];
       const float4 q1 = s1[w][j];
       const uint32_t idx = (uint32_t)(bstart + j);
-      const float rgb[3] = {q1.z, q1.w, q2.x};
       const float dx = __fsub_rn(q0.x, fpx);
       const float dx2 = __fmul_rn(dx, dx);
       const float a0 = __fmul_rn(q0.z, dx2);
@@ -408,10 +530,32 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
 #pragma unroll
       for (int q = 0; q < 16; q++) acc[q] = 0.f;
       bool any = false;
+      if constexpr (NP == 0) {
+        const float rgb[3] = {q1.z, q1.w, q2.x};
 #pragma unroll
-      for (int k = 0; k < PPT; k++)
-        any |= bwd_pair(idx < nl[k], q0, q1, rgb, a0, a1, __fsub_rn(q0.y, fpy + (float)k), dx, dx2, cA2dx, cBdx, T[k],
-                        dCS[k], dC[k], bgd[k], acc);
+        for (int k = 0; k < PPT; k++)
+          any |= bwd_pair(idx < nl[k], q0, q1, rgb, a0, a1, __fsub_rn(q0.y, fpy + (float)k), dx, dx2, cA2dx, cBdx,
+                          T[k], dCS[k], dC[k], bgd[k], acc);
+      } else {
+        const float2 cC = bc2(q1.x), A1 = bc2(a1), A0 = bc2(a0), op = bc2(q1.y);
+        const float2 r = bc2(q1.z), g = bc2(q1.w), b = bc2(q2.x), qy = bc2(q0.y);
+        float2 racc[3] = {bc2(0.f), bc2(0.f), bc2(0.f)}, oacc = bc2(0.f);
+        float2 S0 = bc2(0.f), S1 = bc2(0.f), S2 = bc2(0.f);
+#pragma unroll
+        for (int jp = 0; jp < NP; jp++)
+          any |= bwd_pair2(idx < nl[2 * jp], idx < nl[2 * jp + 1], cC, A1, A0, op, r, g, b,
+                           __fadd2_rn(qy, nfy[jp]), T2[jp], dCS2[jp], dC2[jp], bgd2[jp], racc, oacc, S0, S1, S2);
+        // mean and conic gradients of p2 from the moments of dL/dp2
+        const float m0 = S0.x + S0.y, m1 = S1.x + S1.y;
+        acc[0] = fmaf(q0.w, m1, cA2dx * m0);        // sum dp (cB dy + 2 cA dx)
+        acc[1] = fmaf(2.f * q1.x, m1, cBdx * m0);   // sum dp (2 cC dy + cB dx)
+        acc[2] = dx2 * m0;
+        acc[3] = dx * m1;
+        acc[4] = S2.x + S2.y;
+        acc[5] = oacc.x + oacc.y;
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[6 + c] = racc[c].x + racc[c].y;
+      }
       const uint32_t contrib = __ballot_sync(0xffffffffu, any);
       if (contrib) push_grad(a.g2d, gplane, (int64_t)v * a.stride + sg[w][j], acc, lane, contrib, a.direct_max);
     }

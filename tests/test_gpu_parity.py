@@ -113,6 +113,35 @@ def test_binning_is_bit_exact(ctx, name):
     assert np.array_equal(gk, keys)
     assert np.array_equal(gv, vals)
     assert np.array_equal(gr, ranges)
+    # the sort ran only the passes whose digit varies (the depth exponent byte
+    # is one digit for these scenes and is skipped)
+    ctrl = ctx.gs_get_buffer(gs.GS_BUF_SORT_CTRL).cpu().numpy().astype(np.int64)
+    npass = ctrl.size - 1
+    digits = [(keys >> np.uint64(8 * p)) & np.uint64(255) for p in range(npass)]
+    for p in range(npass):
+        assert bool(ctrl[p] & 2) == (keys.size == 0 or np.unique(digits[p]).size == 1)
+
+
+def test_binning_with_empty_and_uneven_views(ctx):
+    """Views that see nothing (first, middle, last) among views of different
+    sizes: the per-view segments of both sorts stay aligned."""
+    scene = inputs.random_scene(9000, 2, 14, extent=0.7)
+    away = inputs.pinhole(inputs.look_at((0.0, 0.0, 3.0), target=(0.0, 0.0, 6.0), up=(0.0, 1.0, 0.0)), 64, 48)
+    cams = [away, mixed_cams()[0], away, mixed_cams()[2], inputs.pinhole(inputs.look_at((2.2, -1.0, 0.4)), 33, 17),
+            away]
+    run_forward(ctx, scene, cams)
+    n, stride = scene["n"], scene["params"].shape[1]
+    r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
+    r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+    r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
+    keys, vals, ranges, per_view = expected_binning(r0, r2, r3, cams, n, stride)
+    assert per_view[0] == per_view[2] == per_view[5] == 0 and per_view[1] > 0 and per_view[3] > 0
+    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)
+    gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64)
+    gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
+    assert np.array_equal(gk, keys)
+    assert np.array_equal(gv, vals)
+    assert np.array_equal(gr, ranges)
 
 
 VARIANTS = [1, 2, 4, 8]
