@@ -128,11 +128,15 @@ typedef enum {
                             tile.  All variants give the same result up to
                             FP32 rounding. */
   GS_OPT_RASTER_BWD = 1, /* backward compositing kernel, same values */
-  GS_OPT_BWD_DIRECT = 2  /* backward: a warp whose pixels meet a Gaussian in at
+  GS_OPT_BWD_DIRECT = 2, /* backward: a warp whose pixels meet a Gaussian in at
                             most this many lanes (0..32, default 2) adds the
                             lanes' gradients with per-lane atomics instead of
                             a warp reduction.  Same result up to FP32
                             summation order. */
+  GS_OPT_SORT_ITEMS = 3  /* keys per thread of a radix-sort partition: 12, 16
+                            (default), 20 or 24 (partitions of 256 x items
+                            keys).  Same result.  Fixed once a training graph
+                            is captured (GS_ESTATE). */
 } gs_option;
 
 /* Set / read an option.  Errors: GS_EINVAL (unknown option, bad value). */

@@ -16,7 +16,7 @@ import torch
 from . import gs
 
 CANDIDATES = {gs.GS_OPT_RASTER_FWD: [2, 8, 4, 1], gs.GS_OPT_RASTER_BWD: [2, 4, 8, 1],
-              gs.GS_OPT_BWD_DIRECT: [2, 0, 4, 8]}
+              gs.GS_OPT_BWD_DIRECT: [2, 0, 4, 8], gs.GS_OPT_SORT_ITEMS: [16, 12, 20, 24]}
 
 
 def workload_key(n, cams, batch):

@@ -162,8 +162,8 @@ void launch_duplicate(const DuplicateArgs& a, cudaStream_t s) {
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // keys per partition
+// keys per thread (12, 16, 20 or 24; a context option, autotuned): a
+// partition holds 256 x items keys
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kFlagAggregate = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
@@ -171,8 +171,13 @@ constexpr uint32_t kValueMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 20;  // look-back rounds before giving up (about a second)
 constexpr int kLookWindow = 16;       // statuses read per look-back round
 
-size_t sort_lookback_bytes(int64_t count) {
-  const int64_t parts = (count + kSortTile - 1) / kSortTile;
+int64_t sort_partitions(int64_t count, int items) {
+  const int64_t tile = (int64_t)kSortThreads * items;
+  return (count + tile - 1) / tile;
+}
+
+size_t sort_lookback_bytes(int64_t count, int items) {
+  const int64_t parts = sort_partitions(count, items);
   return (size_t)(parts > 0 ? parts : 1) * kRadix * sizeof(uint32_t);
 }
 
@@ -210,28 +215,35 @@ constexpr uint32_t kCtrlParity = 1u, kCtrlTrivial = 2u;
 // flight before ranking); keys and then values go through one shared buffer,
 // which keeps the block at 46 KB of shared memory and 64 registers per thread
 // (four blocks per SM).  hist_pass: exclusive digit offsets of this pass.
+template <int ITEMS>
 struct SortSmem {
+  static constexpr int kTile = kSortThreads * ITEMS;
   uint32_t warp_hist[kSortWarps][kRadix];  // per-warp digit counts -> offsets
   uint32_t digit_start[kRadix];            // exclusive scan of the tile's digit counts
   uint32_t global_base[kRadix];            // global destination of the digit's first key
   uint32_t part;
   int timed_out;
-  uint64_t buf[kSortTile];                 // keys, then values, in tile-sorted order
-  uint8_t dig[kSortTile];                  // digit of each tile-sorted position
+  uint64_t buf[kTile];                     // keys, then values, in tile-sorted order
+  uint8_t dig[kTile];                      // digit of each tile-sorted position
 };
 
-__global__ void __launch_bounds__(kSortThreads, 4) onesweep_pass_kernel(SortArgs a, int pass) {
+template <int ITEMS, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel(SortArgs a, int pass) {
+  constexpr int kSortItems = ITEMS;
+  constexpr int kSortTile = kSortThreads * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
+  SortSmem<ITEMS>& sm = *reinterpret_cast<SortSmem<ITEMS>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t count = min((int64_t)*a.count, a.capacity);
   const uint32_t ctrl = a.ctrl[pass];
   if (ctrl & kCtrlTrivial) return;  // whole block: this digit is the same for every key
   const int par = (int)(ctrl & kCtrlParity);
-  const uint64_t* __restrict__ kin = a.keys[par];
-  const uint32_t* __restrict__ vin = a.vals[par];
-  uint64_t* __restrict__ kout = a.keys[par ^ 1];
-  uint32_t* __restrict__ vout = a.vals[par ^ 1];
+  // selects, not a dynamically indexed parameter array (which would be
+  // copied to local memory)
+  const uint64_t* __restrict__ kin = par ? a.keys[1] : a.keys[0];
+  const uint32_t* __restrict__ vin = par ? a.vals[1] : a.vals[0];
+  uint64_t* __restrict__ kout = par ? a.keys[0] : a.keys[1];
+  uint32_t* __restrict__ vout = par ? a.vals[0] : a.vals[1];
   const int shift = kRadixBits * pass;
   const uint32_t* __restrict__ hist_pass = a.hist_scan + pass * kRadix;
   uint32_t* lookback = a.lookback + (size_t)pass * a.lookback_stride;
@@ -379,21 +391,31 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_pass_kernel(SortArgs
   }
 }
 
-void launch_onesweep_pass(const SortArgs& a, int pass, int64_t grid, cudaStream_t s) {
-  if (grid <= 0) return;
-  const size_t smem = sizeof(SortSmem);
+template <int ITEMS, int MIN_BLOCKS>
+static void launch_pass(const SortArgs& a, int pass, int64_t grid, cudaStream_t s) {
+  const size_t smem = sizeof(SortSmem<ITEMS>);
   // once per device (the attribute is per device; not repeated inside a graph capture)
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    cudaFuncSetAttribute(onesweep_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(onesweep_pass_kernel<ITEMS, MIN_BLOCKS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  onesweep_pass_kernel<<<(unsigned)grid, kSortThreads, smem, s>>>(a, pass);
+  onesweep_pass_kernel<ITEMS, MIN_BLOCKS><<<(unsigned)grid, kSortThreads, smem, s>>>(a, pass);
 }
 
-int64_t sort_partitions(int64_t count) { return (count + kSortTile - 1) / kSortTile; }
+void launch_onesweep_pass(const SortArgs& a, int pass, int items, cudaStream_t s) {
+  const int64_t grid = sort_partitions(a.capacity, items);
+  if (grid <= 0) return;
+  switch (items) {
+    case 12: launch_pass<12, 4>(a, pass, grid, s); break;
+    case 20: launch_pass<20, 3>(a, pass, grid, s); break;
+    case 24: launch_pass<24, 2>(a, pass, grid, s); break;
+    default: launch_pass<16, 4>(a, pass, grid, s); break;
+  }
+}
 
 // Exclusive scan of each pass's 256 digit counts, and the pass control
 // words (one block of 256 threads, passes in order).
@@ -444,10 +466,10 @@ void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, cudaStream_t s
 __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __restrict__ ranges) {
   const int64_t count = min((int64_t)*a.count, a.capacity);
   const int par = (int)(a.ctrl[a.npass] & kCtrlParity);
-  const uint64_t* __restrict__ keys = a.keys[par];
+  const uint64_t* __restrict__ keys = par ? a.keys[1] : a.keys[0];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.sorted_keys = a.keys[par];
-    *a.sorted_vals = a.vals[par];
+    *a.sorted_keys = keys;
+    *a.sorted_vals = par ? a.vals[1] : a.vals[0];
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {

@@ -59,6 +59,7 @@ struct gs_ctx {
   int raster_bwd = 2;
   int bwd_direct = 2;  // per-lane gradient atomics when at most this many lanes contribute
   int sort_passes = 0;  // LSD passes of the last sort
+  int sort_items = 16;  // keys per thread of a sort partition
 
   // last batch
   int B = 0, deg = 0;
@@ -440,7 +441,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   while (((int64_t)1 << bin_bits) < c->bins) bin_bits++;
   const int npass = (32 + bin_bits + 7) / 8;  // the 32 depth bits and the bin bits
   c->sort_passes = npass;
-  const size_t lb = sort_lookback_bytes(cap);
+  const size_t lb = sort_lookback_bytes(cap, c->sort_items);
   GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
   GS_TRY(ensure(c, c->hist_scan, sizeof(uint32_t) * (8 * 256 + 16)));
   GS_TRY(ensure(c, c->lookback, lb * npass));
@@ -495,7 +496,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   GS_CHECK_LAUNCH(c);
   for (int p = 0; p < npass; p++) {
     LaunchScope ls(c, "onesweep_pass");
-    launch_onesweep_pass(sa, p, sort_partitions(cap), c->stream);
+    launch_onesweep_pass(sa, p, c->sort_items, c->stream);
   }
   GS_CHECK_LAUNCH(c);
   GS_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * c->bins, c->stream));
@@ -703,6 +704,12 @@ gs_status gs_set_option(gs_ctx* c, int32_t option, int64_t value) {
       if (value < 0 || value > 32) return fail(c, GS_EINVAL, "direct-atomic lane limit must be 0..32");
       c->bwd_direct = (int)value;
       return GS_OK;
+    case GS_OPT_SORT_ITEMS:
+      if (value != 12 && value != 16 && value != 20 && value != 24)
+        return fail(c, GS_EINVAL, "sort items per thread must be 12, 16, 20 or 24");
+      if (c->capturing || c->gexec) return fail(c, GS_ESTATE, "sort partition size is fixed once a graph is captured");
+      c->sort_items = (int)value;
+      return GS_OK;
     default:
       return fail(c, GS_EINVAL, "unknown option %d", option);
   }
@@ -714,6 +721,7 @@ gs_status gs_get_option(gs_ctx* c, int32_t option, int64_t* value) {
     case GS_OPT_RASTER_FWD: *value = c->raster_fwd; return GS_OK;
     case GS_OPT_RASTER_BWD: *value = c->raster_bwd; return GS_OK;
     case GS_OPT_BWD_DIRECT: *value = c->bwd_direct; return GS_OK;
+    case GS_OPT_SORT_ITEMS: *value = c->sort_items; return GS_OK;
     default: return fail(c, GS_EINVAL, "unknown option %d", option);
   }
 }

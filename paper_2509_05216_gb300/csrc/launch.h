@@ -94,10 +94,11 @@ struct SortArgs {
   const uint32_t** sorted_vals;
 };
 
-size_t sort_lookback_bytes(int64_t count);
-int64_t sort_partitions(int64_t count);
+size_t sort_lookback_bytes(int64_t count, int items);
+int64_t sort_partitions(int64_t count, int items);
 void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, cudaStream_t s);
-void launch_onesweep_pass(const SortArgs& a, int pass, int64_t grid, cudaStream_t s);
+// items: keys per thread (12, 16, 20 or 24); the grid covers a.capacity
+void launch_onesweep_pass(const SortArgs& a, int pass, int items, cudaStream_t s);
 void launch_tile_ranges(const SortArgs& a, int64_t grid_hint, uint2* ranges, cudaStream_t s);
 
 void launch_raster_fwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s);

@@ -64,39 +64,23 @@ struct ShEval {
   }
 };
 
-// Intermediate values of one (view, Gaussian) projection.
-struct ProjState {
-  float tx, ty, tz;
-  float ux, uy;       // clamped slopes used in J
-  bool clx, cly;      // slope clamped
-  float s[3];         // exp(log-scale)
-  float qn[4];        // normalised quaternion
-  float qinv;         // 1 / |q|
-  float Rq[9];        // rotation of the normalised quaternion
-  float Sig[6];       // Sigma: 00 01 02 11 12 22
-  float T[6];         // J W (2x3, row-major)
-  float c00, c01, c11, det;
+// View-independent part of the covariance: Sigma = M M^T with
+// M = R(q / |q|) diag(exp(s)), computed once per Gaussian.
+struct GaussCov {
+  float s[3];    // exp(log-scale)
+  float qn[4];   // normalised quaternion
+  float qinv;    // 1 / |q|
+  float Rq[9];   // rotation of the normalised quaternion
+  float Sig[6];  // Sigma: 00 01 02 11 12 22
 };
 
-// Covariance part of the projection (shared by forward and backward).
-__device__ __forceinline__ void project_cov(const ViewRec& V, const float* mean, const float* lsc,
-                                            const float* quat, float depth, ProjState& st) {
-  const float* R = V.R;
-  st.tx = fmaf(R[0], mean[0], fmaf(R[1], mean[1], fmaf(R[2], mean[2], V.t[0])));
-  st.ty = fmaf(R[3], mean[0], fmaf(R[4], mean[1], fmaf(R[5], mean[2], V.t[1])));
-  st.tz = depth;
-  float ux = st.tx / st.tz, uy = st.ty / st.tz;
-  st.clx = fabsf(ux) > V.limx;
-  st.cly = fabsf(uy) > V.limy;
-  st.ux = fminf(fmaxf(ux, -V.limx), V.limx);
-  st.uy = fminf(fmaxf(uy, -V.limy), V.limy);
-
-  for (int i = 0; i < 3; i++) st.s[i] = expf(lsc[i]);
+__device__ __forceinline__ void gauss_cov(const float* lsc, const float* quat, GaussCov& gc) {
+  for (int i = 0; i < 3; i++) gc.s[i] = expf(lsc[i]);
   float qq = quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3];
-  st.qinv = rsqrtf(qq);
-  for (int i = 0; i < 4; i++) st.qn[i] = quat[i] * st.qinv;
-  const float w = st.qn[0], x = st.qn[1], y = st.qn[2], z = st.qn[3];
-  float* Q = st.Rq;
+  gc.qinv = rsqrtf(qq);
+  for (int i = 0; i < 4; i++) gc.qn[i] = quat[i] * gc.qinv;
+  const float w = gc.qn[0], x = gc.qn[1], y = gc.qn[2], z = gc.qn[3];
+  float* Q = gc.Rq;
   Q[0] = 1.f - 2.f * (y * y + z * z);
   Q[1] = 2.f * (x * y - w * z);
   Q[2] = 2.f * (x * z + w * y);
@@ -108,13 +92,37 @@ __device__ __forceinline__ void project_cov(const ViewRec& V, const float* mean,
   Q[8] = 1.f - 2.f * (x * x + y * y);
   float M[9];
   for (int i = 0; i < 3; i++)
-    for (int j = 0; j < 3; j++) M[3 * i + j] = Q[3 * i + j] * st.s[j];
-  st.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
-  st.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
-  st.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
-  st.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
-  st.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
-  st.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    for (int j = 0; j < 3; j++) M[3 * i + j] = Q[3 * i + j] * gc.s[j];
+  gc.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  gc.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  gc.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  gc.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  gc.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  gc.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+}
+
+// View-dependent part of one (view, Gaussian) projection.
+struct ProjState {
+  float tx, ty, tz;
+  float ux, uy;       // clamped slopes used in J
+  bool clx, cly;      // slope clamped
+  float T[6];         // J W (2x3, row-major)
+  float c00, c01, c11, det;
+};
+
+// Sigma' = J W Sigma W^T J^T + 0.3 I for one view (shared by forward and
+// backward).
+__device__ __forceinline__ void project_cov(const ViewRec& V, const float* mean, const float* Sig, float depth,
+                                            ProjState& st) {
+  const float* R = V.R;
+  st.tx = fmaf(R[0], mean[0], fmaf(R[1], mean[1], fmaf(R[2], mean[2], V.t[0])));
+  st.ty = fmaf(R[3], mean[0], fmaf(R[4], mean[1], fmaf(R[5], mean[2], V.t[1])));
+  st.tz = depth;
+  float ux = st.tx / st.tz, uy = st.ty / st.tz;
+  st.clx = fabsf(ux) > V.limx;
+  st.cly = fabsf(uy) > V.limy;
+  st.ux = fminf(fmaxf(ux, -V.limx), V.limx);
+  st.uy = fminf(fmaxf(uy, -V.limy), V.limy);
 
   const float itz = 1.f / st.tz;
   const float J00 = V.fx * itz, J02 = -V.fx * st.ux * itz;
@@ -124,7 +132,7 @@ __device__ __forceinline__ void project_cov(const ViewRec& V, const float* mean,
     st.T[3 + j] = J11 * R[3 + j] + J12 * R[6 + j];
   }
   // Sigma' = T Sigma T^T + 0.3 I
-  const float* S = st.Sig;
+  const float* S = Sig;
   float a[3], b[3];  // a = Sigma T0^T, b = Sigma T1^T
   a[0] = S[0] * st.T[0] + S[1] * st.T[1] + S[2] * st.T[2];
   a[1] = S[1] * st.T[0] + S[3] * st.T[1] + S[4] * st.T[2];
@@ -158,6 +166,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
     for (int i = 0; i < 3 * K; i++) sh[i] = __ldg(P + (11 + i) * S + g);
   }
   const float opacity = 1.f / (1.f + expf(-op));
+  GaussCov gc;
+  gauss_cov(lsc, quat, gc);  // view-independent: once per Gaussian
   uint32_t total = 0;
   for (int v = 0; v < a.B; v++) {
     const ViewRec& V = a.views[v];
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
       depth = depth_key(V, mean[0], mean[1], mean[2]);
       if (depth > V.znear) {
         ProjState st;
-        project_cov(V, mean, lsc, quat, depth, st);
+        project_cov(V, mean, gc.Sig, depth, st);
         if (st.det != 0.f) {
           const float idet = 1.f / st.det;
           // lambda_max = mid + sqrt(max(0.1, mid^2 - det)); mid^2 - det is
@@ -248,26 +258,40 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
 // Backward, colour part: dL/drgb per (view, Gaussian) -> dL/dSH and the
 // part of dL/dmean that flows through the view direction.  Writes the SH
 // gradient planes and initialises the mean planes.
+//
+// A block holds 32 Gaussians and three warps, one per colour channel: a
+// thread keeps only its channel's K coefficients and gradients in registers
+// (the channels are independent except through the direction gradient, which
+// is linear in the per-channel weights and is summed over the three warps at
+// the end), so three times as many warps fit on an SM as with one thread per
+// Gaussian, which hides the latency of the per-view chains.
 template <int DEG>
-__global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a) {
+__global__ void __launch_bounds__(96) project_bwd_color_kernel(ProjectBwdArgs a) {
   constexpr int K = ShEval<DEG>::K;
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.n) return;
+  __shared__ float s_gm[3][3][32];
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * 32 + lane;
+  const bool live = g < a.n;
   const float* P = a.params;
   const int64_t S = a.stride, plane = (int64_t)a.B * S;
-  float mean[3], sh[3 * K], gsh[3 * K];
+  float mean[3] = {0.f, 0.f, 0.f}, sh[K], gsh[K];
 #pragma unroll
-  for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
+  for (int k = 0; k < K; k++) {
+    sh[k] = live ? __ldg(P + (11 + 3 * k + c) * S + g) : 0.f;
+    gsh[k] = 0.f;
+  }
+  if (live) {
 #pragma unroll
-  for (int i = 0; i < 3 * K; i++) {
-    sh[i] = __ldg(P + (11 + i) * S + g);
-    gsh[i] = 0.f;
+    for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
   }
   float gm[3] = {0.f, 0.f, 0.f};
+  const float* gch = a.g2d + (6 + c) * plane;
+  // the next view's gradient is loaded while this view is processed
+  float nxt = live ? __ldg(gch + g) : 0.f;
   for (int v = 0; v < a.B; v++) {
-    const int64_t o = (int64_t)v * S + g;
-    const float grgb[3] = {__ldg(a.g2d + 6 * plane + o), __ldg(a.g2d + 7 * plane + o), __ldg(a.g2d + 8 * plane + o)};
-    if (grgb[0] == 0.f && grgb[1] == 0.f && grgb[2] == 0.f) continue;
+    const float gc_in = nxt;
+    if (live && v + 1 < a.B) nxt = __ldg(gch + (int64_t)(v + 1) * S + g);
+    if (gc_in == 0.f) continue;
     const ViewRec& V = a.views[v];
     // rgb_c = max(0, 0.5 + sum_k sh_kc Y_k(d)), d = (mu - campos) / |mu - campos|
     float dx = mean[0] - V.campos[0], dy = mean[1] - V.campos[1], dz = mean[2] - V.campos[2];
@@ -275,24 +299,15 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
     dx *= inv; dy *= inv; dz *= inv;
     float Y[K];
     ShEval<DEG>::basis(dx, dy, dz, Y);
-    float gc[3];
+    float acc = 0.5f;
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      float acc = 0.5f;
-#pragma unroll
-      for (int k = 0; k < K; k++) acc = fmaf(sh[3 * k + c], Y[k], acc);
-      gc[c] = acc < 0.f ? 0.f : grgb[c];
-    }
+    for (int k = 0; k < K; k++) acc = fmaf(sh[k], Y[k], acc);
+    if (acc < 0.f) continue;  // clamped channel: no gradient
     float wk[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
-      float acc = 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        gsh[3 * k + c] = fmaf(gc[c], Y[k], gsh[3 * k + c]);
-        acc = fmaf(gc[c], sh[3 * k + c], acc);
-      }
-      wk[k] = acc;
+      gsh[k] = fmaf(gc_in, Y[k], gsh[k]);
+      wk[k] = gc_in * sh[k];
     }
     float gdx, gdy, gdz;
     ShEval<DEG>::grad(dx, dy, dz, wk, gdx, gdy, gdz);
@@ -302,10 +317,17 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
     gm[2] += (gdz - dz * dd) * inv;
   }
   float* G = a.grads;
+  if (live) {
 #pragma unroll
-  for (int i = 0; i < 3; i++) G[i * S + g] = gm[i];
+    for (int k = 0; k < K; k++) G[(11 + 3 * k + c) * S + g] = gsh[k];
+  }
 #pragma unroll
-  for (int i = 0; i < 3 * K; i++) G[(11 + i) * S + g] = gsh[i];
+  for (int i = 0; i < 3; i++) s_gm[c][i][lane] = gm[i];
+  __syncthreads();
+  if (c == 0 && live) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) G[i * S + g] = s_gm[0][i][lane] + s_gm[1][i][lane] + s_gm[2][i][lane];
+  }
 }
 
 // Backward, geometry part: dL/d(mu2D, conic, opacity) per (view, Gaussian)
@@ -326,7 +348,11 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
   const float op = __ldg(P + 10 * S + g);
   const float opacity = 1.f / (1.f + expf(-op));
 
-  float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gop = 0.f;
+  GaussCov gc;
+  gauss_cov(lsc, quat, gc);  // view-independent: once per Gaussian
+  // dL/dSigma summed over the views: the chain from Sigma to the scale and
+  // rotation is linear in it, so it runs once per Gaussian after the loop
+  float gm[3] = {0.f, 0.f, 0.f}, gSig[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gop = 0.f;
   // prefetch the first view's six gradient values
   float cur[6], nxt[6];
 #pragma unroll
@@ -344,7 +370,7 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
     const float depth = depth_key(V, mean[0], mean[1], mean[2]);
     if (!(depth > V.znear)) continue;
     ProjState st;
-    project_cov(V, mean, lsc, quat, depth, st);
+    project_cov(V, mean, gc.Sig, depth, st);
 
     // conic = (c11, -c01, c00) / det  ->  Sigma'
     const float id = 1.f / st.det, id2 = id * id;
@@ -361,7 +387,7 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
       GT[j] = gc00 * st.T[j] + gh * st.T[3 + j];
       GT[3 + j] = gh * st.T[j] + gc11 * st.T[3 + j];
     }
-    const float* Sg = st.Sig;
+    const float* Sg = gc.Sig;
     const float Sfull[9] = {Sg[0], Sg[1], Sg[2], Sg[1], Sg[3], Sg[4], Sg[2], Sg[4], Sg[5]};
     float gT[6];
 #pragma unroll
@@ -369,11 +395,10 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
 #pragma unroll
       for (int b = 0; b < 3; b++)
         gT[3 * i + b] = 2.f * (GT[3 * i] * Sfull[b] + GT[3 * i + 1] * Sfull[3 + b] + GT[3 * i + 2] * Sfull[6 + b]);
-    float gS[9];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-      for (int j = 0; j < 3; j++) gS[3 * i + j] = st.T[i] * GT[j] + st.T[3 + i] * GT[3 + j];
+      for (int j = 0; j < 3; j++) gSig[3 * i + j] += st.T[i] * GT[j] + st.T[3 + i] * GT[3 + j];
     // T = J W
     const float* R = V.R;
     const float gJ00 = gT[0] * R[0] + gT[1] * R[1] + gT[2] * R[2];
@@ -399,43 +424,41 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
     // t = W mu + tau
 #pragma unroll
     for (int j = 0; j < 3; j++) gm[j] += R[j] * gtx + R[3 + j] * gty + R[6 + j] * gtz;
-    // Sigma = M M^T, M = Rq diag(s): dL/dM = (gS + gS^T) M
-    float gR[9];
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-      float gsj = 0.f;
-#pragma unroll
-      for (int i = 0; i < 3; i++) {
-        float gMij = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; k++) gMij += (gS[3 * i + k] + gS[3 * k + i]) * st.Rq[3 * k + j] * st.s[j];
-        gsj += gMij * st.Rq[3 * i + j];
-        gR[3 * i + j] = gMij * st.s[j];
-      }
-      gls[j] += gsj * st.s[j];
-    }
-    // rotation of the unit quaternion (w, x, y, z)
-    const float w = st.qn[0], x = st.qn[1], y = st.qn[2], z = st.qn[3];
-    float gqn[4];
-    gqn[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
-    gqn[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] -
-                    2.f * x * gR[8]);
-    gqn[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] -
-                    2.f * y * gR[8]);
-    gqn[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] +
-                    y * gR[7]);
-    const float dq = gqn[0] * st.qn[0] + gqn[1] * st.qn[1] + gqn[2] * st.qn[2] + gqn[3] * st.qn[3];
-#pragma unroll
-    for (int i = 0; i < 4; i++) gq[i] += (gqn[i] - st.qn[i] * dq) * st.qinv;
     gop += gsig * opacity * (1.f - opacity);
   }
+  // Sigma = M M^T, M = Rq diag(s): dL/dM = (gS + gS^T) M
+  float gR[9], gls[3];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    float gsj = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      float gMij = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; k++) gMij += (gSig[3 * i + k] + gSig[3 * k + i]) * gc.Rq[3 * k + j] * gc.s[j];
+      gsj += gMij * gc.Rq[3 * i + j];
+      gR[3 * i + j] = gMij * gc.s[j];
+    }
+    gls[j] = gsj * gc.s[j];
+  }
+  // rotation of the unit quaternion (w, x, y, z)
+  const float w = gc.qn[0], x = gc.qn[1], y = gc.qn[2], z = gc.qn[3];
+  float gqn[4];
+  gqn[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+  gqn[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] -
+                  2.f * x * gR[8]);
+  gqn[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] -
+                  2.f * y * gR[8]);
+  gqn[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] +
+                  y * gR[7]);
+  const float dq = gqn[0] * gc.qn[0] + gqn[1] * gc.qn[1] + gqn[2] * gc.qn[2] + gqn[3] * gc.qn[3];
   float* G = a.grads;
 #pragma unroll
   for (int i = 0; i < 3; i++) G[i * S + g] += gm[i];
 #pragma unroll
   for (int i = 0; i < 3; i++) G[(3 + i) * S + g] = gls[i];
 #pragma unroll
-  for (int i = 0; i < 4; i++) G[(6 + i) * S + g] = gq[i];
+  for (int i = 0; i < 4; i++) G[(6 + i) * S + g] = (gqn[i] - gc.qn[i] * dq) * gc.qinv;
   G[10 * S + g] = gop;
 }
 
@@ -453,14 +476,15 @@ void launch_project_fwd(const ProjectArgs& a, int deg, cudaStream_t s) {
 int project_fwd_block() { return 256; }
 
 void launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t s) {
+  const unsigned cblocks = (unsigned)((a.n + 31) / 32);  // 32 Gaussians x 3 channels
+  switch (deg) {
+    case 0: project_bwd_color_kernel<0><<<cblocks, 96, 0, s>>>(a); break;
+    case 1: project_bwd_color_kernel<1><<<cblocks, 96, 0, s>>>(a); break;
+    case 2: project_bwd_color_kernel<2><<<cblocks, 96, 0, s>>>(a); break;
+    default: project_bwd_color_kernel<3><<<cblocks, 96, 0, s>>>(a); break;
+  }
   const int threads = 128;
   const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
-  switch (deg) {
-    case 0: project_bwd_color_kernel<0><<<blocks, threads, 0, s>>>(a); break;
-    case 1: project_bwd_color_kernel<1><<<blocks, threads, 0, s>>>(a); break;
-    case 2: project_bwd_color_kernel<2><<<blocks, threads, 0, s>>>(a); break;
-    default: project_bwd_color_kernel<3><<<blocks, threads, 0, s>>>(a); break;
-  }
   project_bwd_geom_kernel<<<blocks, threads, 0, s>>>(a);
 }
 

@@ -496,23 +496,38 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
   const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
   const float fpx = (float)px, fpy = (float)py0;
   const int64_t gplane = (int64_t)a.B * a.stride;
+  // lane j's record of the next batch (towards the front), loaded while the
+  // warp walks this one
+  float4 n0, n1, n2;
+  uint32_t ng = 0;
+  {
+    const int i = max(0, total - 32) + lane;
+    if (i < total) {
+      ng = vals[rg.x + i];
+      stage_one(a, v, ng, n0, n1, n2);
+    }
+  }
   for (int bend = total; bend > 0; bend -= 32) {
     const int bstart = max(0, bend - 32);
     const int i = bstart + lane;
     bool hit = false;
     __syncwarp();
     if (i < bend) {
-      const uint32_t g = vals[rg.x + i];
-      float4 r0, r1, r2;
-      stage_one(a, v, g, r0, r1, r2);
-      s0[w][lane] = r0;
-      s1[w][lane] = r1;
-      s2[w][lane] = r2;
-      sg[w][lane] = g;
-      hit = ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
+      s0[w][lane] = n0;
+      s1[w][lane] = n1;
+      s2[w][lane] = n2;
+      sg[w][lane] = ng;
+      hit = ellipse_hits(n0, n1, n2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
     }
     uint32_t mask = __ballot_sync(0xffffffffu, hit);
     __syncwarp();
+    if (bstart > 0) {
+      const int k = max(0, bstart - 32) + lane;
+      if (k < bstart) {
+        ng = vals[rg.x + k];
+        stage_one(a, v, ng, n0, n1, n2);
+      }
+    }
     while (mask) {  // back to front
       const int j = 31 - __clz(mask);
       mask ^= 1u << j;

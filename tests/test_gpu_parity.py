@@ -232,6 +232,29 @@ def test_options_reject_bad_values(ctx):
     with pytest.raises(gs.GsError):
         ctx.gs_set_option(gs.GS_OPT_BWD_DIRECT, -1)
     assert 0 <= ctx.gs_get_option(gs.GS_OPT_BWD_DIRECT) <= 32
+    with pytest.raises(gs.GsError):
+        ctx.gs_set_option(gs.GS_OPT_SORT_ITEMS, 8)
+    assert ctx.gs_get_option(gs.GS_OPT_SORT_ITEMS) in (12, 16, 20, 24)
+
+
+@pytest.mark.parametrize("items", [12, 20, 24])
+def test_sort_partition_sizes_give_the_same_binning(ctx, items):
+    """Every radix-sort partition size sorts to the same keys, values and
+    ranges (bit-exact against the CPU recomputation)."""
+    scene, cams = SCENES["random_deg3_mixed"]()
+    ctx.gs_set_option(gs.GS_OPT_SORT_ITEMS, items)
+    try:
+        run_forward(ctx, scene, cams)
+        n, stride = scene["n"], scene["params"].shape[1]
+        r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
+        r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+        r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
+        keys, vals, ranges, _ = expected_binning(r0, r2, r3, cams, n, stride)
+        assert np.array_equal(ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64), keys)
+        assert np.array_equal(ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64), vals)
+        assert np.array_equal(ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64), ranges)
+    finally:
+        ctx.gs_set_option(gs.GS_OPT_SORT_ITEMS, 16)
 
 
 @pytest.mark.parametrize("direct", [0, 3, 32])
