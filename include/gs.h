@@ -316,7 +316,9 @@ gs_status gs_serve_stats(gs_server* srv, int64_t* batches, int64_t* rendered, in
 /* ---------------------------------------------------------------- inspection */
 
 /* Intermediate buffers of the last batch (device pointers owned by the
- * context, valid until the next call that rewrites them). */
+ * context, valid until the next call that rewrites them).  REC0..REC2 are
+ * interleaved: entry i of each is at byte offset 48 i from its pointer
+ * (one 48-byte record of three float4 per (view, Gaussian)). */
 typedef enum {
   GS_BUF_REC0 = 0,   /* float4 [B][N]: mu_x, mu_y, cA, cB with cA = -A log2(e) / 2,
                         cB = -B log2(e) for the conic (A, B, C) */

@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
     uint32_t dbits = 0;
     if (cnt) {
-      const float4 r0 = a.rec0[o];
+      const float4 r0 = a.rec0[kRecStride * o];
       tile_rect(V, r0.x, r0.y, a.rec3[o].x, x0, x1, y0, y1);
-      dbits = __float_as_uint(a.rec2[o].w);
+      dbits = __float_as_uint(a.rec2[kRecStride * o].w);
     }
     const int rw = x1 - x0;
     for (uint32_t q0 = 0; q0 < vtot; q0 += 32) {

@@ -67,7 +67,7 @@ struct gs_ctx {
   bool projected = false, sorted = false, rastered = false;
   std::vector<ViewRec> views_h;
 
-  DevBuf views, rec0, rec1, rec2, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
+  DevBuf views, rec, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
       target_slot, host_tgt0, host_tgt1;
 
@@ -303,7 +303,7 @@ void gs_destroy(gs_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->views, &c->rec0, &c->rec1, &c->rec2, &c->rec3, &c->tiles, &c->block_sums, &c->block_offsets,
+  DevBuf* bufs[] = {&c->views, &c->rec, &c->rec3, &c->tiles, &c->block_sums, &c->block_offsets,
                     &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->hist_scan,
                     &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
                     &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1};
@@ -365,9 +365,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   const int64_t n = params->n, stride = params->stride;
   const int64_t nb = (n + project_fwd_block() - 1) / project_fwd_block();
   GS_TRY(ensure(c, c->views, sizeof(ViewRec) * B));
-  GS_TRY(ensure(c, c->rec0, sizeof(float4) * B * stride));
-  GS_TRY(ensure(c, c->rec1, sizeof(float4) * B * stride));
-  GS_TRY(ensure(c, c->rec2, sizeof(float4) * B * stride));
+  GS_TRY(ensure(c, c->rec, sizeof(float4) * kRecStride * B * stride));
   GS_TRY(ensure(c, c->rec3, sizeof(int2) * B * stride));
   GS_TRY(ensure(c, c->tiles, sizeof(uint32_t) * B * stride));
   GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * nb));
@@ -383,9 +381,9 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   a.stride = stride;
   a.views = P<ViewRec>(c->views);
   a.B = B;
-  a.rec0 = P<float4>(c->rec0);
-  a.rec1 = P<float4>(c->rec1);
-  a.rec2 = P<float4>(c->rec2);
+  a.rec0 = P<float4>(c->rec);
+  a.rec1 = P<float4>(c->rec) + 1;
+  a.rec2 = P<float4>(c->rec) + 2;
   a.rec3 = P<int2>(c->rec3);
   a.tiles = P<uint32_t>(c->tiles);
   a.block_sums = P<uint32_t>(c->block_sums);
@@ -453,8 +451,8 @@ gs_status gs_bin_sort(gs_ctx* c) {
   d.stride = c->stride;
   d.views = P<ViewRec>(c->views);
   d.B = c->B;
-  d.rec0 = P<float4>(c->rec0);
-  d.rec2 = P<float4>(c->rec2);
+  d.rec0 = P<float4>(c->rec);
+  d.rec2 = P<float4>(c->rec) + 2;
   d.rec3 = P<int2>(c->rec3);
   d.tiles = P<uint32_t>(c->tiles);
   d.block_offsets = P<uint32_t>(c->block_offsets);
@@ -517,9 +515,9 @@ static RasterArgs raster_args(gs_ctx* c) {
   r.stride = c->stride;
   r.ranges = P<uint2>(c->ranges);
   r.vals = reinterpret_cast<const uint32_t* const*>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
-  r.rec0 = P<float4>(c->rec0);
-  r.rec1 = P<float4>(c->rec1);
-  r.rec2 = P<float4>(c->rec2);
+  r.rec0 = P<float4>(c->rec);
+  r.rec1 = P<float4>(c->rec) + 1;
+  r.rec2 = P<float4>(c->rec) + 2;
   r.tfinal = P<float>(c->tfinal);
   r.nlast = P<uint32_t>(c->nlast);
   return r;
@@ -648,9 +646,13 @@ gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
   if (!c || !ptr || !count) return GS_EINVAL;
   const int64_t bn = (int64_t)c->B * c->stride;
   switch (which) {
-    case GS_BUF_REC0: if (!c->projected) return GS_ESTATE; *ptr = c->rec0.p; *count = bn; break;
-    case GS_BUF_REC1: if (!c->projected) return GS_ESTATE; *ptr = c->rec1.p; *count = bn; break;
-    case GS_BUF_REC2: if (!c->projected) return GS_ESTATE; *ptr = c->rec2.p; *count = bn; break;
+    case GS_BUF_REC0:
+    case GS_BUF_REC1:
+    case GS_BUF_REC2:
+      if (!c->projected) return GS_ESTATE;
+      *ptr = P<float4>(c->rec) + (which - GS_BUF_REC0);  // stride kRecStride float4
+      *count = bn;
+      break;
     case GS_BUF_REC3: if (!c->projected) return GS_ESTATE; *ptr = c->rec3.p; *count = bn; break;
     case GS_BUF_KEYS:
     case GS_BUF_VALS: {

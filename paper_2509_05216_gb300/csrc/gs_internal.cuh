@@ -17,6 +17,11 @@ constexpr float kDilation = 0.3f;       // added to the 2D covariance diagonal
 constexpr float kGuard = 1.3f;          // slope clamp, in half fields of view
 constexpr float kLog2e = 1.4426950408889634f;
 
+// Projected records: three float4 per (view, Gaussian), stored together
+// (48 bytes), so a compositing kernel's gather of one record touches two
+// 32-byte sectors instead of three.  Record k of entry o is rec[kRecStride * o + k].
+constexpr int kRecStride = 3;
+
 // Device status word bits.
 constexpr int kStatusCapacity = 1;
 constexpr int kStatusTimeout = 2;

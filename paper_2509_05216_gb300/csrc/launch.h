@@ -13,8 +13,8 @@ struct ProjectArgs {
   int64_t n, stride;
   const ViewRec* views;
   int B;
-  float4* rec0;
-  float4* rec1;
+  float4* rec0;  // records 0, 1, 2 of entry o at rec0[3 o], rec1[3 o], rec2[3 o]
+  float4* rec1;  // (one interleaved array: rec1 = rec0 + 1, rec2 = rec0 + 2)
   float4* rec2;
   int2* rec3;
   uint32_t* tiles;       // [B][stride]

@@ -232,9 +232,9 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
           }
         }
       }
-      a.rec0[o] = r0;
-      a.rec1[o] = r1;
-      a.rec2[o] = make_float4(blue, ex.x, ex.y, depth);
+      a.rec0[kRecStride * o] = r0;
+      a.rec1[kRecStride * o] = r1;
+      a.rec2[kRecStride * o] = make_float4(blue, ex.x, ex.y, depth);
       a.rec3[o] = make_int2(tiles ? radius : 0, (int)tiles);
       a.tiles[o] = tiles;
     }

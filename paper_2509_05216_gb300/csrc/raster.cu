@@ -43,9 +43,9 @@ __device__ __forceinline__ void stage_one(const RasterArgs& a, int v, uint32_t g
     return;
   }
   const int64_t o = (int64_t)v * a.stride + g;
-  s0 = a.rec0[o];
-  s1 = a.rec1[o];
-  s2 = a.rec2[o];
+  s0 = a.rec0[kRecStride * o];
+  s1 = a.rec1[kRecStride * o];
+  s2 = a.rec2[kRecStride * o];
 }
 
 // Does the splat's alpha >= 1/255 box meet the pixel rectangle [x0,x1]x[y0,y1]?

@@ -158,9 +158,9 @@ def params_struct(t: torch.Tensor, n: int, deg: int) -> gs_params:
 class _DevArray:
     """Zero-copy view of a device buffer for torch.as_tensor."""
 
-    def __init__(self, ptr, shape, typestr):
+    def __init__(self, ptr, shape, typestr, strides=None):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
-                                         "version": 3, "strides": None}
+                                         "version": 3, "strides": strides}
 
 
 class Context:
@@ -316,7 +316,9 @@ class Context:
         if n == 0:
             return torch.empty(spec[0], device="cuda:%d" % self.device,
                                dtype={"<f4": torch.float32, "<i8": torch.int64, "<i4": torch.int32}[spec[1]])
-        t = torch.as_tensor(_DevArray(ptr.value, *spec), device="cuda:%d" % self.device)
+        # the three projected records are interleaved (48 bytes per entry)
+        strides = (48, 4) if which in (GS_BUF_REC0, GS_BUF_REC1, GS_BUF_REC2) else None
+        t = torch.as_tensor(_DevArray(ptr.value, *spec, strides=strides), device="cuda:%d" % self.device)
         return t.clone()
 
 
