@@ -252,7 +252,9 @@ def _sample_isosurface(fg, lo, hi, iso, n, seed, res=96, jitter=0.0, device=None
     are drawn uniformly (seeded) and a uniform point inside each is
     Newton-projected onto the level set, so the density is close to uniform
     per unit area.  Points that do not converge or leave their cell's
-    neighbourhood are redrawn.
+    neighbourhood are redrawn.  The points are returned in the order a
+    contour filter emits them: by the grid cell that holds them, x fastest,
+    then y, then z (the draws themselves do not depend on this order).
     """
     import torch
     dev = _device(device)
@@ -292,7 +294,10 @@ def _sample_isosurface(fg, lo, hi, iso, n, seed, res=96, jitter=0.0, device=None
         x = x[ok].cpu().numpy()
         out.append(x)
         have += x.shape[0]
-    return np.concatenate(out, axis=0)[:n]
+    pts = np.concatenate(out, axis=0)[:n]
+    cell = np.clip(np.floor((pts - lo) / h).astype(np.int64), 0, res - 1)
+    order = np.argsort((cell[:, 2] * res + cell[:, 1]) * res + cell[:, 0], kind="stable")
+    return pts[order]
 
 
 # ---------------------------------------------------------------- config 2
