@@ -263,6 +263,31 @@ def algorithmic_work(name, n, P, B, I, pairs, pixels):
     return None, None
 
 
+def recorded_traffic(kernel, variant):
+    """DRAM bytes per launch of a compositing kernel variant from the ncu
+    summary in profiles/, or None when that summary was taken on another
+    version of the kernel source (its sha1 is recorded beside the numbers)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2509_05216_gb300", "csrc", "raster.cu")
+    summary = os.path.join(ROOT, "profiles", "raster_traffic_blobs4M_2048sq_B16.md")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        text = open(summary).read()
+    except OSError:
+        return None
+    if ("raster.cu sha1 %s" % sha) not in text:
+        return None
+    tag = "%s_kernel<%d>:" % (kernel, variant)
+    for line in text.splitlines():
+        line = line.strip().strip("|").strip()
+        if line.startswith(tag):
+            try:
+                return float(line[len(tag):].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -420,9 +445,11 @@ def gpu_arm(args):
         clk_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak = 152 * 128 * 2 * clk_max * 1e6 / 1e12  # FP32 TFLOP/s, FMA = 2
         achieved = work / (avg_ms / 1e3) / 1e12
+        variant = tuned.get(gs.GS_OPT_RASTER_BWD if dom["name"] == "raster_bwd" else gs.GS_OPT_RASTER_FWD, 2)
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom["name"],
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom["name"], variant),
+                "kernel": "%s<%d>" % (dom["name"], variant),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"}
 
     # plain path: one view per launch, Adam after each view
     ctx2 = gs.Context(local)
