@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
   const float opacity = 1.f / (1.f + expf(-op));
   GaussCov gc;
   gauss_cov(lsc, quat, gc);  // view-independent: once per Gaussian
+  __shared__ float4 s_rec[8][32 * kRecStride];  // 256 threads: 8 warps x 32 records
   uint32_t total = 0;
   for (int v = 0; v < a.B; v++) {
     const ViewRec& V = a.views[v];
@@ -232,11 +233,24 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
           }
         }
       }
-      a.rec0[kRecStride * o] = r0;
-      a.rec1[kRecStride * o] = r1;
-      a.rec2[kRecStride * o] = make_float4(blue, ex.x, ex.y, depth);
       a.rec3[o] = make_int2(tiles ? radius : 0, (int)tiles);
       a.tiles[o] = tiles;
+    }
+    // the warp's 32 records (48 bytes each) go out through shared memory as
+    // 96 coalesced 16-byte stores instead of 3 x 32 stores at a 48-byte stride
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4* stage = s_rec[wid];
+    __syncwarp();
+    stage[3 * lane] = r0;
+    stage[3 * lane + 1] = r1;
+    stage[3 * lane + 2] = make_float4(blue, ex.x, ex.y, depth);
+    __syncwarp();
+    const int64_t g0 = g - lane;  // the warp's first Gaussian
+    float4* dst = a.rec0 + kRecStride * ((int64_t)v * a.stride + g0);
+#pragma unroll
+    for (int m = 0; m < kRecStride; m++) {
+      const int f = lane + 32 * m;
+      if (g0 + f / kRecStride < a.n) dst[f] = stage[f];
     }
     total += tiles;
   }

@@ -496,11 +496,14 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
   const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
   const float fpx = (float)px, fpy = (float)py0;
   const int64_t gplane = (int64_t)a.B * a.stride;
-  // lane j's record of the next batch (towards the front), loaded while the
-  // warp walks this one
+  // with 4+ pixels per thread, lane j's record of the next batch (towards
+  // the front) is loaded while the warp walks this one (measured faster
+  // there; slower with 1-2 pixels per thread, where the extra registers cost
+  // occupancy)
+  constexpr bool kPrefetch = PPT >= 4;
   float4 n0, n1, n2;
   uint32_t ng = 0;
-  {
+  if constexpr (kPrefetch) {
     const int i = max(0, total - 32) + lane;
     if (i < total) {
       ng = vals[rg.x + i];
@@ -513,6 +516,10 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
     bool hit = false;
     __syncwarp();
     if (i < bend) {
+      if constexpr (!kPrefetch) {
+        ng = vals[rg.x + i];
+        stage_one(a, v, ng, n0, n1, n2);
+      }
       s0[w][lane] = n0;
       s1[w][lane] = n1;
       s2[w][lane] = n2;
@@ -521,11 +528,13 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
     }
     uint32_t mask = __ballot_sync(0xffffffffu, hit);
     __syncwarp();
-    if (bstart > 0) {
-      const int k = max(0, bstart - 32) + lane;
-      if (k < bstart) {
-        ng = vals[rg.x + k];
-        stage_one(a, v, ng, n0, n1, n2);
+    if constexpr (kPrefetch) {
+      if (bstart > 0) {
+        const int k = max(0, bstart - 32) + lane;
+        if (k < bstart) {
+          ng = vals[rg.x + k];
+          stage_one(a, v, ng, n0, n1, n2);
+        }
       }
     }
     while (mask) {  // back to front
