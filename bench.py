@@ -187,8 +187,7 @@ class Trainer:
         c = self.ctx
         c.gs_project(self.p, self.n, self.deg, cams)
         c.gs_bin_sort()
-        c.gs_raster_fwd(img)
-        c.gs_l1_loss(img, target, self.loss, dimg)
+        c.gs_raster_fwd_l1(img, target, self.loss, dimg)
         c.gs_raster_bwd(self.p, self.n, self.deg, dimg, self.g)
         self.t += 1
         c.gs_adam(self.p, self.g, self.m, self.v, self.n, self.deg, HP, self.t)
@@ -254,8 +253,6 @@ def algorithmic_work(name, n, P, B, I, pairs, pixels):
         return "hbm", 24.0 * I
     if name == "tile_ranges":
         return "hbm", 8.0 * I
-    if name == "l1_loss":
-        return "hbm", 12.0 * 3 * pixels
     if name == "raster_fwd":
         return "alu", RASTER_OPS_FWD * pairs
     if name == "raster_bwd":

@@ -176,6 +176,17 @@ gs_status gs_bin_sort(gs_ctx* ctx);
  * Errors: GS_ESTATE (no gs_bin_sort), GS_EINVAL (images NULL), GS_ECUDA. */
 gs_status gs_raster_fwd(gs_ctx* ctx, float* images);
 
+/* gs_raster_fwd and gs_l1_loss(images, targets) in one pass: the compositing
+ * kernel also writes dL/dimages = sign(image - target) / count and one
+ * partial sum of |image - target| per warp, which a second kernel adds in a
+ * fixed order into *loss = mean |image - target| (count = 3 x pixels of the
+ * batch).  images may be NULL (not written); targets, loss and dL_dimages:
+ * device, image layout.  Same results as the two calls (the loss up to FP32
+ * summation order).
+ * Errors: GS_ESTATE (no gs_bin_sort), GS_EINVAL (NULL targets, loss or
+ * dL_dimages), GS_ECUDA. */
+gs_status gs_raster_fwd_l1(gs_ctx* ctx, float* images, const float* targets, float* loss, float* dL_dimages);
+
 /* Step 4, backward.  Given dL/dimages (device, image layout), walks every
  * tile list in reverse from each pixel's last contributor, recovering T by
  * division, and writes dL/dparams into grads->data (device, overwritten;
@@ -228,8 +239,8 @@ gs_status gs_adam(gs_ctx* ctx, gs_params* p, const gs_params* g, gs_params* m, g
 
 /* ---------------------------------------------------------------- CUDA graph */
 
-/* Capture one whole training step (gs_project, gs_bin_sort, gs_raster_fwd,
- * gs_l1_loss against `targets`, gs_raster_bwd, gs_adam) into a CUDA graph
+/* Capture one whole training step (gs_project, gs_bin_sort, gs_raster_fwd_l1
+ * against `targets`, gs_raster_bwd, gs_adam) into a CUDA graph
  * owned by the context, for replay with gs_train_graph_launch.  Needs a
  * context created with a fixed instance_capacity (nothing in the step then
  * reads the device on the host).  Runs the step once uncaptured first (no
@@ -331,7 +342,8 @@ typedef enum {
   GS_BUF_TFINAL = 6, /* float [pixels]: transmittance after the last contributor */
   GS_BUF_NLAST = 7,  /* uint32 [pixels]: 1 + list position of the last contributor */
   GS_BUF_G2D = 8,    /* float [9][B][N] planes: dL/d(mu_x, mu_y, A, B, C, opacity, r, g, b) */
-  GS_BUF_REC3 = 9,   /* int2 [B][N]: radius, tiles touched (0: culled) */
+  GS_BUF_REC3 = 9,   /* int4 [B][N]: radius, tiles touched (0: culled), tile rect
+                        x0 | x1 << 16 and y0 | y1 << 16 (half-open) */
   GS_BUF_SORT_CTRL = 10 /* uint32 [npass + 1]: control word of each sort pass; bit 1
                         set = pass skipped (its digit is the same for every key),
                         bit 0 = source buffer */

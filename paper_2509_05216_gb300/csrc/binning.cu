@@ -6,6 +6,14 @@
 // (bin << 32) | bits(depth).  Depths are positive FP32 values, so their bit
 // patterns order like the values.  The sort is stable, so equal keys keep the
 // emission order, which is increasing Gaussian index within a bin.
+//
+// Instances are emitted view by view (view v's instances form one segment),
+// and the sort orders each segment on its own by (bin - view's first bin,
+// depth): the bins of different views never interleave, so the view part of
+// the bin needs no radix pass (5 executed passes instead of 6 for 16 views
+// of 2048^2).
+#include <algorithm>
+
 #include "gs_internal.cuh"
 #include "launch.h"
 
@@ -13,13 +21,17 @@ namespace gs {
 
 // ---------------------------------------------------------------- scan
 
-// Exclusive scan of the per-block instance counts of the projection, one
-// block of 1024 threads looping over chunks; writes the total too.
+// Exclusive scan of the projection's per-(view, block) instance counts: block
+// v of the grid scans view v's nb counts (1024 threads looping over chunks)
+// and writes the view's total.
 __global__ void __launch_bounds__(1024) scan_block_sums_kernel(const uint32_t* __restrict__ sums,
                                                                 int64_t nb, uint32_t* __restrict__ offsets,
-                                                                uint64_t* __restrict__ total) {
+                                                                uint64_t* __restrict__ view_total) {
   __shared__ uint64_t warp_tot[32];
   __shared__ uint64_t carry;
+  const int v = blockIdx.x;
+  sums += (int64_t)v * nb;
+  offsets += (int64_t)v * nb;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -51,57 +63,77 @@ __global__ void __launch_bounds__(1024) scan_block_sums_kernel(const uint32_t* _
     if (threadIdx.x == 1023) carry = excl + x;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *total = carry;
+  if (threadIdx.x == 0) view_total[v] = carry;
 }
 
-void launch_scan_block_sums(const uint32_t* sums, int64_t nb, uint32_t* offsets, uint64_t* total,
-                            cudaStream_t s) {
-  scan_block_sums_kernel<<<1, 1024, 0, s>>>(sums, nb, offsets, total);
+// Segment offsets: seg[v] = first instance of view v, seg[B] = *total.
+__global__ void segment_offsets_kernel(const uint64_t* __restrict__ view_total, int B, uint32_t* __restrict__ seg,
+                                       uint64_t* __restrict__ total) {
+  if (threadIdx.x != 0) return;
+  uint64_t run = 0;
+  for (int v = 0; v < B; v++) {
+    seg[v] = (uint32_t)min(run, (uint64_t)0xffffffffu);
+    run += view_total[v];
+  }
+  seg[B] = (uint32_t)min(run, (uint64_t)0xffffffffu);
+  *total = run;
+}
+
+void launch_scan_block_sums(const uint32_t* sums, int64_t nb, int B, uint32_t* offsets, uint64_t* view_total,
+                            uint32_t* seg, uint64_t* total, cudaStream_t s) {
+  scan_block_sums_kernel<<<B, 1024, 0, s>>>(sums, nb, offsets, view_total);
+  segment_offsets_kernel<<<1, 32, 0, s>>>(view_total, B, seg, total);
 }
 
 // ---------------------------------------------------------------- duplicate
 
-// Same block partition as the projection (256 Gaussians per block, all views).
-// Each warp emits the instances of its 32 Gaussians view by view: the
-// warp's (Gaussian, view) items are expanded cooperatively, lane j writing
-// output position base + 32 i + j of the chunk i, so every store of keys and
-// values is coalesced.  Within a view the order is (Gaussian, ty, tx), so in
-// every bin the instances appear in increasing Gaussian index, which the
-// stable sort preserves for equal keys.
+// Same block partition as the projection (256 Gaussians per block).  Each
+// warp emits the instances of its 32 Gaussians view by view into view v's
+// segment (offset: the view's first instance + the block's scanned count +
+// the earlier warps of the block): the warp's (Gaussian, view) items are
+// expanded cooperatively, lane j writing output position base + 32 i + j of
+// the chunk i, so every store of keys and values is coalesced.  Within a
+// view the order is (Gaussian, ty, tx), so in every bin the instances appear
+// in increasing Gaussian index, which the stable sort preserves for equal
+// keys.
 __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
+  __shared__ uint32_t wtot[kMaxViews][8];
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = g < a.n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t mine = 0;
-  if (live)
-    for (int v = 0; v < a.B; v++) mine += a.tiles[(int64_t)v * a.stride + g];
-  // per-warp totals -> block exclusive scan over warps
-  __shared__ uint32_t wsum[32];
-  const uint32_t wtot = __reduce_add_sync(0xffffffffu, mine);
-  if (lane == 0) wsum[wid] = wtot;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    uint32_t w = lane < nw ? wsum[lane] : 0u;
-    uint32_t winc = w;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, winc, off);
-      if (lane >= off) winc += y;
-    }
-    wsum[lane] = winc - w;
-  }
-  __syncthreads();
-  int64_t base = (int64_t)a.block_offsets[blockIdx.x] + wsum[wid];
-  if (wtot == 0) return;
-  if (base + wtot > a.capacity) {
-    if (lane == 0) atomicOr(a.status, kStatusCapacity);
-    return;
-  }
-  const unsigned lt = (1u << lane) - 1u;
+  const int64_t nb = gridDim.x;
   for (int v = 0; v < a.B; v++) {
+    const uint32_t c = live ? a.tiles[(int64_t)v * a.stride + g] : 0u;
+    const uint32_t t = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) wtot[v][wid] = t;
+  }
+  __syncthreads();
+  // the next view's count, rect and depth are loaded while this view's
+  // instances are written
+  uint32_t n_cnt = 0, n_dbits = 0;
+  int4 n_r3 = make_int4(0, 0, 0, 0);
+  auto load_view = [&](int v) {
     const int64_t o = (int64_t)v * a.stride + g;
-    const uint32_t cnt = live ? a.tiles[o] : 0u;
+    n_cnt = live ? a.tiles[o] : 0u;
+    if (n_cnt) {
+      n_r3 = a.rec3[o];
+      n_dbits = __float_as_uint(a.rec2[kRecStride * o].w);
+    }
+  };
+  load_view(0);
+  for (int v = 0; v < a.B; v++) {
+    const uint32_t cnt = n_cnt, dbits = n_dbits;
+    const int4 r3 = n_r3;
+    if (v + 1 < a.B) load_view(v + 1);
+    const uint32_t vtot = wtot[v][wid];
+    if (vtot == 0) continue;
+    uint32_t wpre = 0;
+    for (int w = 0; w < wid; w++) wpre += wtot[v][w];
+    const int64_t base = (int64_t)a.seg[v] + a.block_offsets[(int64_t)v * nb + blockIdx.x] + wpre;
+    if (base + vtot > a.capacity) {
+      if (lane == 0) atomicOr(a.status, kStatusCapacity);
+      continue;
+    }
     // exclusive offsets of the warp's items in this view
     uint32_t inc = cnt;
 #pragma unroll
@@ -110,17 +142,11 @@ __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
       if (lane >= off) inc += y;
     }
     const uint32_t excl = inc - cnt;
-    const uint32_t vtot = __shfl_sync(0xffffffffu, inc, 31);
-    if (vtot == 0) continue;
     const ViewRec& V = a.views[v];
-    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-    uint32_t dbits = 0;
-    if (cnt) {
-      const float4 r0 = a.rec0[kRecStride * o];
-      tile_rect(V, r0.x, r0.y, a.rec3[o].x, x0, x1, y0, y1);
-      dbits = __float_as_uint(a.rec2[kRecStride * o].w);
-    }
-    const int rw = x1 - x0;
+    // the projection's tile rect
+    const int x0 = cnt ? (r3.z & 0xffff) : 0;
+    const int rw = cnt ? (int)((uint32_t)r3.z >> 16) - x0 : 0;
+    const int y0 = cnt ? (r3.w & 0xffff) : 0;
     for (uint32_t q0 = 0; q0 < vtot; q0 += 32) {
       const uint32_t q = q0 + lane;
       // owner: the last lane whose exclusive offset is <= q
@@ -146,9 +172,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
         a.vals[base + q] = (uint32_t)(g - lane + own);
       }
     }
-    base += vtot;
   }
-  (void)lt;
 }
 
 void launch_duplicate(const DuplicateArgs& a, cudaStream_t s) {
@@ -171,57 +195,90 @@ constexpr uint32_t kValueMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 20;  // look-back rounds before giving up (about a second)
 constexpr int kLookWindow = 16;       // statuses read per look-back round
 
-int64_t sort_partitions(int64_t count, int items) {
+// Partitions never straddle a view's segment: at most one partial
+// partition per segment.
+int64_t sort_partitions(int64_t count, int items, int segments) {
   const int64_t tile = (int64_t)kSortThreads * items;
-  return (count + tile - 1) / tile;
+  return (count + tile - 1) / tile + segments;
 }
 
-size_t sort_lookback_bytes(int64_t count, int items) {
-  const int64_t parts = sort_partitions(count, items);
+size_t sort_lookback_bytes(int64_t count, int items, int segments) {
+  const int64_t parts = sort_partitions(count, items, segments);
   return (size_t)(parts > 0 ? parts : 1) * kRadix * sizeof(uint32_t);
 }
 
-// Digit counts of every pass in one read of the keys.  hist: [npass][256].
-__global__ void __launch_bounds__(256) digit_histogram_kernel(const uint64_t* __restrict__ keys,
-                                                               const uint64_t* __restrict__ count_ptr,
-                                                               int64_t capacity, int npass,
-                                                               uint32_t* __restrict__ hist) {
+// Largest u in [0, B) with off[u] <= i (off nondecreasing): for i below
+// off[B], the non-empty segment holding i.
+__device__ __forceinline__ int segment_of(const uint32_t* off, int B, uint64_t i) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((uint64_t)off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Digit counts of every pass of every view in one read of the keys.  hist:
+// [B][npass][256], digits of key - (view's first bin << 32).  Block (x, v)
+// counts view v's segment with a grid stride over the x blocks of the view,
+// in shared memory; the tile digits stay constant over long runs of keys
+// (emission order), so their counts are first aggregated over the lanes
+// holding the same digit.
+__global__ void __launch_bounds__(256) digit_histogram_kernel(SortArgs a) {
   __shared__ uint32_t sh[8][kRadix];
   for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
-  const int64_t count = min((int64_t)*count_ptr, capacity);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = keys[i];
-    for (int p = 0; p < npass; p++) atomicAdd(&sh[p][(k >> (kRadixBits * p)) & (kRadix - 1)], 1u);
+  const int v = blockIdx.y;
+  const int64_t count = min((int64_t)*a.count, a.capacity);
+  const int64_t lo = min((int64_t)a.seg[v], count), hi = min((int64_t)a.seg[v + 1], count);
+  const uint64_t kb = (uint64_t)a.views[v].tile_offset << 32;
+  const uint64_t* __restrict__ keys = a.keys[0];
+  const int npass = a.npass, lane = threadIdx.x & 31;
+  for (int64_t i0 = lo + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < hi;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    const bool ok = i < hi;
+    const uint64_t k = ok ? keys[i] - kb : 0ull;
+    for (int p = 0; p < npass; p++) {
+      const uint32_t dg = (uint32_t)(k >> (kRadixBits * p)) & (kRadix - 1);
+      if (p < 4) {
+        if (ok) atomicAdd(&sh[p][dg], 1u);
+      } else {
+        const unsigned peers = __match_any_sync(0xffffffffu, ok ? dg : (uint32_t)kRadix);
+        if (ok && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&sh[p][dg], (uint32_t)__popc(peers));
+      }
+    }
   }
   __syncthreads();
+  uint32_t* h = a.hist + (int64_t)v * npass * kRadix;
   for (int i = threadIdx.x; i < npass * kRadix; i += blockDim.x) {
     const uint32_t c = (&sh[0][0])[i];
-    if (c) atomicAdd(&hist[i], c);
+    if (c) atomicAdd(&h[i], c);
   }
 }
 
-// Passes whose digit histogram is a single bucket leave the order unchanged
+// Passes where every view's keys share one digit leave the order unchanged
 // and are skipped.  ctrl[p] (written once per sort by digit_scan_kernel):
 // bit 0 = which ping-pong buffer holds the keys before pass p (p == npass:
 // the sorted result), bit 1 = pass p is skipped.
 constexpr uint32_t kCtrlParity = 1u, kCtrlTrivial = 2u;
 
-// One LSD pass: rank keys of the partition by digit (stable), find the
-// partition's offset for each digit by decoupled look-back over the earlier
-// partitions (bounded waits), then scatter through shared memory so that the
-// global writes are coalesced.  Keys are loaded up front (all loads in
-// flight before ranking); keys and then values go through one shared buffer,
-// which keeps the block at 46 KB of shared memory and 64 registers per thread
-// (four blocks per SM).  hist_pass: exclusive digit offsets of this pass.
+// One LSD pass, each view's segment sorted on its own: a partition lies in
+// one segment; rank its keys by digit of key - (view's first bin << 32)
+// (stable), find its offset for each digit by decoupled look-back over the
+// earlier partitions of its segment (bounded waits), then scatter through
+// shared memory so that the global writes are coalesced.  Keys are loaded up
+// front (all loads in flight before ranking); keys and then values go
+// through one shared buffer (46 KB for 16 keys per thread).
 template <int ITEMS>
 struct SortSmem {
   static constexpr int kTile = kSortThreads * ITEMS;
   uint32_t warp_hist[kSortWarps][kRadix];  // per-warp digit counts -> offsets
   uint32_t digit_start[kRadix];            // exclusive scan of the tile's digit counts
   uint32_t global_base[kRadix];            // global destination of the digit's first key
-  uint32_t part;
+  uint32_t wtot[kSortWarps];
+  uint32_t part, seg, seg_lo, seg_hi, first_part;
+  uint64_t key_base;
   int timed_out;
   uint64_t buf[kTile];                     // keys, then values, in tile-sorted order
   uint8_t dig[kTile];                      // digit of each tile-sorted position
@@ -234,9 +291,8 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem<ITEMS>& sm = *reinterpret_cast<SortSmem<ITEMS>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t count = min((int64_t)*a.count, a.capacity);
   const uint32_t ctrl = a.ctrl[pass];
-  if (ctrl & kCtrlTrivial) return;  // whole block: this digit is the same for every key
+  if (ctrl & kCtrlTrivial) return;  // whole block: every view has one digit here
   const int par = (int)(ctrl & kCtrlParity);
   // selects, not a dynamically indexed parameter array (which would be
   // copied to local memory)
@@ -245,33 +301,46 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   uint64_t* __restrict__ kout = par ? a.keys[0] : a.keys[1];
   uint32_t* __restrict__ vout = par ? a.vals[0] : a.vals[1];
   const int shift = kRadixBits * pass;
-  const uint32_t* __restrict__ hist_pass = a.hist_scan + pass * kRadix;
-  uint32_t* lookback = a.lookback + (size_t)pass * a.lookback_stride;
-  int* status = a.status;
+  const uint32_t nparts = a.part_off[a.B];
   if (tid == 0) {
-    sm.part = atomicAdd(a.counters + pass, 1u);
+    const uint32_t part = atomicAdd(a.counters + pass, 1u);
+    sm.part = part;
     sm.timed_out = 0;
+    if (part < nparts) {
+      const int u = segment_of(a.part_off, a.B, part);
+      const uint32_t cap = (uint32_t)min(a.capacity, (int64_t)0xffffffff);
+      sm.seg = (uint32_t)u;
+      sm.first_part = a.part_off[u];
+      sm.seg_lo = min(a.seg[u], cap);
+      sm.seg_hi = min(a.seg[u + 1], cap);
+      sm.key_base = (uint64_t)a.views[u].tile_offset << 32;
+    }
   }
   for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&sm.warp_hist[0][0])[i] = 0;
   __syncthreads();
   const uint32_t part = sm.part;
-  const int64_t nparts = (count + kSortTile - 1) / kSortTile;
-  if ((int64_t)part >= nparts) return;
-  const int64_t base = (int64_t)part * kSortTile;
-  const int64_t wbase = base + (int64_t)wid * kSortItems * 32 + lane;  // item i at wbase + 32 i
+  if (part >= nparts) return;
+  const int v = (int)sm.seg;
+  const uint32_t lp0 = part - sm.first_part;  // partition index inside the segment
+  const int64_t base = (int64_t)sm.seg_lo + (int64_t)lp0 * kSortTile;
+  const int n_here = (int)min((int64_t)kSortTile, (int64_t)sm.seg_hi - base);
+  const uint64_t kb = sm.key_base;
+  const uint32_t* __restrict__ hist_pass = a.hist_scan + ((int64_t)v * a.npass + pass) * kRadix;
+  uint32_t* lookback = a.lookback + (size_t)pass * a.lookback_stride;
+  const int wl = wid * kSortItems * 32 + lane;  // item i at base + wl + 32 i
 
   uint64_t key[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    const int64_t p = wbase + 32 * i;
-    key[i] = p < count ? kin[p] : ~0ull;
+    const int p = wl + 32 * i;
+    key[i] = p < n_here ? kin[base + p] - kb : ~0ull;
   }
   // stable rank inside the warp (warp-striped order), 16-bit per item
   uint32_t rk[kSortItems / 2];
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    const bool ok = wbase + 32 * i < count;
+    const bool ok = wl + 32 * i < n_here;
     const uint32_t d = ok ? (uint32_t)(key[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     uint32_t r = 0, before = 0;
@@ -286,7 +355,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   }
   __syncthreads();
 
-  // per digit: counts over warps -> warp offsets; publish the tile count
+  // per digit: counts over warps -> warp offsets; publish the partition count
   const uint32_t d = tid;  // kSortThreads == kRadix
   uint32_t tile_count = 0;
 #pragma unroll
@@ -296,8 +365,8 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     tile_count += c;
   }
   volatile uint32_t* lb = lookback;
-  lb[(int64_t)part * kRadix + d] = (part == 0 ? kFlagPrefix : kFlagAggregate) | tile_count;
-  // digit starts inside the tile (block exclusive scan over the 256 digits)
+  lb[(int64_t)part * kRadix + d] = (lp0 == 0 ? kFlagPrefix : kFlagAggregate) | tile_count;
+  // digit starts inside the partition (block exclusive scan over the 256 digits)
   {
     uint32_t inc = tile_count;
 #pragma unroll
@@ -305,34 +374,34 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
       uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
       if (lane >= off) inc += y;
     }
-    __shared__ uint32_t wtot[kSortWarps];
-    if (lane == 31) wtot[wid] = inc;
+    if (lane == 31) sm.wtot[wid] = inc;
     __syncthreads();
     uint32_t wpre = 0;
-    for (int w = 0; w < wid; w++) wpre += wtot[w];
+    for (int w = 0; w < wid; w++) wpre += sm.wtot[w];
     sm.digit_start[d] = wpre + inc - tile_count;
   }
   __syncthreads();
-  const int n_here = (int)((count - base) < kSortTile ? (count - base) : kSortTile);
-  // keys -> tile-sorted positions in shared memory (frees the key registers
-  // before the look-back); remember the positions for the values
+  // keys -> partition-sorted positions in shared memory (frees the key
+  // registers before the look-back); remember the positions for the values
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    const bool ok = wbase + 32 * i < count;
+    const bool ok = wl + 32 * i < n_here;
     const uint32_t r = (rk[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-    uint32_t lp = 0xffffu;
+    uint32_t lpos = 0xffffu;
     if (ok) {
       const uint32_t dd = (uint32_t)(key[i] >> shift) & (kRadix - 1);
-      lp = sm.digit_start[dd] + sm.warp_hist[wid][dd] + r;
-      sm.buf[lp] = key[i];
-      sm.dig[lp] = (uint8_t)dd;
+      lpos = sm.digit_start[dd] + sm.warp_hist[wid][dd] + r;
+      sm.buf[lpos] = key[i] + kb;
+      sm.dig[lpos] = (uint8_t)dd;
     }
-    if (i & 1) rk[i >> 1] = (rk[i >> 1] & 0xffffu) | (lp << 16); else rk[i >> 1] = (rk[i >> 1] & 0xffff0000u) | lp;
+    if (i & 1) rk[i >> 1] = (rk[i >> 1] & 0xffffu) | (lpos << 16); else rk[i >> 1] = (rk[i >> 1] & 0xffff0000u) | lpos;
   }
-  // decoupled look-back over the earlier partitions, kLookWindow statuses
-  // per round trip; a status that is not ready yet is re-read (bounded)
+  // decoupled look-back over the earlier partitions of this segment,
+  // kLookWindow statuses per round trip; a status that is not ready yet is
+  // re-read (bounded)
   uint32_t excl = 0;
-  if (part > 0) {
+  if (lp0 > 0) {
+    const int64_t first = (int64_t)sm.first_part;
     int64_t j = (int64_t)part - 1;
     int rounds = 0;
     bool found = false;
@@ -340,7 +409,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
       uint32_t w[kLookWindow];
 #pragma unroll
       for (int t = 0; t < kLookWindow; t++)
-        w[t] = (j - t >= 0) ? (uint32_t)lb[(j - t) * kRadix + d] : (uint32_t)kFlagPrefix;
+        w[t] = (j - t >= first) ? (uint32_t)lb[(j - t) * kRadix + d] : (uint32_t)kFlagPrefix;
       int used = 0;
       bool stalled = false;
 #pragma unroll
@@ -356,38 +425,39 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
         if (flag == kFlagPrefix) found = true;
       }
       j -= used;
-      if (!found && (++rounds > kSpinLimit || j < 0)) {
+      if (!found && ++rounds > kSpinLimit) {
         sm.timed_out = 1;
         break;
       }
     }
     lb[(int64_t)part * kRadix + d] = kFlagPrefix | ((excl + tile_count) & kValueMask);
   }
-  sm.global_base[d] = hist_pass[d] + excl;
+  sm.global_base[d] = sm.seg_lo + hist_pass[d] + excl;
   __syncthreads();
   if (sm.timed_out) {
-    if (tid == 0) atomicOr(status, kStatusTimeout);
+    if (tid == 0) atomicOr(a.status, kStatusTimeout);
     return;
   }
-  for (int lp = tid; lp < n_here; lp += kSortThreads) {
-    const uint32_t dd = sm.dig[lp];
-    const uint32_t dst = sm.global_base[dd] + (lp - sm.digit_start[dd]);
-    if (dst < (uint64_t)count) kout[dst] = sm.buf[lp];
+  const uint32_t hi = sm.seg_hi;
+  for (int q = tid; q < n_here; q += kSortThreads) {
+    const uint32_t dd = sm.dig[q];
+    const uint32_t dst = sm.global_base[dd] + ((uint32_t)q - sm.digit_start[dd]);
+    if (dst < hi) kout[dst] = sm.buf[q];
   }
   __syncthreads();
   // values through the same buffer
   uint32_t* vb = reinterpret_cast<uint32_t*>(sm.buf);
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
-    const int64_t p = wbase + 32 * i;
-    const uint32_t lp = (rk[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-    if (p < count) vb[lp] = vin[p];
+    const int p = wl + 32 * i;
+    const uint32_t lpos = (rk[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
+    if (p < n_here) vb[lpos] = vin[base + p];
   }
   __syncthreads();
-  for (int lp = tid; lp < n_here; lp += kSortThreads) {
-    const uint32_t dd = sm.dig[lp];
-    const uint32_t dst = sm.global_base[dd] + (lp - sm.digit_start[dd]);
-    if (dst < (uint64_t)count) vout[dst] = vb[lp];
+  for (int q = tid; q < n_here; q += kSortThreads) {
+    const uint32_t dd = sm.dig[q];
+    const uint32_t dst = sm.global_base[dd] + ((uint32_t)q - sm.digit_start[dd]);
+    if (dst < hi) vout[dst] = vb[q];
   }
 }
 
@@ -407,7 +477,7 @@ static void launch_pass(const SortArgs& a, int pass, int64_t grid, cudaStream_t 
 }
 
 void launch_onesweep_pass(const SortArgs& a, int pass, int items, cudaStream_t s) {
-  const int64_t grid = sort_partitions(a.capacity, items);
+  const int64_t grid = sort_partitions(a.capacity, items, a.B);
   if (grid <= 0) return;
   switch (items) {
     case 12: launch_pass<12, 4>(a, pass, grid, s); break;
@@ -417,20 +487,18 @@ void launch_onesweep_pass(const SortArgs& a, int pass, int items, cudaStream_t s
   }
 }
 
-// Exclusive scan of each pass's 256 digit counts, and the pass control
-// words (one block of 256 threads, passes in order).
-__global__ void __launch_bounds__(kRadix) digit_scan_kernel(const uint32_t* __restrict__ hist,
-                                                             const uint64_t* __restrict__ count_ptr,
-                                                             int64_t capacity, int npass,
-                                                             uint32_t* __restrict__ scanned,
-                                                             uint32_t* __restrict__ ctrl) {
+// Exclusive scan of each (view, pass)'s 256 digit counts (block v of the
+// grid: view v), and whether the view's keys share one digit in the pass.
+__global__ void __launch_bounds__(kRadix) digit_scan_kernel(SortArgs a) {
   __shared__ uint32_t wsum[kRadix / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t count = (uint32_t)min((int64_t)*count_ptr, capacity);
-  uint32_t parity = 0;
-  for (int p = 0; p < npass; p++) {
-    const uint32_t c = hist[p * kRadix + tid];
-    const bool trivial = __syncthreads_or(c == count) != 0;
+  const int v = blockIdx.x;
+  const uint32_t cap = (uint32_t)min(a.capacity, (int64_t)0xffffffff);
+  const uint32_t cnt = min(a.seg[v + 1], cap) - min(a.seg[v], cap);
+  for (int p = 0; p < a.npass; p++) {
+    const int64_t o = ((int64_t)v * a.npass + p) * kRadix + tid;
+    const uint32_t c = a.hist[o];
+    const bool single = __syncthreads_or(c == cnt) != 0;
     uint32_t inc = c;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -441,28 +509,54 @@ __global__ void __launch_bounds__(kRadix) digit_scan_kernel(const uint32_t* __re
     __syncthreads();
     uint32_t pre = 0;
     for (int w = 0; w < wid; w++) pre += wsum[w];
-    scanned[p * kRadix + tid] = pre + inc - c;
-    if (tid == 0) ctrl[p] = parity | (trivial ? kCtrlTrivial : 0u);
-    if (!trivial) parity ^= 1u;
+    a.hist_scan[o] = pre + inc - c;
+    if (tid == 0) a.single[v * 8 + p] = single ? 1u : 0u;
     __syncthreads();
   }
-  if (tid == 0) ctrl[npass] = parity;
 }
 
-void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, cudaStream_t s) {
+// Pass control words and the first partition of every view's segment (one
+// thread; B <= 64 views, npass <= 8).
+__global__ void sort_control_kernel(SortArgs a, int items) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t parity = 0;
+  for (int p = 0; p < a.npass; p++) {
+    bool trivial = true;
+    for (int v = 0; v < a.B; v++) trivial &= a.single[v * 8 + p] != 0;
+    a.ctrl[p] = parity | (trivial ? kCtrlTrivial : 0u);
+    if (!trivial) parity ^= 1u;
+  }
+  a.ctrl[a.npass] = parity;
+  const uint32_t cap = (uint32_t)min(a.capacity, (int64_t)0xffffffff);
+  const uint32_t tile = (uint32_t)(kSortThreads * items);
+  uint32_t run = 0;
+  for (int v = 0; v < a.B; v++) {
+    a.part_off[v] = run;
+    const uint32_t cnt = min(a.seg[v + 1], cap) - min(a.seg[v], cap);
+    run += (cnt + tile - 1) / tile;
+  }
+  a.part_off[a.B] = run;
+}
+
+void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, int items, cudaStream_t s) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // about 8 blocks per SM over all views, at least one per view
   int64_t want = (grid_hint + 4095) / 4096;
-  const unsigned blocks = (unsigned)(want < 1 ? 1 : (want > (int64_t)sms * 8 ? (int64_t)sms * 8 : want));
-  digit_histogram_kernel<<<blocks, 256, 0, s>>>(a.keys[0], a.count, a.capacity, a.npass, a.hist);
-  digit_scan_kernel<<<1, kRadix, 0, s>>>(a.hist, a.count, a.capacity, a.npass, a.hist_scan, a.ctrl);
+  want = want < 1 ? 1 : (want > (int64_t)sms * 8 ? (int64_t)sms * 8 : want);
+  const unsigned per_view = (unsigned)std::max<int64_t>(1, want / a.B);
+  digit_histogram_kernel<<<dim3(per_view, a.B), 256, 0, s>>>(a);
+  digit_scan_kernel<<<a.B, kRadix, 0, s>>>(a);
+  sort_control_kernel<<<1, 32, 0, s>>>(a, items);
 }
 
 // ---------------------------------------------------------------- tile ranges
 
 // ranges[bin] = [first, last + 1) of the bin in the sorted keys; block 0
-// also records which buffers hold the sorted list.
+// also records which buffers hold the sorted list.  Each key is loaded once:
+// a lane compares its bin with its neighbours' through shuffles (the warp's
+// edge lanes load one neighbour each).
 __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __restrict__ ranges) {
   const int64_t count = min((int64_t)*a.count, a.capacity);
   const int par = (int)(a.ctrl[a.npass] & kCtrlParity);
@@ -471,12 +565,19 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __r
     *a.sorted_keys = keys;
     *a.sorted_vals = par ? a.vals[1] : a.vals[0];
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t bin = (uint32_t)(keys[i] >> 32);
-    if ((int64_t)bin >= a.bins) continue;  // only after a capacity overflow (reported by the status)
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != bin) ranges[bin].x = (uint32_t)i;
-    if (i == count - 1 || (uint32_t)(keys[i + 1] >> 32) != bin) ranges[bin].y = (uint32_t)(i + 1);
+  const int lane = threadIdx.x & 31;
+  const uint32_t none = 0xffffffffu;
+  for (int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; w0 < count;
+       w0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = w0 + lane;
+    const uint32_t bin = i < count ? (uint32_t)(keys[i] >> 32) : none;
+    uint32_t prev = __shfl_up_sync(0xffffffffu, bin, 1);
+    uint32_t next = __shfl_down_sync(0xffffffffu, bin, 1);
+    if (lane == 0) prev = i > 0 && i - 1 < count ? (uint32_t)(keys[i - 1] >> 32) : none;
+    if (lane == 31) next = i + 1 < count ? (uint32_t)(keys[i + 1] >> 32) : none;
+    if (i >= count || (int64_t)bin >= a.bins) continue;  // (bins only overflow after a capacity overflow)
+    if (prev != bin) ranges[bin].x = (uint32_t)i;
+    if (next != bin) ranges[bin].y = (uint32_t)(i + 1);
   }
 }
 

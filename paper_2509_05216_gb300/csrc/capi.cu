@@ -366,9 +366,9 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   const int64_t nb = (n + project_fwd_block() - 1) / project_fwd_block();
   GS_TRY(ensure(c, c->views, sizeof(ViewRec) * B));
   GS_TRY(ensure(c, c->rec, sizeof(float4) * kRecStride * B * stride));
-  GS_TRY(ensure(c, c->rec3, sizeof(int2) * B * stride));
+  GS_TRY(ensure(c, c->rec3, sizeof(int4) * B * stride));
   GS_TRY(ensure(c, c->tiles, sizeof(uint32_t) * B * stride));
-  GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * nb));
+  GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * B * nb));
   if (c->capturing) {
     // a captured step copies the cameras from the pinned staging area at its start
   } else {
@@ -384,7 +384,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   a.rec0 = P<float4>(c->rec);
   a.rec1 = P<float4>(c->rec) + 1;
   a.rec2 = P<float4>(c->rec) + 2;
-  a.rec3 = P<int2>(c->rec3);
+  a.rec3 = P<int4>(c->rec3);
   a.tiles = P<uint32_t>(c->tiles);
   a.block_sums = P<uint32_t>(c->block_sums);
   {
@@ -408,12 +408,21 @@ gs_status gs_bin_sort(gs_ctx* c) {
   if (!c->projected) return fail(c, GS_ESTATE, "gs_bin_sort needs gs_project first");
   set_device(c);
   c->sorted = c->rastered = false;
-  GS_TRY(ensure(c, c->block_offsets, sizeof(uint32_t) * c->nblocks));
-  GS_TRY(ensure(c, c->total, sizeof(uint64_t)));
+  const int B = c->B;
+  GS_TRY(ensure(c, c->block_offsets, sizeof(uint32_t) * B * c->nblocks));
+  // device words: total (u64) | view totals (u64 x 64) | seg (u32 x 65) | part_off (u32 x 65) | ctrl (u32 x 16)
+  //               | single-digit flags (u32 x 64 x 8)
+  GS_TRY(ensure(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
+                                 sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
+  uint64_t* total = P<uint64_t>(c->total);
+  uint64_t* view_total = total + 1;
+  uint32_t* seg = reinterpret_cast<uint32_t*>(view_total + kMaxViews);
+  uint32_t* part_off = seg + kMaxViews + 1;
+  uint32_t* ctrl = part_off + kMaxViews + 1;
   {
-    LaunchScope ls(c, "scan_block_sums");
-    launch_scan_block_sums(P<uint32_t>(c->block_sums), c->nblocks, P<uint32_t>(c->block_offsets),
-                           P<uint64_t>(c->total), c->stream);
+    LaunchScope ls(c, "scan_block_sums", 2);
+    launch_scan_block_sums(P<uint32_t>(c->block_sums), c->nblocks, B, P<uint32_t>(c->block_offsets), view_total,
+                           seg, total, c->stream);
   }
   GS_CHECK_LAUNCH(c);
   // capacity: the exact count (grow-on-demand contexts read it, one stream
@@ -435,13 +444,17 @@ gs_status gs_bin_sort(gs_ctx* c) {
   GS_TRY(ensure(c, c->vals0, sizeof(uint32_t) * cap));
   GS_TRY(ensure(c, c->vals1, sizeof(uint32_t) * cap));
   GS_TRY(ensure(c, c->ranges, sizeof(uint2) * c->bins));
-  int bin_bits = 0;
-  while (((int64_t)1 << bin_bits) < c->bins) bin_bits++;
-  const int npass = (32 + bin_bits + 7) / 8;  // the 32 depth bits and the bin bits
+  // each view is sorted on its own: the 32 depth bits and the bits of the
+  // largest tile index inside a view
+  int64_t most_tiles = 1;
+  for (int v = 0; v < B; v++) most_tiles = std::max<int64_t>(most_tiles, (int64_t)c->views_h[v].gw * c->views_h[v].gh);
+  int tile_bits = 0;
+  while (((int64_t)1 << tile_bits) < most_tiles) tile_bits++;
+  const int npass = (32 + tile_bits + 7) / 8;
   c->sort_passes = npass;
-  const size_t lb = sort_lookback_bytes(cap, c->sort_items);
-  GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
-  GS_TRY(ensure(c, c->hist_scan, sizeof(uint32_t) * (8 * 256 + 16)));
+  const size_t lb = sort_lookback_bytes(cap, c->sort_items, B);
+  GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * (size_t)B * 8 * 256));
+  GS_TRY(ensure(c, c->hist_scan, sizeof(uint32_t) * (size_t)B * 8 * 256));
   GS_TRY(ensure(c, c->lookback, lb * npass));
   GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
   GS_TRY(ensure(c, c->sorted_slots, 2 * sizeof(void*)));
@@ -453,9 +466,10 @@ gs_status gs_bin_sort(gs_ctx* c) {
   d.B = c->B;
   d.rec0 = P<float4>(c->rec);
   d.rec2 = P<float4>(c->rec) + 2;
-  d.rec3 = P<int2>(c->rec3);
+  d.rec3 = P<int4>(c->rec3);
   d.tiles = P<uint32_t>(c->tiles);
   d.block_offsets = P<uint32_t>(c->block_offsets);
+  d.seg = seg;
   d.keys = P<uint64_t>(c->keys0);
   d.vals = P<uint32_t>(c->vals0);
   d.capacity = cap;
@@ -471,12 +485,17 @@ gs_status gs_bin_sort(gs_ctx* c) {
   sa.keys[1] = P<uint64_t>(c->keys1);
   sa.vals[0] = P<uint32_t>(c->vals0);
   sa.vals[1] = P<uint32_t>(c->vals1);
-  sa.count = P<uint64_t>(c->total);
+  sa.count = total;
   sa.capacity = cap;
   sa.bins = c->bins;
+  sa.B = B;
+  sa.views = P<ViewRec>(c->views);
+  sa.seg = seg;
+  sa.part_off = part_off;
   sa.hist = P<uint32_t>(c->hist);
   sa.hist_scan = P<uint32_t>(c->hist_scan);
-  sa.ctrl = P<uint32_t>(c->hist_scan) + 8 * 256;
+  sa.ctrl = ctrl;
+  sa.single = ctrl + 16;
   sa.lookback = P<uint32_t>(c->lookback);
   sa.lookback_stride = lb / sizeof(uint32_t);
   sa.counters = P<uint32_t>(c->counters);
@@ -484,12 +503,12 @@ gs_status gs_bin_sort(gs_ctx* c) {
   sa.status = c->status_d;
   sa.sorted_keys = reinterpret_cast<const uint64_t**>(c->sorted_slots.p);
   sa.sorted_vals = reinterpret_cast<const uint32_t**>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
-  GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * 8 * 256, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * (size_t)B * npass * 256, c->stream));
   GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * 8, c->stream));
   GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * npass, c->stream));
   {
-    LaunchScope ls(c, "digit_histogram", 2);
-    launch_digit_histogram(sa, cap, c->stream);
+    LaunchScope ls(c, "digit_histogram", 3);
+    launch_digit_histogram(sa, cap, c->sort_items, c->stream);
   }
   GS_CHECK_LAUNCH(c);
   for (int p = 0; p < npass; p++) {
@@ -535,6 +554,41 @@ gs_status gs_raster_fwd(gs_ctx* c, float* images) {
   {
     LaunchScope ls(c, "raster_fwd");
     launch_raster_fwd(r, c->bins, c->raster_fwd, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  c->rastered = true;
+  return GS_OK;
+}
+
+gs_status gs_raster_fwd_l1(gs_ctx* c, float* images, const float* targets, float* loss, float* dL_dimages) {
+  if (!c) return GS_EINVAL;
+  if (!c->sorted) return fail(c, GS_ESTATE, "gs_raster_fwd_l1 needs gs_bin_sort first");
+  if (!targets || !loss || !dL_dimages) return fail(c, GS_EINVAL, "targets, loss and dL_dimages must not be NULL");
+  set_device(c);
+  GS_TRY(ensure(c, c->tfinal, sizeof(float) * c->pixels));
+  GS_TRY(ensure(c, c->nlast, sizeof(uint32_t) * c->pixels));
+  const int64_t nparts = raster_fwd_warps(c->bins, c->raster_fwd);
+  // per-warp partial sums, then the 256 block sums of the finishing reduction
+  const size_t part_bytes = (sizeof(float) * std::max<int64_t>(nparts, 1) + 255) / 256 * 256;
+  GS_TRY(ensure(c, c->l1_partial, part_bytes + l1_finish_scratch_bytes()));
+  const int64_t count = 3 * c->pixels;
+  RasterArgs r = raster_args(c);
+  r.image = images;
+  r.target = targets;
+  // inside a captured step the targets are read through the device slot
+  r.target_slot = c->capturing ? reinterpret_cast<const float* const*>(c->target_slot.p) : nullptr;
+  r.l1_grad = dL_dimages;
+  r.l1_partial = P<float>(c->l1_partial);
+  r.inv_count = (float)(1.0 / (double)count);
+  {
+    LaunchScope ls(c, "raster_fwd");
+    launch_raster_fwd(r, c->bins, c->raster_fwd, c->stream);
+  }
+  {
+    LaunchScope ls(c, "l1_loss", 2);
+    launch_l1_finish(P<float>(c->l1_partial), nparts,
+                     reinterpret_cast<double*>(P<unsigned char>(c->l1_partial) + part_bytes), 1.0 / (double)count,
+                     loss, c->stream);
   }
   GS_CHECK_LAUNCH(c);
   c->rastered = true;
@@ -672,7 +726,7 @@ gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
     case GS_BUF_G2D: if (!c->g2d.p) return GS_ESTATE; *ptr = c->g2d.p; *count = 9 * bn; break;
     case GS_BUF_SORT_CTRL:
       if (!c->sorted) return GS_ESTATE;
-      *ptr = P<uint32_t>(c->hist_scan) + 8 * 256;
+      *ptr = reinterpret_cast<uint32_t*>(P<uint64_t>(c->total) + 1 + kMaxViews) + 2 * (kMaxViews + 1);
       *count = c->sort_passes + 1;
       break;
     default: return fail(c, GS_EINVAL, "unknown buffer %d", which);
@@ -740,12 +794,10 @@ gs_status gs_train_graph_capture(gs_ctx* c, gs_params* p, gs_params* g, gs_param
   // 1. one uncaptured pass (no parameter update) sizes every workspace
   GS_TRY(gs_project(c, p, cams, B));
   GS_TRY(gs_bin_sort(c));
-  GS_TRY(gs_raster_fwd(c, images));
-  const int64_t count = 3 * c->pixels;
-  GS_TRY(gs_l1_loss(c, images, targets, count, loss, dL_dimages));
+  GS_TRY(ensure(c, c->target_slot, sizeof(void*)));
+  GS_TRY(gs_raster_fwd_l1(c, images, targets, loss, dL_dimages));
   GS_TRY(gs_raster_bwd(c, p, dL_dimages, g));
   GS_TRY(ensure(c, c->adam_consts, 65 * sizeof(float)));
-  GS_TRY(ensure(c, c->target_slot, sizeof(void*)));
   GS_TRY(gs_sync(c));
   // 2. capture on a private stream
   if (!c->graph_stream) GS_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
@@ -774,8 +826,7 @@ gs_status gs_train_graph_capture(gs_ctx* c, gs_params* p, gs_params* g, gs_param
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->staged_ev, c->stream, cudaEventRecordExternal);
     if (e == cudaSuccess) st = gs_project(c, p, cams, B);
     if (e == cudaSuccess && st == GS_OK) st = gs_bin_sort(c);
-    if (e == cudaSuccess && st == GS_OK) st = gs_raster_fwd(c, images);
-    if (e == cudaSuccess && st == GS_OK) st = gs_l1_loss(c, images, targets, count, loss, dL_dimages);
+    if (e == cudaSuccess && st == GS_OK) st = gs_raster_fwd_l1(c, images, targets, loss, dL_dimages);
     if (e == cudaSuccess && st == GS_OK) st = gs_raster_bwd(c, p, dL_dimages, g);
     if (e == cudaSuccess && st == GS_OK) st = gs_adam(c, p, g, m, v, hp, 1);
     const cudaError_t e2 = cudaStreamEndCapture(c->graph_stream, &graph);
@@ -800,7 +851,7 @@ gs_status gs_train_graph_capture(gs_ctx* c, gs_params* p, gs_params* g, gs_param
   c->graph_hp = *hp;
   c->graph_planes = n_planes(p->sh_degree);
   c->graph_loss = loss;
-  c->graph_count = count;
+  c->graph_count = 3 * c->pixels;
   return GS_OK;
 }
 

@@ -16,9 +16,9 @@ struct ProjectArgs {
   float4* rec0;  // records 0, 1, 2 of entry o at rec0[3 o], rec1[3 o], rec2[3 o]
   float4* rec1;  // (one interleaved array: rec1 = rec0 + 1, rec2 = rec0 + 2)
   float4* rec2;
-  int2* rec3;
+  int4* rec3;            // (radius, tiles, x0 | x1 << 16, y0 | y1 << 16) per (view, Gaussian)
   uint32_t* tiles;       // [B][stride]
-  uint32_t* block_sums;  // [ceil(n / block)]
+  uint32_t* block_sums;  // [B][ceil(n / block)] instance counts per view and block
 };
 
 struct ProjectBwdArgs {
@@ -36,9 +36,10 @@ struct DuplicateArgs {
   int B;
   const float4* rec0;
   const float4* rec2;
-  const int2* rec3;
+  const int4* rec3;
   const uint32_t* tiles;
-  const uint32_t* block_offsets;  // exclusive scan of the projection block sums
+  const uint32_t* block_offsets;  // [B][blocks] exclusive scan of each view's block counts
+  const uint32_t* seg;            // [B + 1] first instance of each view's segment
   uint64_t* keys;
   uint32_t* vals;
   int64_t capacity;
@@ -55,20 +56,28 @@ struct RasterArgs {
   const float4* rec0;
   const float4* rec1;
   const float4* rec2;
-  float* image;         // [B][3][H][W] concatenated
+  float* image;         // [B][3][H][W] concatenated (forward: may be NULL when fused with the L1 loss)
   float* tfinal;        // [pixels]
   uint32_t* nlast;      // [pixels]
   const float* dimage;  // backward only
   float* g2d;           // backward only: 9 planes of [B][stride]
   int direct_max;       // backward only: at most this many contributing lanes -> per-lane atomics
+  // forward fused with the L1 loss (target non-NULL or read from target_slot):
+  // writes dL/dimage = sign(image - target) * inv_count and one partial sum
+  // of |image - target| per block
+  const float* target;
+  const float* const* target_slot;
+  float* l1_grad;
+  float* l1_partial;
+  float inv_count;
 };
 
 int project_fwd_block();
 void launch_project_fwd(const ProjectArgs& a, int deg, cudaStream_t s);
 void launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t s);
 
-void launch_scan_block_sums(const uint32_t* sums, int64_t nb, uint32_t* offsets, uint64_t* total,
-                            cudaStream_t s);
+void launch_scan_block_sums(const uint32_t* sums, int64_t nb, int B, uint32_t* offsets, uint64_t* view_total,
+                            uint32_t* seg, uint64_t* total, cudaStream_t s);
 void launch_duplicate(const DuplicateArgs& a, cudaStream_t s);
 
 // LSD radix sort of (key, value) pairs on key bits [0, 8 npass), ping-pong
@@ -82,8 +91,13 @@ struct SortArgs {
   const uint64_t* count;     // device: number of pairs (clamped to capacity)
   int64_t capacity;          // pairs the buffers hold
   int64_t bins;              // valid bin ids are [0, bins)
-  uint32_t* hist;            // [8][256] digit counts
-  uint32_t* hist_scan;       // [8][256] exclusive digit offsets
+  int B;                     // views: one segment each
+  const ViewRec* views;      // a view's first bin is subtracted before the digits are taken
+  const uint32_t* seg;       // [B + 1] segment offsets
+  uint32_t* part_off;        // [B + 1] first partition of each segment
+  uint32_t* single;          // [B][8] 1 if the view's keys share one digit in the pass
+  uint32_t* hist;            // [B][npass][256] digit counts
+  uint32_t* hist_scan;       // [B][npass][256] exclusive digit offsets within the segment
   uint32_t* ctrl;            // [npass + 1] pass control: source buffer, skipped
   uint32_t* lookback;        // [npass][lookback_stride]
   size_t lookback_stride;    // uint32 per pass (sort_lookback_bytes / 4)
@@ -94,14 +108,19 @@ struct SortArgs {
   const uint32_t** sorted_vals;
 };
 
-size_t sort_lookback_bytes(int64_t count, int items);
-int64_t sort_partitions(int64_t count, int items);
-void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, cudaStream_t s);
+size_t sort_lookback_bytes(int64_t count, int items, int segments);
+int64_t sort_partitions(int64_t count, int items, int segments);
+void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, int items, cudaStream_t s);
 // items: keys per thread (12, 16, 20 or 24); the grid covers a.capacity
 void launch_onesweep_pass(const SortArgs& a, int pass, int items, cudaStream_t s);
 void launch_tile_ranges(const SortArgs& a, int64_t grid_hint, uint2* ranges, cudaStream_t s);
 
 void launch_raster_fwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s);
+// warps of a forward launch (one L1 partial sum each when fused)
+int64_t raster_fwd_warps(int64_t bins, int ppt);
+int64_t l1_finish_scratch_bytes();
+void launch_l1_finish(const float* partial, int64_t nparts, double* scratch, double inv_count, float* loss,
+                      cudaStream_t s);
 void launch_raster_bwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s);
 
 void launch_l1(const float* x, const float* y, const float* const* y_slot, int64_t count, float* partial,

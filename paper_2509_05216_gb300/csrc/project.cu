@@ -169,12 +169,15 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
   GaussCov gc;
   gauss_cov(lsc, quat, gc);  // view-independent: once per Gaussian
   __shared__ float4 s_rec[8][32 * kRecStride];  // 256 threads: 8 warps x 32 records
-  uint32_t total = 0;
+  __shared__ uint32_t s_bsum[kMaxViews];          // the block's instance count per view
+  for (int i = threadIdx.x; i < a.B; i += blockDim.x) s_bsum[i] = 0;
+  __syncthreads();
   for (int v = 0; v < a.B; v++) {
     const ViewRec& V = a.views[v];
     const int64_t o = (int64_t)v * a.stride + g;
     uint32_t tiles = 0;
     int radius = 0;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;  // tile rect (half-open)
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
     float depth = 0.f, blue = 0.f;
     float2 ex = make_float2(-3.0e38f, -3.0e38f);
@@ -194,7 +197,6 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
           radius = (int)ceilf(3.f * sqrtf(lam));
           const float mx = fmaf(V.fx, st.tx / st.tz, V.cx);
           const float my = fmaf(V.fy, st.ty / st.tz, V.cy);
-          int x0, x1, y0, y1;
           if (radius > 0 && tile_rect(V, mx, my, radius, x0, x1, y0, y1)) {
             tiles = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
             // colour
@@ -230,10 +232,11 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
             ex = make_float2(hx, hy);
           } else {
             radius = 0;
+            x0 = x1 = y0 = y1 = 0;
           }
         }
       }
-      a.rec3[o] = make_int2(tiles ? radius : 0, (int)tiles);
+      a.rec3[o] = make_int4(tiles ? radius : 0, (int)tiles, x0 | (x1 << 16), y0 | (y1 << 16));
       a.tiles[o] = tiles;
     }
     // the warp's 32 records (48 bytes each) go out through shared memory as
@@ -252,21 +255,13 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
       const int f = lane + 32 * m;
       if (g0 + f / kRecStride < a.n) dst[f] = stage[f];
     }
-    total += tiles;
+    const uint32_t wt = __reduce_add_sync(0xffffffffu, tiles);
+    if (lane == 0 && wt) atomicAdd(&s_bsum[v], wt);
   }
-  // block total of the instance counts (for the scan)
-  __shared__ uint32_t red[32];
-  uint32_t s = total;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  // the block's instance count per view (for the per-view scans)
   __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0u;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (threadIdx.x == 0) a.block_sums[blockIdx.x] = s;
-  }
+  for (int i = threadIdx.x; i < a.B; i += blockDim.x)
+    a.block_sums[(int64_t)i * gridDim.x + blockIdx.x] = s_bsum[i];
 }
 
 // Backward, colour part: dL/drgb per (view, Gaussian) -> dL/dSH and the

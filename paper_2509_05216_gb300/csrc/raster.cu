@@ -350,7 +350,11 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   G geo;
-  if (!geo.init(a, bins, w, lane)) return;
+  if (!geo.init(a, bins, w, lane)) {
+    // a warp past the last tile (one-warp-per-tile shape): no pixels, a zero L1 partial
+    if (lane == 0 && (a.target || a.target_slot)) a.l1_partial[(int64_t)blockIdx.x * NWB + w] = 0.f;
+    return;
+  }
   const int v = geo.v, px = geo.px, py0 = geo.py0;
   const ViewRec& V = a.views[v];
   const uint2 rg = a.ranges[geo.bin];
@@ -431,17 +435,43 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     }
   }
   const int64_t plane = (int64_t)V.W * V.H;
-  float* img = a.image + 3 * V.pix_offset;
+  float* img = a.image ? a.image + 3 * V.pix_offset : nullptr;
+  const float* tgt = a.target_slot ? *a.target_slot : a.target;
+  const bool l1 = tgt != nullptr;
+  float l1sum = 0.f;
 #pragma unroll
   for (int k = 0; k < PPT; k++) {
     const int py = py0 + k;
     if (px >= V.W || py >= V.H) continue;
     const int64_t p = (int64_t)py * V.W + px;
-    img[p] = fmaf(T[k], V.bg[0], C[k][0]);
-    img[plane + p] = fmaf(T[k], V.bg[1], C[k][1]);
-    img[2 * plane + p] = fmaf(T[k], V.bg[2], C[k][2]);
+    const float c0 = fmaf(T[k], V.bg[0], C[k][0]);
+    const float c1 = fmaf(T[k], V.bg[1], C[k][1]);
+    const float c2 = fmaf(T[k], V.bg[2], C[k][2]);
+    if (img) {
+      img[p] = c0;
+      img[plane + p] = c1;
+      img[2 * plane + p] = c2;
+    }
     a.tfinal[V.pix_offset + p] = T[k];
     a.nlast[V.pix_offset + p] = last[k];
+    if (l1) {
+      // L1 loss mean |C - target| and its gradient sign(C - target) / count
+      const float* t = tgt + 3 * V.pix_offset;
+      float* gd = a.l1_grad + 3 * V.pix_offset;
+      const float cc[3] = {c0, c1, c2};
+#pragma unroll
+      for (int ch = 0; ch < 3; ch++) {
+        const float d = cc[ch] - t[ch * plane + p];
+        l1sum += fabsf(d);
+        gd[ch * plane + p] = d > 0.f ? a.inv_count : (d < 0.f ? -a.inv_count : 0.f);
+      }
+    }
+  }
+  if (l1) {
+    // one partial sum per warp (fixed order: deterministic)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l1sum += __shfl_down_sync(0xffffffffu, l1sum, off);
+    if (lane == 0) a.l1_partial[(int64_t)blockIdx.x * NWB + w] = l1sum;
   }
 }
 
@@ -592,6 +622,61 @@ void launch_shape(bool fwd, const RasterArgs& a, int64_t bins, cudaStream_t s) {
   const unsigned blocks = (unsigned)((bins + G::TPB - 1) / G::TPB);
   if (fwd) raster_fwd_kernel<PPT><<<blocks, G::THREADS, 0, s>>>(a, bins);
   else raster_bwd_kernel<PPT><<<blocks, G::THREADS, 0, s>>>(a, bins);
+}
+
+int64_t raster_fwd_warps(int64_t bins, int ppt) {
+  // L1 partial sums of a fused forward: one per warp of the launch
+  switch (ppt) {
+    case 1: return bins * Geo<1>::NW * Geo<1>::TPB;
+    case 4: return bins * Geo<4>::NW * Geo<4>::TPB;
+    case 8: return (bins + Geo<8>::TPB - 1) / Geo<8>::TPB * Geo<8>::NW * Geo<8>::TPB;
+    default: return bins * Geo<2>::NW * Geo<2>::TPB;
+  }
+}
+
+// Sum of the partials in a fixed order: 256 blocks each add a strided
+// subset (FP64, a handful of terms per thread) and a tree inside the block;
+// one block adds the 256 block sums.  The loss is deterministic.
+constexpr int kL1FinishBlocks = 256;
+
+__global__ void __launch_bounds__(256) l1_partials_kernel(const float* __restrict__ partial, int64_t nparts,
+                                                          double* __restrict__ block_sums) {
+  __shared__ double red[8];
+  double t = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nparts; i += (int64_t)gridDim.x * blockDim.x)
+    t += partial[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < 8; w++) u += red[w];
+    block_sums[blockIdx.x] = u;
+  }
+}
+
+__global__ void __launch_bounds__(256) l1_finish_tree_kernel(const double* __restrict__ block_sums, double inv_count,
+                                                             float* loss) {
+  __shared__ double red[8];
+  double t = threadIdx.x < kL1FinishBlocks ? block_sums[threadIdx.x] : 0.0;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < 8; w++) u += red[w];
+    *loss = (float)(u * inv_count);
+  }
+}
+
+int64_t l1_finish_scratch_bytes() { return kL1FinishBlocks * sizeof(double); }
+
+void launch_l1_finish(const float* partial, int64_t nparts, double* scratch, double inv_count, float* loss,
+                      cudaStream_t s) {
+  l1_partials_kernel<<<kL1FinishBlocks, 256, 0, s>>>(partial, nparts, scratch);
+  l1_finish_tree_kernel<<<1, 256, 0, s>>>(scratch, inv_count, loss);
 }
 
 void launch_raster_fwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s) {

@@ -79,7 +79,7 @@ class gs_serve_cfg(ctypes.Structure):
                 ("output_pool_bytes", ctypes.c_int64)]
 
 
-EXPORTS = ["gs_train_graph_capture", "gs_train_graph_launch", "gs_train_graph_launch_host", "gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
+EXPORTS = ["gs_raster_fwd_l1", "gs_train_graph_capture", "gs_train_graph_launch", "gs_train_graph_launch_host", "gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
            "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
            "gs_get_counts"]
@@ -111,6 +111,7 @@ def load(path: str | None = None):
     L.gs_get_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
     L.gs_train_graph_capture.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), P(gs_params), P(gs_adam_hp),
                                          P(gs_camera), i32, vp, vp, vp, vp]
+    L.gs_raster_fwd_l1.argtypes = [vp, vp, vp, vp, vp]
     L.gs_train_graph_launch.argtypes = [vp, P(gs_camera), i32, vp, i64]
     L.gs_train_graph_launch_host.argtypes = [vp, P(gs_camera), i32, vp, i64, vp]
     L.gs_serve_create.argtypes = [P(vp), ctypes.c_int, P(gs_params), P(gs_serve_cfg)]
@@ -214,6 +215,16 @@ class Context:
         assert images.is_cuda and images.dtype == torch.float32 and images.is_contiguous()
         self._check(self.L.gs_raster_fwd(self.h, ctypes.c_void_p(images.data_ptr())), "gs_raster_fwd")
 
+    def gs_raster_fwd_l1(self, images, targets: torch.Tensor, loss: torch.Tensor, dimages: torch.Tensor):
+        """Forward compositing fused with the L1 loss (images may be None)."""
+        self._bind_stream()
+        for t in (targets, loss, dimages):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        ip = ctypes.c_void_p(images.data_ptr()) if images is not None else None
+        self._check(self.L.gs_raster_fwd_l1(self.h, ip, ctypes.c_void_p(targets.data_ptr()),
+                                            ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(dimages.data_ptr())),
+                    "gs_raster_fwd_l1")
+
     def gs_raster_bwd(self, params: torch.Tensor, n: int, deg: int, dL_dimages: torch.Tensor,
                       grads: torch.Tensor):
         self._bind_stream()
@@ -311,7 +322,7 @@ class Context:
         n = cnt.value
         spec = {GS_BUF_REC0: ((n, 4), "<f4"), GS_BUF_REC1: ((n, 4), "<f4"), GS_BUF_REC2: ((n, 4), "<f4"),
                 GS_BUF_KEYS: ((n,), "<i8"), GS_BUF_VALS: ((n,), "<i4"), GS_BUF_RANGES: ((n, 2), "<i4"),
-                GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((9, n // 9), "<f4"), GS_BUF_REC3: ((n, 2), "<i4"),
+                GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((9, n // 9), "<f4"), GS_BUF_REC3: ((n, 4), "<i4"),
                 GS_BUF_SORT_CTRL: ((n,), "<i4")}[which]
         if n == 0:
             return torch.empty(spec[0], device="cuda:%d" % self.device,

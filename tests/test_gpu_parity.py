@@ -11,7 +11,7 @@ import pytest
 import torch
 
 from paper_2509_05216_gb300 import gs, inputs
-from tests.gpu_helpers import expected_binning, rel_l2, run_forward, to_dev_images
+from tests.gpu_helpers import cpu_rect, expected_binning, rel_l2, run_forward, to_dev_images
 
 pytestmark = pytest.mark.gpu
 
@@ -113,13 +113,26 @@ def test_binning_is_bit_exact(ctx, name):
     assert np.array_equal(gk, keys)
     assert np.array_equal(gv, vals)
     assert np.array_equal(gr, ranges)
-    # the sort ran only the passes whose digit varies (the depth exponent byte
-    # is one digit for these scenes and is skipped)
+    # the packed tile rect of every touching (view, Gaussian) pair
+    for v, c in enumerate(cams):
+        sl = slice(v * stride, v * stride + n)
+        x0, x1, y0, y1 = cpu_rect(r0[sl, 0], r0[sl, 1], r3[sl, 0].astype(np.int64), c["width"], c["height"])
+        on = r3[sl, 1] > 0
+        px, py = r3[sl, 2].astype(np.int64), r3[sl, 3].astype(np.int64)
+        assert np.array_equal((px & 0xFFFF)[on], x0[on]) and np.array_equal((px >> 16)[on], x1[on])
+        assert np.array_equal((py & 0xFFFF)[on], y0[on]) and np.array_equal((py >> 16)[on], y1[on])
+    # the sort ran only the passes whose digit varies in some view (the
+    # depth exponent byte is one digit for these scenes and is skipped)
     ctrl = ctx.gs_get_buffer(gs.GS_BUF_SORT_CTRL).cpu().numpy().astype(np.int64)
     npass = ctrl.size - 1
-    digits = [(keys >> np.uint64(8 * p)) & np.uint64(255) for p in range(npass)]
+    # each view's segment is sorted on key - (view's first bin << 32)
+    offs = np.cumsum([0] + [((c["width"] + 15) // 16) * ((c["height"] + 15) // 16) for c in cams])
+    view = np.searchsorted(offs, (keys >> np.uint64(32)).astype(np.int64), side="right") - 1
+    local = keys - (offs[view].astype(np.uint64) << np.uint64(32))
     for p in range(npass):
-        assert bool(ctrl[p] & 2) == (keys.size == 0 or np.unique(digits[p]).size == 1)
+        dg = (local >> np.uint64(8 * p)) & np.uint64(255)
+        one = all(np.unique(dg[view == v]).size <= 1 for v in range(len(cams)))
+        assert bool(ctrl[p] & 2) == one
 
 
 def test_binning_with_empty_and_uneven_views(ctx):
@@ -325,6 +338,31 @@ def test_l1_loss_matches_oracle(ctx, oracle):
     ref, gref = oracle.l1(x, y)
     assert abs(loss.item() - ref) <= 1e-6 * ref
     np.testing.assert_allclose(grad.cpu().numpy(), gref, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("variant", [2, 8])
+def test_fused_forward_l1_matches_separate_calls(ctx, variant):
+    """gs_raster_fwd_l1 writes the same image and dL/dimage as gs_raster_fwd
+    followed by gs_l1_loss, and the same loss up to summation order; without
+    an image output too."""
+    scene, cams = SCENES["random_deg3_mixed"]()
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, variant)
+    p, img = run_forward(ctx, scene, cams)
+    _, total = gs.image_offsets(cams)
+    rng = np.random.default_rng(12)
+    tgt = torch.from_numpy(rng.uniform(0, 1, total).astype(np.float32)).cuda()
+    loss_a, grad_a = torch.zeros(1, device="cuda"), torch.empty(total, device="cuda")
+    ctx.gs_l1_loss(img, tgt, loss_a, grad_a)
+    img_b, loss_b, grad_b = torch.empty(total, device="cuda"), torch.zeros(1, device="cuda"), torch.empty(total, device="cuda")
+    ctx.gs_raster_fwd_l1(img_b, tgt, loss_b, grad_b)
+    loss_c, grad_c = torch.zeros(1, device="cuda"), torch.empty(total, device="cuda")
+    ctx.gs_raster_fwd_l1(None, tgt, loss_c, grad_c)
+    ctx.gs_sync()
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, 2)
+    assert torch.equal(img, img_b)
+    assert torch.equal(grad_a, grad_b) and torch.equal(grad_a, grad_c)
+    assert abs(loss_a.item() - loss_b.item()) <= 1e-6 * loss_a.item()
+    assert loss_b.item() == loss_c.item()
 
 
 def test_adam_matches_oracle(ctx, oracle):
