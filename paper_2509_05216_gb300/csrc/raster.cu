@@ -107,22 +107,6 @@ __device__ __forceinline__ float splat_alpha2(float op, float p2, float& G) {
   return fminf(kAlphaClamp, __fmul_rn(op, G));
 }
 
-// Sum 16 per-lane values over the warp, reduce-scatter style: afterwards
-// lanes 2q and 2q+1 hold the total of value q (16 shuffles instead of 80).
-__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane) {
-#pragma unroll
-  for (int off = 16, half = 8; off >= 2; off >>= 1, half >>= 1) {
-    const bool up = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < half; i++) {
-      const float send = up ? v[i] : v[i + half];
-      const float keep = up ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
 // Accumulators hold d/d(mu_x, mu_y) of p2 and raw dx^2, dx dy, dy^2 sums;
 // the scale of value q undoes those scalings.
 __device__ __forceinline__ float grad_scale(int q) {
@@ -131,8 +115,8 @@ __device__ __forceinline__ float grad_scale(int q) {
 
 // Apply a warp's gradient of one Gaussian.  `contrib`: ballot of the lanes
 // whose pixels contributed.  With few such lanes each adds its own 9 values
-// (9 atomic instructions for the warp); otherwise a reduce-scatter leaves
-// the total of value q in lanes 2q, 2q+1 and lane 2q adds it (16 shuffles).
+// (9 atomic instructions for the warp); otherwise the 9 values are summed
+// over the warp (14 shuffles) and one lane per value adds the total.
 __device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec, float (&acc)[16], int lane,
                                           uint32_t contrib, int direct_max) {
   if (__popc(contrib) <= direct_max) {
@@ -142,9 +126,26 @@ __device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec
     }
     return;
   }
-  const float tot = warp_reduce_scatter16(acc, lane);
-  const int q = lane >> 1;
-  if ((lane & 1) == 0 && q < 9) atomicAdd(g2d + q * plane + rec, tot * grad_scale(q));
+  // values 0..7: reduce-scatter over three levels, then two butterfly steps
+  // (lanes 4q hold value q); value 8: a full butterfly (14 shuffles in all)
+#pragma unroll
+  for (int off = 16, half = 4; off >= 4; off >>= 1, half >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; i++) {
+      const float send = up ? acc[i] : acc[i + half];
+      const float keep = up ? acc[i + half] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  float t8 = acc[8];
+  float t = acc[0];
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t8 += __shfl_xor_sync(0xffffffffu, t8, off);
+  if ((lane & 3) == 0) atomicAdd(g2d + (lane >> 2) * plane + rec, t * grad_scale(lane >> 2));
+  if (lane == 1) atomicAdd(g2d + 8 * plane + rec, t8 * grad_scale(8));
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
