@@ -267,9 +267,11 @@ constexpr uint32_t kCtrlParity = 1u, kCtrlTrivial = 2u;
 // one segment; rank its keys by digit of key - (view's first bin << 32)
 // (stable), find its offset for each digit by decoupled look-back over the
 // earlier partitions of its segment (bounded waits), then scatter through
-// shared memory so that the global writes are coalesced.  Keys are loaded up
-// front (all loads in flight before ranking); keys and then values go
-// through one shared buffer (46 KB for 16 keys per thread).
+// shared memory so that the global writes are coalesced.  The 32-bit halves
+// of the keys that hold the pass's digit are loaded up front (all loads in
+// flight before ranking; half the registers of whole keys, which spilled);
+// keys and then values go through one shared buffer (42 KB for 16 keys per
+// thread), and the scatter takes each staged key's digit from the key.
 template <int ITEMS>
 struct SortSmem {
   static constexpr int kTile = kSortThreads * ITEMS;
@@ -281,7 +283,6 @@ struct SortSmem {
   uint64_t key_base;
   int timed_out;
   uint64_t buf[kTile];                     // keys, then values, in tile-sorted order
-  uint8_t dig[kTile];                      // digit of each tile-sorted position
 };
 
 template <int ITEMS, int MIN_BLOCKS>
@@ -329,11 +330,18 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   uint32_t* lookback = a.lookback + (size_t)pass * a.lookback_stride;
   const int wl = wid * kSortItems * 32 + lane;  // item i at base + wl + 32 i
 
-  uint64_t key[kSortItems];
+  // the pass's digit lies in one 32-bit half of the key (8-bit digits):
+  // only that half is held in registers for the ranking; the whole key is
+  // read again (from L2) when it is staged in sorted order
+  const int hw = shift >= 32 ? 1 : 0;
+  const int wsh = shift & 31;
+  const uint32_t wsub = hw ? (uint32_t)(kb >> 32) : 0u;
+  const uint32_t* __restrict__ kin32 = reinterpret_cast<const uint32_t*>(kin) + hw;
+  uint32_t word[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
     const int p = wl + 32 * i;
-    key[i] = p < n_here ? kin[base + p] - kb : ~0ull;
+    word[i] = p < n_here ? kin32[2 * (base + p)] - wsub : 0u;
   }
   // stable rank inside the warp (warp-striped order), 16-bit per item
   uint32_t rk[kSortItems / 2];
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
     const bool ok = wl + 32 * i < n_here;
-    const uint32_t d = ok ? (uint32_t)(key[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
+    const uint32_t d = ok ? (word[i] >> wsh) & (kRadix - 1) : (uint32_t)kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     uint32_t r = 0, before = 0;
     if (ok) {
@@ -381,18 +389,17 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     sm.digit_start[d] = wpre + inc - tile_count;
   }
   __syncthreads();
-  // keys -> partition-sorted positions in shared memory (frees the key
-  // registers before the look-back); remember the positions for the values
+  // keys -> partition-sorted positions in shared memory (before the
+  // look-back); remember the positions for the values
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
     const bool ok = wl + 32 * i < n_here;
     const uint32_t r = (rk[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
     uint32_t lpos = 0xffffu;
     if (ok) {
-      const uint32_t dd = (uint32_t)(key[i] >> shift) & (kRadix - 1);
+      const uint32_t dd = (word[i] >> wsh) & (kRadix - 1);
       lpos = sm.digit_start[dd] + sm.warp_hist[wid][dd] + r;
-      sm.buf[lpos] = key[i] + kb;
-      sm.dig[lpos] = (uint8_t)dd;
+      sm.buf[lpos] = kin[base + wl + 32 * i];
     }
     if (i & 1) rk[i >> 1] = (rk[i >> 1] & 0xffffu) | (lpos << 16); else rk[i >> 1] = (rk[i >> 1] & 0xffff0000u) | lpos;
   }
@@ -438,11 +445,20 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
     return;
   }
+  // sorted keys out, coalesced; the digit of a staged key is taken from the
+  // key itself, and each thread keeps its destinations for the values
   const uint32_t hi = sm.seg_hi;
-  for (int q = tid; q < n_here; q += kSortThreads) {
-    const uint32_t dd = sm.dig[q];
-    const uint32_t dst = sm.global_base[dd] + ((uint32_t)q - sm.digit_start[dd]);
-    if (dst < hi) kout[dst] = sm.buf[q];
+  uint32_t dst[kSortItems];
+#pragma unroll
+  for (int t = 0; t < kSortItems; t++) {
+    const int q = tid + t * kSortThreads;
+    dst[t] = 0xffffffffu;
+    if (q < n_here) {
+      const uint64_t k = sm.buf[q];
+      const uint32_t dd = (uint32_t)((k - kb) >> shift) & (kRadix - 1);
+      dst[t] = sm.global_base[dd] + ((uint32_t)q - sm.digit_start[dd]);
+      if (dst[t] < hi) kout[dst[t]] = k;
+    }
   }
   __syncthreads();
   // values through the same buffer
@@ -454,10 +470,10 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     if (p < n_here) vb[lpos] = vin[base + p];
   }
   __syncthreads();
-  for (int q = tid; q < n_here; q += kSortThreads) {
-    const uint32_t dd = sm.dig[q];
-    const uint32_t dst = sm.global_base[dd] + ((uint32_t)q - sm.digit_start[dd]);
-    if (dst < hi) vout[dst] = vb[q];
+#pragma unroll
+  for (int t = 0; t < kSortItems; t++) {
+    const int q = tid + t * kSortThreads;
+    if (q < n_here && dst[t] < hi) vout[dst[t]] = vb[q];
   }
 }
 
