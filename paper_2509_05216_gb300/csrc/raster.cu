@@ -109,17 +109,19 @@ __device__ __forceinline__ bool ellipse_hits(const float4& r0, const float4& r1,
 
 // The same test against the NG lane-group rectangles of a warp (bit g of
 // the result: group g), sharing the per-record terms.
+// Lane-group survivors: the exact test against the warp's rectangle, then
+// the alpha >= 1/255 box against each group's rectangle (bit g: group g).
+// The box is looser than the ellipse but costs four compares per group.
 template <class Geom>
-__device__ __forceinline__ uint32_t ellipse_group_bits(const float4& r0, const float4& r1, const float4& r2,
-                                                       const Geom& geo) {
-  if (!box_hits(r0, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1)) return 0u;
-  const EllipseTerms t = ellipse_terms(r0, r1);
+__device__ __forceinline__ uint32_t box_group_bits(const float4& r0, const float4& r1, const float4& r2,
+                                                   const Geom& geo) {
+  if (!ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1)) return 0u;
   uint32_t bits = 0;
 #pragma unroll
   for (int g = 0; g < Geom::NG; g++) {
     float x0, x1, y0, y1;
     geo.group_rect(g, x0, x1, y0, y1);
-    bits |= ellipse_rect(t, r0, r2, x0, x1, y0, y1) ? 1u << g : 0u;
+    bits |= box_hits(r0, r2, x0, x1, y0, y1) ? 1u << g : 0u;
   }
   return bits;
 }
@@ -391,14 +393,13 @@ struct Shape<8> {  // 1 warp per tile, 4 tiles per block
   static constexpr int NW = 1, TPB = 4, CW = 16;
 };
 
-// Lane groups (backward only): the warp's lanes form NG = 32 / GW groups,
-// each owning a GCW x GRH sub-rectangle of the warp's pixels and walking
-// only the Gaussians that reach it.  With 2 pixels per thread the backward
-// uses 4 groups of 4 x 4 pixels: they walk 66 % as many survivors as the
-// whole 8 x 8 warp rectangle on the benchmark scene (5 % faster backward in
-// A/B runs; the forward measured slower with groups and walks per warp).
+// Lane groups: the warp's lanes form NG = 32 / GW groups, each owning a
+// GCW x GRH sub-rectangle of the warp's pixels and walking only the
+// Gaussians whose box reaches it (the warp iterates max over groups; a lane
+// whose group has run out takes no-op steps).  With 2 pixels per thread both
+// compositing kernels use 4 groups of 4 x 4 pixels.
 template <int PPT>
-struct BwdGroup {
+struct LaneGroups {
   static constexpr int GW = PPT == 2 ? 8 : 32;
 };
 
@@ -443,7 +444,7 @@ struct Geo {
 
 template <int PPT>
 __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArgs a, int64_t bins) {
-  using G = Geo<PPT>;
+  using G = Geo<PPT, LaneGroups<PPT>::GW>;
   constexpr int NWB = G::NW * G::TPB;  // warps per block
   constexpr int NP = PPT / 2;          // pixel pairs per thread
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
@@ -486,19 +487,33 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     const int i = b0 + lane;
     bool hit = false;
     __syncwarp();
+    uint32_t gbits = 0;
     if (i < n) {
       float4 r0, r1, r2;
       stage_one(a, v, vals[rg.x + i], r0, r1, r2);
       s0[w][lane] = r0;
       s1[w][lane] = r1;
       s2[w][lane] = r2;
-      hit = ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
+      if constexpr (G::NG > 1) gbits = box_group_bits(r0, r1, r2, geo);
+      else hit = ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
     }
     // each lane culls its own record; the warp walks the survivors in order
     uint32_t mask = __ballot_sync(0xffffffffu, hit);
+    int iters = 32;
+    if constexpr (G::NG > 1) {
+      int most = 0;
+#pragma unroll
+      for (int g = 0; g < G::NG; g++) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (gbits >> g) & 1u);
+        mask = g == geo.grp ? m : mask;
+        most = max(most, __popc(m));
+      }
+      iters = most;
+    }
     __syncwarp();
-    while (mask) {
-      const int j = __ffs(mask) - 1;
+    for (int it = 0; G::NG > 1 ? it < iters : mask != 0u; it++) {
+      const bool act = mask != 0u;
+      const int j = act ? __ffs(mask) - 1 : 0;
       mask &= mask - 1u;
       const float4 q0 = s0[w][j];
       const float4 q2 = s2[w][j];
@@ -514,10 +529,13 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
       } else {
         const float2 cC = bc2(q1.x), A1 = bc2(a1), A0 = bc2(a0), op = bc2(q1.y);
         const float2 r = bc2(q1.z), g = bc2(q1.w), b = bc2(q2.x), qy = bc2(q0.y);
+        // a lane whose group has no survivor left changes nothing
+        uint32_t dn = act ? done : all_done;
 #pragma unroll
         for (int jp = 0; jp < NP; jp++)
-          fwd_pair2(cC, A1, A0, op, r, g, b, __fadd2_rn(qy, nfy[jp]), 1u << (2 * jp), idx, done, T2[jp], C2[jp],
+          fwd_pair2(cC, A1, A0, op, r, g, b, __fadd2_rn(qy, nfy[jp]), 1u << (2 * jp), idx, dn, T2[jp], C2[jp],
                     last[2 * jp], last[2 * jp + 1]);
+        done = act ? dn : done;
       }
     }
   }
@@ -576,7 +594,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
 
 template <int PPT>
 __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArgs a, int64_t bins) {
-  using G = Geo<PPT, BwdGroup<PPT>::GW>;
+  using G = Geo<PPT, LaneGroups<PPT>::GW>;
   constexpr int NWB = G::NW * G::TPB;
   constexpr int NP = PPT / 2;  // pixel pairs per thread (0: the scalar one-pixel path)
   constexpr int NS = NP > 0 ? NP : 1;
@@ -654,7 +672,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
       s1[w][lane] = n1;
       s2[w][lane] = n2;
       sg[w][lane] = ng;
-      if constexpr (G::NG > 1) gbits = ellipse_group_bits(n0, n1, n2, geo);
+      if constexpr (G::NG > 1) gbits = box_group_bits(n0, n1, n2, geo);
       else hit = ellipse_hits(n0, n1, n2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
     }
     uint32_t mask = __ballot_sync(0xffffffffu, hit);
