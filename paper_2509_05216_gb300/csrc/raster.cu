@@ -193,7 +193,7 @@ __device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec
 template <int GW>
 __device__ __forceinline__ void push_grad_group(float* g2d, int64_t plane, int64_t rec, float (&acc)[16], int lane,
                                                 uint32_t contrib, int direct_max) {
-  static_assert(GW == 8 || GW == 16 || GW == 32, "lane groups of 8, 16 or 32");
+  static_assert(GW == 4 || GW == 8 || GW == 16 || GW == 32, "lane groups of 4, 8, 16 or 32");
   const int gl = lane % GW;
   const uint32_t gbits = GW == 32 ? contrib : (contrib >> (lane - gl)) & ((1u << (GW % 32)) - 1u);
   if (__all_sync(0xffffffffu, __popc(gbits) <= direct_max)) {
@@ -203,25 +203,49 @@ __device__ __forceinline__ void push_grad_group(float* g2d, int64_t plane, int64
     }
     return;
   }
+  if constexpr (GW == 4) {
+    // two reduce-scatter levels: lane (b1, b0) of the group holds values
+    // 4 b1 + 2 b0 and 4 b1 + 2 b0 + 1
 #pragma unroll
-  for (int off = GW / 2, half = 4; half >= 1; off >>= 1, half >>= 1) {
-    const bool up = (lane & off) != 0;
+    for (int off = 2, half = 4; off >= 1; off >>= 1, half >>= 1) {
+      const bool up = (lane & off) != 0;
 #pragma unroll
-    for (int i = 0; i < half; i++) {
-      const float send = up ? acc[i] : acc[i + half];
-      const float keep = up ? acc[i + half] : acc[i];
-      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      for (int i = 0; i < half; i++) {
+        const float send = up ? acc[i] : acc[i + half];
+        const float keep = up ? acc[i + half] : acc[i];
+        acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
     }
-  }
-  constexpr int S = GW / 8;  // lanes holding each of values 0..7
-  float t = acc[0], t8 = acc[8];
+    float t8 = acc[8];
+    t8 += __shfl_xor_sync(0xffffffffu, t8, 2);
+    t8 += __shfl_xor_sync(0xffffffffu, t8, 1);
+    if (gbits) {
+      const int q = 4 * ((gl >> 1) & 1) + 2 * (gl & 1);
+      atomicAdd(g2d + q * plane + rec, acc[0] * grad_scale(q));
+      atomicAdd(g2d + (q + 1) * plane + rec, acc[1] * grad_scale(q + 1));
+      if (gl == 0) atomicAdd(g2d + 8 * plane + rec, t8 * grad_scale(8));
+    }
+  } else {
 #pragma unroll
-  for (int off = S / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    for (int off = GW / 2, half = 4; half >= 1; off >>= 1, half >>= 1) {
+      const bool up = (lane & off) != 0;
 #pragma unroll
-  for (int off = GW / 2; off >= 1; off >>= 1) t8 += __shfl_xor_sync(0xffffffffu, t8, off);
-  if (gbits) {
-    if (gl % S == 0) atomicAdd(g2d + (gl / S) * plane + rec, t * grad_scale(gl / S));
-    if (gl == 1) atomicAdd(g2d + 8 * plane + rec, t8 * grad_scale(8));
+      for (int i = 0; i < half; i++) {
+        const float send = up ? acc[i] : acc[i + half];
+        const float keep = up ? acc[i + half] : acc[i];
+        acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+    constexpr int S = GW / 8;  // lanes holding each of values 0..7
+    float t = acc[0], t8 = acc[8];
+#pragma unroll
+    for (int off = S / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+#pragma unroll
+    for (int off = GW / 2; off >= 1; off >>= 1) t8 += __shfl_xor_sync(0xffffffffu, t8, off);
+    if (gbits) {
+      if (gl % S == 0) atomicAdd(g2d + (gl / S) * plane + rec, t * grad_scale(gl / S));
+      if (gl == 1) atomicAdd(g2d + 8 * plane + rec, t8 * grad_scale(8));
+    }
   }
 }
 
@@ -396,11 +420,13 @@ struct Shape<8> {  // 1 warp per tile, 4 tiles per block
 // Lane groups: the warp's lanes form NG = 32 / GW groups, each owning a
 // GCW x GRH sub-rectangle of the warp's pixels and walking only the
 // Gaussians whose box reaches it (the warp iterates max over groups; a lane
-// whose group has run out takes no-op steps).  With 2 pixels per thread both
-// compositing kernels use 4 groups of 4 x 4 pixels.
+// whose group has run out takes no-op steps).  With 2 pixels per thread the
+// forward uses 4 groups of 4 x 4 pixels and the backward, whose work per
+// survivor is larger, 8 groups of 2 x 4.
 template <int PPT>
 struct LaneGroups {
-  static constexpr int GW = PPT == 2 ? 8 : 32;
+  static constexpr int FWD = PPT == 2 ? 8 : 32;
+  static constexpr int BWD = PPT == 2 ? 4 : 32;
 };
 
 template <int PPT, int GWv = 32>
@@ -444,7 +470,7 @@ struct Geo {
 
 template <int PPT>
 __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArgs a, int64_t bins) {
-  using G = Geo<PPT, LaneGroups<PPT>::GW>;
+  using G = Geo<PPT, LaneGroups<PPT>::FWD>;
   constexpr int NWB = G::NW * G::TPB;  // warps per block
   constexpr int NP = PPT / 2;          // pixel pairs per thread
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
@@ -594,7 +620,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
 
 template <int PPT>
 __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArgs a, int64_t bins) {
-  using G = Geo<PPT, LaneGroups<PPT>::GW>;
+  using G = Geo<PPT, LaneGroups<PPT>::BWD>;
   constexpr int NWB = G::NW * G::TPB;
   constexpr int NP = PPT / 2;  // pixel pairs per thread (0: the scalar one-pixel path)
   constexpr int NS = NP > 0 ? NP : 1;
