@@ -527,14 +527,16 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     uint32_t mask = __ballot_sync(0xffffffffu, hit);
     int iters = 32;
     if constexpr (G::NG > 1) {
-      int most = 0;
 #pragma unroll
       for (int g = 0; g < G::NG; g++) {
         const uint32_t m = __ballot_sync(0xffffffffu, (gbits >> g) & 1u);
         mask = g == geo.grp ? m : mask;
-        most = max(most, __popc(m));
       }
-      iters = most;
+      // a group whose pixels have all stopped walks nothing more
+      const uint32_t fin = __ballot_sync(0xffffffffu, done == all_done);
+      const uint32_t gm = G::GW == 32 ? 0xffffffffu : ((1u << (G::GW % 32)) - 1u) << (geo.grp * G::GW);
+      if ((fin & gm) == gm) mask = 0u;
+      iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mask));
     }
     __syncwarp();
     for (int it = 0; G::NG > 1 ? it < iters : mask != 0u; it++) {
@@ -667,6 +669,10 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
   }
   // this warp only walks the entries before its pixels' last contributors
   const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
+  // the same over the lane group
+  int gmax = (int)mymax;
+#pragma unroll
+  for (int off = G::GW / 2; off >= 1 && G::GW < 32; off >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, off));
   const float fpx = (float)px, fpy = (float)py0;
   const int64_t gplane = (int64_t)a.B * a.stride;
   // with 4+ pixels per thread, lane j's record of the next batch (towards
@@ -704,14 +710,15 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
     uint32_t mask = __ballot_sync(0xffffffffu, hit);
     int iters = 32;
     if constexpr (G::NG > 1) {
-      int most = 0;
 #pragma unroll
       for (int g = 0; g < G::NG; g++) {
         const uint32_t m = __ballot_sync(0xffffffffu, (gbits >> g) & 1u);
         mask = g == geo.grp ? m : mask;
-        most = max(most, __popc(m));
       }
-      iters = most;
+      // entries at or past the group's last contributor change nothing
+      const int lim = gmax - bstart;
+      mask = lim <= 0 ? 0u : (lim >= 32 ? mask : mask & ((1u << lim) - 1u));
+      iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mask));
     }
     __syncwarp();
     if constexpr (kPrefetch) {
