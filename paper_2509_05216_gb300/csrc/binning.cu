@@ -583,17 +583,34 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __r
   }
   const int lane = threadIdx.x & 31;
   const uint32_t none = 0xffffffffu;
-  for (int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; w0 < count;
-       w0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = w0 + lane;
-    const uint32_t bin = i < count ? (uint32_t)(keys[i] >> 32) : none;
-    uint32_t prev = __shfl_up_sync(0xffffffffu, bin, 1);
-    uint32_t next = __shfl_down_sync(0xffffffffu, bin, 1);
-    if (lane == 0) prev = i > 0 && i - 1 < count ? (uint32_t)(keys[i - 1] >> 32) : none;
-    if (lane == 31) next = i + 1 < count ? (uint32_t)(keys[i + 1] >> 32) : none;
-    if (i >= count || (int64_t)bin >= a.bins) continue;  // (bins only overflow after a capacity overflow)
-    if (prev != bin) ranges[bin].x = (uint32_t)i;
-    if (next != bin) ranges[bin].y = (uint32_t)(i + 1);
+  // a warp takes 128 consecutive keys per round: four loads in flight per
+  // lane, neighbours across the four chunks by shuffles
+  constexpr int U = 4;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t* __restrict__ hi32 = reinterpret_cast<const uint32_t*>(keys) + 1;  // bin = upper half
+  for (int64_t w0 = warp * 32 * U; w0 < count; w0 += nwarps * 32 * U) {
+    uint32_t bin[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t i = w0 + 32 * u + lane;
+      bin[u] = i < count ? hi32[2 * i] : none;
+    }
+    const uint32_t before = (lane == 0 && w0 > 0) ? hi32[2 * (w0 - 1)] : none;
+    const uint32_t after = (lane == 31 && w0 + 32 * U < count) ? hi32[2 * (w0 + 32 * U)] : none;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t i = w0 + 32 * u + lane;
+      uint32_t prev = __shfl_up_sync(0xffffffffu, bin[u], 1);
+      uint32_t next = __shfl_down_sync(0xffffffffu, bin[u], 1);
+      const uint32_t prev_chunk = __shfl_sync(0xffffffffu, u > 0 ? bin[u > 0 ? u - 1 : 0] : none, 31);
+      const uint32_t next_chunk = __shfl_sync(0xffffffffu, u < U - 1 ? bin[u < U - 1 ? u + 1 : 0] : none, 0);
+      if (lane == 0) prev = u > 0 ? prev_chunk : before;
+      if (lane == 31) next = u < U - 1 ? next_chunk : after;
+      if (i >= count || (int64_t)bin[u] >= a.bins) continue;  // (bins only overflow after a capacity overflow)
+      if (prev != bin[u]) ranges[bin[u]].x = (uint32_t)i;
+      if (next != bin[u]) ranges[bin[u]].y = (uint32_t)(i + 1);
+    }
   }
 }
 

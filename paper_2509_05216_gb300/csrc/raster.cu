@@ -583,6 +583,17 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   float* img = a.image ? a.image + 3 * V.pix_offset : nullptr;
   const float* tgt = a.target_slot ? *a.target_slot : a.target;
   const bool l1 = tgt != nullptr;
+  // the targets are loaded before any store (the stores could alias them,
+  // which would serialise each load behind the stores before it)
+  float tv[PPT][3];
+#pragma unroll
+  for (int k = 0; k < PPT; k++) {
+    const int py = py0 + k;
+    const bool in = l1 && px < V.W && py < V.H;
+    const int64_t p = (int64_t)py * V.W + px;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) tv[k][ch] = in ? __ldg(tgt + 3 * V.pix_offset + ch * plane + p) : 0.f;
+  }
   float l1sum = 0.f;
 #pragma unroll
   for (int k = 0; k < PPT; k++) {
@@ -601,12 +612,11 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     a.nlast[V.pix_offset + p] = last[k];
     if (l1) {
       // L1 loss mean |C - target| and its gradient sign(C - target) / count
-      const float* t = tgt + 3 * V.pix_offset;
       float* gd = a.l1_grad + 3 * V.pix_offset;
       const float cc[3] = {c0, c1, c2};
 #pragma unroll
       for (int ch = 0; ch < 3; ch++) {
-        const float d = cc[ch] - t[ch * plane + p];
+        const float d = cc[ch] - tv[k][ch];
         l1sum += fabsf(d);
         gd[ch * plane + p] = d > 0.f ? a.inv_count : (d < 0.f ? -a.inv_count : 0.f);
       }
