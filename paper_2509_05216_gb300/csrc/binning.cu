@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nb = gridDim.x;
   for (int v = 0; v < a.B; v++) {
-    const uint32_t c = live ? a.tiles[(int64_t)v * a.stride + g] : 0u;
+    const uint32_t c = live ? a.tiles[(int64_t)v * a.stride + g].x : 0u;
     const uint32_t t = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0) wtot[v][wid] = t;
   }
@@ -114,11 +114,10 @@ __global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
   int4 n_r3 = make_int4(0, 0, 0, 0);
   auto load_view = [&](int v) {
     const int64_t o = (int64_t)v * a.stride + g;
-    n_cnt = live ? a.tiles[o] : 0u;
-    if (n_cnt) {
-      n_r3 = a.rec3[o];
-      n_dbits = __float_as_uint(a.rec2[kRecStride * o].w);
-    }
+    const uint2 td = live ? a.tiles[o] : make_uint2(0u, 0u);
+    n_cnt = td.x;
+    n_dbits = td.y;
+    if (n_cnt) n_r3 = a.rec3[o];
   };
   load_view(0);
   for (int v = 0; v < a.B; v++) {

@@ -367,7 +367,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   GS_TRY(ensure(c, c->views, sizeof(ViewRec) * B));
   GS_TRY(ensure(c, c->rec, sizeof(float4) * kRecStride * B * stride));
   GS_TRY(ensure(c, c->rec3, sizeof(int4) * B * stride));
-  GS_TRY(ensure(c, c->tiles, sizeof(uint32_t) * B * stride));
+  GS_TRY(ensure(c, c->tiles, sizeof(uint2) * B * stride));
   GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * B * nb));
   if (c->capturing) {
     // a captured step copies the cameras from the pinned staging area at its start
@@ -385,7 +385,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   a.rec1 = P<float4>(c->rec) + 1;
   a.rec2 = P<float4>(c->rec) + 2;
   a.rec3 = P<int4>(c->rec3);
-  a.tiles = P<uint32_t>(c->tiles);
+  a.tiles = P<uint2>(c->tiles);
   a.block_sums = P<uint32_t>(c->block_sums);
   {
     LaunchScope ls(c, "project_fwd");
@@ -464,10 +464,8 @@ gs_status gs_bin_sort(gs_ctx* c) {
   d.stride = c->stride;
   d.views = P<ViewRec>(c->views);
   d.B = c->B;
-  d.rec0 = P<float4>(c->rec);
-  d.rec2 = P<float4>(c->rec) + 2;
   d.rec3 = P<int4>(c->rec3);
-  d.tiles = P<uint32_t>(c->tiles);
+  d.tiles = P<uint2>(c->tiles);
   d.block_offsets = P<uint32_t>(c->block_offsets);
   d.seg = seg;
   d.keys = P<uint64_t>(c->keys0);

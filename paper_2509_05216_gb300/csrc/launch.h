@@ -17,7 +17,7 @@ struct ProjectArgs {
   float4* rec1;  // (one interleaved array: rec1 = rec0 + 1, rec2 = rec0 + 2)
   float4* rec2;
   int4* rec3;            // (radius, tiles, x0 | x1 << 16, y0 | y1 << 16) per (view, Gaussian)
-  uint32_t* tiles;       // [B][stride]
+  uint2* tiles;          // [B][stride]: (tiles touched, bits of the depth)
   uint32_t* block_sums;  // [B][ceil(n / block)] instance counts per view and block
 };
 
@@ -34,10 +34,8 @@ struct DuplicateArgs {
   int64_t n, stride;
   const ViewRec* views;
   int B;
-  const float4* rec0;
-  const float4* rec2;
   const int4* rec3;
-  const uint32_t* tiles;
+  const uint2* tiles;  // (tiles touched, bits of the depth)
   const uint32_t* block_offsets;  // [B][blocks] exclusive scan of each view's block counts
   const uint32_t* seg;            // [B + 1] first instance of each view's segment
   uint64_t* keys;

@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
         }
       }
       a.rec3[o] = make_int4(tiles ? radius : 0, (int)tiles, x0 | (x1 << 16), y0 | (y1 << 16));
-      a.tiles[o] = tiles;
+      a.tiles[o] = make_uint2(tiles, __float_as_uint(depth));
     }
     // the warp's 32 records (48 bytes each) go out through shared memory as
     // 96 coalesced 16-byte stores instead of 3 x 32 stores at a 48-byte stride
