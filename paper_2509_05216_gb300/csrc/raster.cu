@@ -436,7 +436,7 @@ struct Geo {
   static constexpr int RW = CW, RH = (32 / CW) * PPT;  // warp rectangle
   // lane groups: NG groups of GW lanes, each a GCW x GRH pixel rectangle
   static constexpr int GW = GWv, NG = 32 / GW;
-  static constexpr int GCW = GW >= CW ? CW : GW / 2, GRH = (GW / GCW) * PPT, NGX = RW / GCW;
+  static constexpr int GCW = GW >= 16 ? CW : GW / 2, GRH = (GW / GCW) * PPT, NGX = RW / GCW;
   int64_t bin;
   int v, px, py0, grp;
   float wx0, wx1, wy0, wy1;
