@@ -895,6 +895,11 @@ gs_status gs_train_graph_launch_host(gs_ctx* c, const gs_camera* cams, int32_t B
   DevBuf& buf = slot ? c->host_tgt1 : c->host_tgt0;
   const size_t bytes = sizeof(float) * (size_t)c->graph_count;
   GS_TRY(ensure(c, buf, bytes));
+  // the upload is issued once the previous replay has started (has copied
+  // its staging area): issued earlier, it occupied the copy engine ahead of
+  // that replay's own small staging copy and delayed the replay by the
+  // length of the upload
+  GS_CUDA(c, cudaEventSynchronize(c->staged_ev));
   // the buffer is rewritten once the replay that read it (two calls ago) is done
   GS_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->tgt_free[slot], 0));
   GS_CUDA(c, cudaMemcpyAsync(buf.p, host_targets, bytes, cudaMemcpyHostToDevice, c->copy_stream));

@@ -189,7 +189,8 @@ __device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec
 // The same for groups of GW lanes that each walk their own Gaussian (lane
 // groups aligned to GW; contrib is the warp's ballot): the direct path is
 // taken when it holds for every group; otherwise each group sums its 9
-// values over its lanes (3 reduce-scatter levels, then butterflies).
+// values over its lanes (up to 3 reduce-scatter levels for values 0..7,
+// then butterflies; a butterfly for value 8) and adds the totals.
 template <int GW>
 __device__ __forceinline__ void push_grad_group(float* g2d, int64_t plane, int64_t rec, float (&acc)[16], int lane,
                                                 uint32_t contrib, int direct_max) {
