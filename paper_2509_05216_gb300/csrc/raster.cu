@@ -14,7 +14,9 @@
 // tile's list independently (no block barriers).  It stages 32 records at a
 // time, one per lane; each lane tests its record's alpha >= 1/255 ellipse
 // (with a rounding margin) against the warp's pixel rectangle, and the warp
-// walks only the survivors (a ballot mask).  This removes only pairs that
+// walks only the survivors (a ballot mask); with 2 pixels per thread the
+// warp's lanes form groups that each walk the survivors whose box reaches
+// their own sub-rectangle (see LaneGroups).  This removes only pairs that
 // the per-pixel test would skip, so the result is unchanged.
 #include "gs_internal.cuh"
 #include "launch.h"
@@ -524,7 +526,8 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
       if constexpr (G::NG > 1) gbits = box_group_bits(r0, r1, r2, geo);
       else hit = ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
     }
-    // each lane culls its own record; the warp walks the survivors in order
+    // each lane culls its own record; the warp (each lane group) walks the
+    // survivors in order
     uint32_t mask = __ballot_sync(0xffffffffu, hit);
     int iters = 32;
     if constexpr (G::NG > 1) {
