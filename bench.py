@@ -230,8 +230,9 @@ def render_targets(ctx, scene, cams, B, batches, device):
     return out, most
 
 
-# Algorithmic work per launch (documented in the design doc): bytes for the
-# HBM-bound kernels, FP32 operations for the compositing kernels.
+# Algorithmic work per launch: bytes for the HBM-bound kernels, FP32
+# operations for the compositing kernels (the operations the method needs
+# at one (pixel, Gaussian) pair, not the issued instructions).
 RASTER_OPS_FWD = 24   # FP32 ops per evaluated (pixel, Gaussian) pair, forward
 RASTER_OPS_BWD = 60   # FP32 ops per evaluated pair, backward
 
