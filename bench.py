@@ -241,13 +241,17 @@ def algorithmic_work(name, n, P, B, I, pairs, pixels):
     """(bound, work per launch scope): bytes for the HBM-bound kernels, FP32
     operations for the compositing kernels.  I = tile instances."""
     if name == "project_fwd":
-        return "hbm", n * (4 * P + B * 60.0)
+        # parameters once; per (view, Gaussian) the 48-byte record, the
+        # 16-byte (radius, tiles, rect) entry and the (tiles, depth) pair
+        return "hbm", n * (4 * P + B * 72.0)
     if name == "project_bwd":
         return "hbm", n * (8 * P + B * 36.0)
     if name == "adam":
         return "hbm", 28.0 * P * n
     if name == "duplicate":
-        return "hbm", n * B * 4.0 + 12.0 * I
+        # tile count, depth bits and packed tile rect per (view, Gaussian);
+        # key and value per instance written
+        return "hbm", n * B * 16.0 + 12.0 * I
     if name == "digit_histogram":
         return "hbm", 8.0 * I
     if name == "onesweep_pass":

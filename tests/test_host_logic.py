@@ -1,0 +1,129 @@
+"""Host-side logic that needs no GPU: the seeded input generators (cameras,
+perturbation, isosurface sampling and its memory order), the autotuner's
+selection and cache, and the benchmark's reading of recorded ncu traffic."""
+import hashlib
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2509_05216_gb300 import autotune, inputs  # noqa: E402
+
+
+def test_orbit_cameras_look_at_the_origin_from_the_radius():
+    r = 4.0
+    cams = inputs.orbit_cameras(5, 3, r, 64, 48)
+    assert len(cams) == 15
+    for c in cams:
+        vm = c["viewmat"]
+        # the origin lies on the optical axis (+z, camera looks forward) at depth r
+        o = vm[:3, :3] @ np.zeros(3) + vm[:3, 3]
+        assert np.allclose(o[:2], 0.0, atol=1e-5) and abs(o[2] - r) < 1e-5
+        # rows of the rotation are orthonormal (FP32-rounded)
+        assert np.allclose(vm[:3, :3] @ vm[:3, :3].T, np.eye(3), atol=1e-6)
+        assert c["fx"] == pytest.approx(64 / (2 * math.tan(math.radians(30.0))), rel=1e-6)
+        assert (c["cx"], c["cy"]) == (31.5, 23.5)
+    # elevations are evenly spaced inside (-75, 75) degrees: no camera at a pole
+    ups = [abs(np.linalg.inv(c["viewmat"])[2, 3]) / r for c in cams]
+    assert max(ups) < math.sin(math.radians(75.0))
+
+
+def test_perturbation_is_seeded_and_bounded():
+    scene = inputs.random_scene(300, 1, 7)
+    p = scene["params"].copy()
+    p[:, :5] = 0.0  # zero entries take the additive form
+    scene = dict(scene, params=p)
+    a = inputs.perturb(scene, 11)
+    b = inputs.perturb(scene, 11)
+    c = inputs.perturb(scene, 12)
+    n = scene["n"]
+    assert np.array_equal(a["params"], b["params"])
+    assert not np.array_equal(a["params"], c["params"])
+    x = p[:, :n].astype(np.float64)
+    y = a["params"][:, :n].astype(np.float64)
+    nz = x != 0.0
+    # p' = p (1 + 0.05 u), u in [-1, 1]: relative change at most 5 %
+    assert np.all(np.abs(y[nz] - x[nz]) <= 0.05 * np.abs(x[nz]) * (1 + 1e-6) + 1e-7)
+    # p = 0: p' = 0.05 u
+    assert np.all(np.abs(y[~nz]) <= 0.05 + 1e-7) and np.any(y[~nz] != 0.0)
+    # padding columns beyond n are untouched
+    assert np.array_equal(a["params"][:, n:], p[:, n:])
+
+
+def test_isosurface_samples_lie_on_the_level_set_in_cell_order():
+    lo, hi, res, n = -2.0 * math.pi, 2.0 * math.pi, 12, 3000
+    pts = inputs._sample_isosurface(inputs._gyroid_fg, lo, hi, 0.0, n, seed=3, res=res, device="cpu")
+    again = inputs._sample_isosurface(inputs._gyroid_fg, lo, hi, 0.0, n, seed=3, res=res, device="cpu")
+    assert pts.shape == (n, 3) and np.array_equal(pts, again)
+    f, _ = inputs._gyroid_fg(torch.from_numpy(pts))
+    assert float(f.abs().max()) < 1e-6
+    assert np.all((pts >= lo) & (pts <= hi))
+    # contour-filter order: by sampling cell, x fastest, then y, then z
+    h = (hi - lo) / res
+    cell = np.clip(np.floor((pts - lo) / h).astype(np.int64), 0, res - 1)
+    key = (cell[:, 2] * res + cell[:, 1]) * res + cell[:, 0]
+    assert np.all(np.diff(key) >= 0)
+    # so that neighbours in memory are near in space: consecutive points are
+    # far closer than random pairs
+    step = np.linalg.norm(np.diff(pts, axis=0), axis=1).mean()
+    rng = np.random.default_rng(0)
+    i, j = rng.integers(0, n, size=(2, 2000))
+    assert step < 0.25 * np.linalg.norm(pts[i] - pts[j], axis=1).mean()
+
+
+class _FakeCtx:
+    def __init__(self):
+        self.options = {}
+
+    def gs_set_option(self, opt, value):
+        self.options[opt] = value
+
+
+def test_autotuner_keeps_the_fastest_value_of_each_option_and_caches(tmp_path, monkeypatch):
+    monkeypatch.setenv("GS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    ctx = _FakeCtx()
+    cost = {1: {2: 5.0, 8: 3.0, 4: 4.0}, 2: {0: 2.0, 2: 1.0}}
+    calls = []
+
+    def fake_time(step, reps=3):
+        calls.append(dict(ctx.options))
+        return sum(cost[o][v] for o, v in ctx.options.items() if o in cost)
+
+    monkeypatch.setattr(autotune, "time_step", fake_time)
+    cands = {1: [2, 8, 4], 2: [0, 2]}
+    chosen = autotune.tune([ctx], lambda: None, "key-a", candidates=cands, rounds=2)
+    assert chosen == {1: 8, 2: 2}
+    assert ctx.options == {1: 8, 2: 2}
+    # every candidate was timed in each of the two rounds
+    assert len(calls) == 2 * (3 + 2)
+    # a second tune of the same workload takes the cached choice without timing
+    calls.clear()
+    ctx2 = _FakeCtx()
+    assert autotune.tune([ctx2], lambda: None, "key-a", candidates=cands) == {1: 8, 2: 2}
+    assert calls == [] and ctx2.options == {1: 8, 2: 2}
+
+
+def test_recorded_traffic_is_used_only_for_the_profiled_source(tmp_path, monkeypatch):
+    src = tmp_path / "paper_2509_05216_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "raster.cu").write_text("// kernel source\n")
+    sha = hashlib.sha1(b"// kernel source\n").hexdigest()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    table = ("| kernel: DRAM bytes per launch | read | write |\n|---|---|---|\n"
+             "| raster_bwd_kernel<2>: 6.5e+09 bytes per launch | read 5.3e+09 | write 1.2e+09 |\n")
+    summary = prof / "raster_traffic_blobs4M_2048sq_B16.md"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    summary.write_text("raster.cu sha1 %s\n\n%s" % (sha, table))
+    assert bench.recorded_traffic("raster_bwd", 2) == 6.5e9
+    assert bench.recorded_traffic("raster_fwd", 2) is None
+    # another version of the kernel source: no recorded traffic
+    summary.write_text("raster.cu sha1 %s\n\n%s" % ("0" * 40, table))
+    assert bench.recorded_traffic("raster_bwd", 2) is None
