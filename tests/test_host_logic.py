@@ -1,6 +1,7 @@
 """Host-side logic that needs no GPU: the seeded input generators (cameras,
 perturbation, isosurface sampling and its memory order), the autotuner's
-selection and cache, and the benchmark's reading of recorded ncu traffic."""
+selection and cache, the benchmark's reading of recorded ncu traffic, and
+the CPU binning reference of the GPU parity tests against brute force."""
 import hashlib
 import math
 import os
@@ -127,3 +128,60 @@ def test_recorded_traffic_is_used_only_for_the_profiled_source(tmp_path, monkeyp
     # another version of the kernel source: no recorded traffic
     summary.write_text("raster.cu sha1 %s\n\n%s" % ("0" * 40, table))
     assert bench.recorded_traffic("raster_bwd", 2) is None
+
+
+def test_cpu_binning_reference_equals_brute_force():
+    """The vectorised CPU binning that the GPU parity tests compare against,
+    checked against a plain loop over (view, Gaussian, tile) and a sort of
+    (key, Gaussian) pairs on small random inputs (empty rects, rects clipped
+    at the image border, equal depths)."""
+    from tests.gpu_helpers import cpu_rect, expected_binning
+    rng = np.random.default_rng(5)
+    cams = [inputs.pinhole(np.eye(4), 70, 45), inputs.pinhole(np.eye(4), 33, 80)]
+    n, stride = 40, 48
+    B = len(cams)
+    rec0 = np.zeros((B * stride, 4), np.float32)
+    rec2 = np.zeros((B * stride, 4), np.float32)
+    rec3 = np.zeros((B * stride, 4), np.int32)
+    for v, c in enumerate(cams):
+        sl = slice(v * stride, v * stride + n)
+        rec0[sl, 0] = rng.uniform(-20, c["width"] + 20, n)
+        rec0[sl, 1] = rng.uniform(-20, c["height"] + 20, n)
+        rad = rng.integers(0, 30, n)
+        x0, x1, y0, y1 = cpu_rect(rec0[sl, 0], rec0[sl, 1], rad, c["width"], c["height"])
+        tiles = (x1 - x0) * (y1 - y0)
+        rec3[sl, 0] = np.where(tiles > 0, rad, 0)
+        rec3[sl, 1] = tiles
+        rec2[sl, 3] = rng.choice(np.float32([1.5, 2.25, 3.0, 7.0]), n)  # many equal depths
+    keys, vals, ranges, per_view = expected_binning(rec0, rec2, rec3, cams, n, stride)
+
+    pairs, tile_off = [], 0
+    ref_per_view = []
+    for v, c in enumerate(cams):
+        gw, gh = (c["width"] + 15) // 16, (c["height"] + 15) // 16
+        count = 0
+        for g in range(n):
+            o = v * stride + g
+            if rec3[o, 1] == 0:
+                continue
+            x0, x1, y0, y1 = (int(t[0]) for t in cpu_rect(rec0[o:o + 1, 0], rec0[o:o + 1, 1],
+                                                          rec3[o:o + 1, 0].astype(np.int64),
+                                                          c["width"], c["height"]))
+            d = int(np.float32(rec2[o, 3]).view(np.uint32))
+            for ty in range(y0, y1):
+                for tx in range(x0, x1):
+                    pairs.append((((tile_off + ty * gw + tx) << 32) | d, g))
+                    count += 1
+        ref_per_view.append(count)
+        tile_off += gw * gh
+    pairs.sort()  # by key, then Gaussian index (the stable order of equal keys)
+    assert list(per_view) == ref_per_view
+    assert [int(k) for k in keys] == [p[0] for p in pairs]
+    assert [int(x) for x in vals] == [p[1] for p in pairs]
+    ref_ranges = np.zeros((tile_off, 2), np.int64)
+    for i, (k, _) in enumerate(pairs):
+        b = k >> 32
+        if i == 0 or (pairs[i - 1][0] >> 32) != b:
+            ref_ranges[b, 0] = i
+        ref_ranges[b, 1] = i + 1
+    assert np.array_equal(ranges, ref_ranges)
