@@ -268,6 +268,8 @@ gs_status gs_train_graph_launch(gs_ctx* ctx, const gs_camera* cams, int32_t B, c
  * uploaded on the context's own copy stream into one of two device buffers,
  * so the upload for the next call overlaps this replay (overlap needs
  * page-locked host memory; pageable memory works but copies synchronously).
+ * The call first waits until the previous replay has started (has copied
+ * its staging area), so that the upload never queues ahead of that copy.
  * The host buffers must stay valid and unchanged until the step has run
  * (gs_sync); *host_loss (may be NULL; page-locked for an asynchronous read)
  * holds the step's loss after gs_sync.
