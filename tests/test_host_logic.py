@@ -1,7 +1,8 @@
 """Host-side logic that needs no GPU: the seeded input generators (cameras,
 perturbation, isosurface sampling and its memory order), the autotuner's
-selection and cache, the benchmark's reading of recorded ncu traffic, and
-the CPU binning reference of the GPU parity tests against brute force."""
+selection and cache, the benchmark's reading of recorded ncu traffic, the
+CPU binning reference of the GPU parity tests against brute force, and the
+reference-set recipe (orientation, KNN scale, Lambertian colour, packing)."""
 import hashlib
 import math
 import os
@@ -185,3 +186,48 @@ def test_cpu_binning_reference_equals_brute_force():
             ref_ranges[b, 0] = i
         ref_ranges[b, 1] = i + 1
     assert np.array_equal(ranges, ref_ranges)
+
+
+def _rotation(q):
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_surface_gaussians_are_oriented_scaled_and_lit_as_stated():
+    """The reference-set recipe: rotation taking +z onto the surface normal,
+    KNN scale, Lambertian DC grey under the SH colour rule."""
+    rng = np.random.default_rng(8)
+    nrm = rng.normal(size=(200, 3))
+    nrm[0] = (0.0, 0.0, -1.0)  # the antipodal case
+    nrm[1] = (0.0, 0.0, 1.0)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    q = inputs._quat_z_to(nrm)
+    for qi, ni in zip(q, nrm):
+        assert np.allclose(_rotation(qi) @ np.array([0.0, 0.0, 1.0]), ni, atol=1e-9)
+    # the colour of the DC term alone: rgb = Y00 sh0 + 0.5 = 0.1 + 0.9 max(0, n.l)
+    y00 = 1.0 / (2.0 * math.sqrt(math.pi))
+    light = np.ones(3) / math.sqrt(3.0)
+    grey = y00 * inputs._lambert_dc(nrm) + 0.5
+    assert np.allclose(grey, 0.1 + 0.9 * np.maximum(0.0, nrm @ light), atol=1e-12)
+    # KNN scale against brute force
+    pts = rng.uniform(-1, 1, size=(300, 3))
+    d2 = ((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    ref = 0.5 * np.log(np.sort(d2, axis=1)[:, :3].mean(1))
+    assert np.allclose(inputs.knn_log_scale(pts), ref, atol=1e-12)
+
+
+def test_parameter_planes_round_trip():
+    rng = np.random.default_rng(9)
+    n, k = 13, 16
+    arrays = dict(means=rng.normal(size=(n, 3)), log_scales=rng.normal(size=(n, 3)),
+                  quats=rng.normal(size=(n, 4)), opacity_logits=rng.normal(size=n),
+                  sh=rng.normal(size=(n, k, 3)))
+    scene = inputs.pack_params(**arrays)
+    assert scene["deg"] == 3 and scene["params"].shape == (59, 16)
+    assert np.all(scene["params"][:, n:] == 0.0)
+    back = inputs.unpack_params(scene)
+    for name, a in arrays.items():
+        assert np.array_equal(back[name], a.astype(np.float32)), name
