@@ -127,20 +127,39 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, interval_ms=50, first_wait_s=3.0):
         self.index = index
+        self.interval_ms = interval_ms
+        self.first_wait_s = first_wait_s
         self.rows = []
+        self.start = 0
         self.proc = None
 
-    def __enter__(self):
+    def _launch(self, interval_ms):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi takes a while to print its first line: wait for it
+        # (bounded) so that the samples cover the region that follows
+        t0 = time.time()
+        while not self.rows and time.time() - t0 < self.first_wait_s:
+            if self.proc.poll() is not None:
+                self.t.join(timeout=1.0)
+                break
+            time.sleep(0.005)
+
+    def __enter__(self):
+        self._launch(self.interval_ms)
+        if self.proc is not None and not self.rows and self.proc.poll() is not None and self.interval_ms < 200:
+            self._launch(200)  # the short interval was refused: the tool's usual one
+        # summarise only the samples taken from here on
+        self.start = len(self.rows)
         return self
 
     def _read(self):
@@ -156,15 +175,16 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        if not self.rows:
+        rows = self.rows[self.start:] or self.rows[-1:]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4)
+        reasons = sorted({names[i] for r in rows for i in range(4)
                           if len(r) > 5 + i and r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 # ---------------------------------------------------------------- GPU arm

@@ -1,8 +1,9 @@
 """Host-side logic that needs no GPU: the seeded input generators (cameras,
 perturbation, isosurface sampling and its memory order), the autotuner's
 selection and cache, the benchmark's reading of recorded ncu traffic, the
-CPU binning reference of the GPU parity tests against brute force, and the
-reference-set recipe (orientation, KNN scale, Lambertian colour, packing)."""
+CPU binning reference of the GPU parity tests against brute force, the
+reference-set recipe (orientation, KNN scale, Lambertian colour, packing)
+and the benchmark's clock sampler (against a stand-in nvidia-smi)."""
 import hashlib
 import math
 import os
@@ -231,3 +232,46 @@ def test_parameter_planes_round_trip():
     back = inputs.unpack_params(scene)
     for name, a in arrays.items():
         assert np.array_equal(back[name], a.astype(np.float32)), name
+
+
+def test_clock_sampler_waits_for_samples_and_summarises_the_region(tmp_path, monkeypatch):
+    """The benchmark's clock record, against a stand-in nvidia-smi that
+    prints one CSV line every 20 ms (the first after 150 ms, like the real
+    tool's start-up)."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\nsleep 0.15\nwhile true; do\n"
+                    "  echo '0, 2070, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active'\n"
+                    "  sleep 0.02\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    import time
+    with bench.ClockSampler(0, interval_ms=20) as clk:
+        assert clk.rows, "the region starts only after the first sample"
+        time.sleep(0.2)
+    s = clk.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    assert s["samples"] >= 3
+    # no nvidia-smi at all: the record says so and the region is not delayed
+    monkeypatch.setenv("PATH", str(tmp_path / "empty"))
+    t0 = time.time()
+    with bench.ClockSampler(0) as clk:
+        pass
+    assert time.time() - t0 < 1.0
+    assert clk.summary()["reasons"] == ["unavailable"]
+
+
+def test_clock_sampler_falls_back_to_the_usual_interval(tmp_path, monkeypatch):
+    """A tool that refuses the short interval: the sampler restarts it at
+    200 ms and still records the region."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\ncase \"$*\" in *'-lms 200'*) ;; *) exit 2 ;; esac\nwhile true; do\n"
+                    "  echo '0, 1980, 2070, 700.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "  sleep 0.05\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    import time
+    with bench.ClockSampler(0, interval_ms=50) as clk:
+        time.sleep(0.15)
+    s = clk.summary()
+    assert s["sm_mhz"] == 1980.0 and s["reasons"] == [] and s["samples"] >= 2
