@@ -133,10 +133,18 @@ typedef enum {
                             lanes' gradients with per-lane atomics instead of
                             a warp reduction.  Same result up to FP32
                             summation order. */
-  GS_OPT_SORT_ITEMS = 3  /* keys per thread of a radix-sort partition: 12, 16
+  GS_OPT_SORT_ITEMS = 3, /* keys per thread of a radix-sort partition: 12, 16
                             (default), 20 or 24 (partitions of 256 x items
                             keys).  Same result.  Fixed once a training graph
                             is captured (GS_ESTATE). */
+  GS_OPT_SORT_WAIT = 4   /* look-back rounds a radix-sort partition waits for
+                            the partitions before it: 1 .. 1048576 (default
+                            1048576, about a second), after which the sort
+                            gives up and the next gs_sync reports
+                            GS_ETIMEOUT.  0: every partition that has to look
+                            back gives up at once (exercises the timeout
+                            path; the blocks return, nothing hangs).  Fixed
+                            once a training graph is captured (GS_ESTATE). */
 } gs_option;
 
 /* Set / read an option.  Errors: GS_EINVAL (unknown option, bad value). */

@@ -191,7 +191,6 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kFlagAggregate = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
-constexpr int kSpinLimit = 1 << 20;  // look-back rounds before giving up (about a second)
 constexpr int kLookWindow = 16;       // statuses read per look-back round
 
 // Partitions never straddle a view's segment: at most one partial
@@ -406,7 +405,9 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   // kLookWindow statuses per round trip; a status that is not ready yet is
   // re-read (bounded)
   uint32_t excl = 0;
-  if (lp0 > 0) {
+  if (lp0 > 0 && a.wait_rounds <= 0) {
+    sm.timed_out = 1;  // give up without looking (exercises the timeout path)
+  } else if (lp0 > 0) {
     const int64_t first = (int64_t)sm.first_part;
     int64_t j = (int64_t)part - 1;
     int rounds = 0;
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
         if (flag == kFlagPrefix) found = true;
       }
       j -= used;
-      if (!found && ++rounds > kSpinLimit) {
+      if (!found && ++rounds > a.wait_rounds) {
         sm.timed_out = 1;
         break;
       }

@@ -60,6 +60,7 @@ struct gs_ctx {
   int bwd_direct = 2;  // per-lane gradient atomics when at most this many lanes contribute
   int sort_passes = 0;  // LSD passes of the last sort
   int sort_items = 16;  // keys per thread of a sort partition
+  int sort_wait = 1 << 20;  // look-back rounds before a sort gives up
 
   // last batch
   int B = 0, deg = 0;
@@ -498,6 +499,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   sa.lookback_stride = lb / sizeof(uint32_t);
   sa.counters = P<uint32_t>(c->counters);
   sa.npass = npass;
+  sa.wait_rounds = c->sort_wait;
   sa.status = c->status_d;
   sa.sorted_keys = reinterpret_cast<const uint64_t**>(c->sorted_slots.p);
   sa.sorted_vals = reinterpret_cast<const uint32_t**>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
@@ -764,6 +766,11 @@ gs_status gs_set_option(gs_ctx* c, int32_t option, int64_t value) {
       if (c->capturing || c->gexec) return fail(c, GS_ESTATE, "sort partition size is fixed once a graph is captured");
       c->sort_items = (int)value;
       return GS_OK;
+    case GS_OPT_SORT_WAIT:
+      if (value < 0 || value > (1 << 20)) return fail(c, GS_EINVAL, "sort wait rounds must be 0..1048576");
+      if (c->capturing || c->gexec) return fail(c, GS_ESTATE, "sort wait is fixed once a graph is captured");
+      c->sort_wait = (int)value;
+      return GS_OK;
     default:
       return fail(c, GS_EINVAL, "unknown option %d", option);
   }
@@ -776,6 +783,7 @@ gs_status gs_get_option(gs_ctx* c, int32_t option, int64_t* value) {
     case GS_OPT_RASTER_BWD: *value = c->raster_bwd; return GS_OK;
     case GS_OPT_BWD_DIRECT: *value = c->bwd_direct; return GS_OK;
     case GS_OPT_SORT_ITEMS: *value = c->sort_items; return GS_OK;
+    case GS_OPT_SORT_WAIT: *value = c->sort_wait; return GS_OK;
     default: return fail(c, GS_EINVAL, "unknown option %d", option);
   }
 }

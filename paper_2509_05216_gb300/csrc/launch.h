@@ -101,6 +101,7 @@ struct SortArgs {
   size_t lookback_stride;    // uint32 per pass (sort_lookback_bytes / 4)
   uint32_t* counters;        // [8] partition tickets
   int npass;
+  int wait_rounds;  // look-back rounds before giving up (0: give up at once)
   int* status;
   const uint64_t** sorted_keys;  // device slots: where the sorted list ends up
   const uint32_t** sorted_vals;
