@@ -267,6 +267,103 @@ def test_sh_basis_orthonormal_by_quadrature(oracle):
     np.testing.assert_allclose(gram, np.eye(16), atol=1e-12)
 
 
+def _band1_scene(mu, sh0, band1):
+    """One small Gaussian at mu with DC sh0 per channel and, in channel c,
+    only the band-1 coefficient k = 1 + c set to band1 (k = 1, 2, 3 multiply
+    the y, z and x components of the view direction)."""
+    sh = np.zeros((1, 4, 3))
+    sh[0, 0, :] = sh0
+    for c in range(3):
+        sh[0, 1 + c, c] = band1
+    return I.pack_params(np.asarray([mu], np.float64), np.full((1, 3), math.log(0.05)),
+                         np.asarray([[1.0, 0.0, 0.0, 0.0]]), np.asarray([0.5]), sh)
+
+
+def test_sh_view_direction_degree1_closed_form(oracle):
+    """Degree-1 colour in closed form: rgb_c = 0.5 + Y00 sh0_c + sqrt(3/(4 pi))
+    sh1_c d_(y, z, x)[c] with d = (mu - eye) / |mu - eye| taken from the eye
+    the test placed.  The second eye lies on the other side of the Gaussian,
+    which flips every component of d and so every band-1 term: a negated
+    direction, or a camera centre taken with the wrong sign, fails here."""
+    c1 = math.sqrt(3.0 / (4.0 * math.pi))
+    mu = (0.3, -0.2, 0.25)
+    sc = _band1_scene(mu, 0.15, 0.6)
+    P = sc["params"][:, 0].astype(np.float64)  # the FP32-rounded values the oracle sees
+    m = P[0:3]
+    cols = []
+    for eye in [(2.0, 2.0, 1.5), (-1.5, -2.2, -1.2)]:
+        cam = I.pinhole(I.look_at(eye, target=mu), 48, 48)
+        pr = oracle.project(sc, cam)
+        assert pr["flags"][0] & oracle.G_VISIBLE
+        d = m - np.asarray(eye, np.float64)
+        d /= np.linalg.norm(d)
+        comp = (d[1], d[2], d[0])  # Y_1,-1 ~ y, Y_1,0 ~ z, Y_1,1 ~ x
+        expect = np.array([0.5 + Y00 * P[11 + c] + c1 * P[11 + 3 * (1 + c) + c] * comp[c] for c in range(3)])
+        # the camera is stored in FP32, so its centre is the eye to ~1e-7
+        np.testing.assert_allclose(pr["raw_rgb"][0], expect, rtol=0, atol=2e-6)
+        np.testing.assert_allclose(pr["rgb"][0], expect, rtol=0, atol=2e-6)
+        cols.append(expect - 0.5 - Y00 * P[11:14])
+    # the two eyes see band-1 terms of opposite sign, each well away from zero
+    assert np.all(cols[0] * cols[1] < 0) and np.all(np.abs(cols[0]) > 0.05)
+
+
+@pytest.mark.parametrize("axis,slope", [(0, 1.0), (0, -0.9), (1, 1.1), (0, 0.5)])
+def test_guard_band_clamps_the_slope_in_J(oracle, axis, slope):
+    """An isotropic Gaussian (Sigma = s^2 I) seen by the axis camera at
+    camera-space t = (t_x, t_y, d): Sigma' = s^2 J J^T + 0.3 I with
+    J = [[fx/d, 0, -fx u_x/d], [0, fy/d, -fy u_y/d]], u the image-plane slope
+    t/d clamped to +-1.3 W/(2 fx) (1.3 H/(2 fy)).  Beyond the guard band the
+    conic is that of the clamped slope, its derivative with respect to the
+    mean along the clamped axis is zero (only J's slope entries depend on
+    it), while mu2D keeps its unclamped derivative fx / d; inside the band
+    (slope 0.5) the same derivative is the closed form of the unclamped J."""
+    cam = axis_camera(64)
+    d, s = 3.0, 0.05
+    # camera axes of the axis camera: x = world x, y = -world y, t_z = d - world z
+    t_lat = slope * d
+    mu = [t_lat, 0.0, 0.0] if axis == 0 else [0.0, -t_lat, 0.0]
+    sc = one_scene([mu], [[math.log(s)] * 3], [[1, 0, 0, 0]], [0.0], [(0.5, 0.5, 0.5)])
+    P = sc["params"][:, 0].astype(np.float64)
+    s2 = math.exp(2.0 * P[3])
+    f = cam["fx"] if axis == 0 else cam["fy"]
+    size = cam["width"] if axis == 0 else cam["height"]
+    lim = 1.3 * size / (2.0 * f)
+    t = abs(P[axis]) if axis == 0 else abs(P[1])
+    u = t / d
+    clamped = u > lim
+    assert clamped == (abs(slope) > lim)
+    uc = min(u, lim)
+    # Sigma' along the lateral axis, and along the other one
+    lat = s2 * (f / d) ** 2 * (1.0 + uc * uc) + 0.3
+    other = s2 * (cam["fx"] / d) ** 2 + 0.3
+    s00, s11 = (lat, other) if axis == 0 else (other, lat)
+    pr = oracle.project(sc, cam)
+    assert pr["flags"][0] & 32  # 2D quantities computed (in front of znear)
+    assert not pr["flags"][0] & oracle.G_MARG_GUARD
+    np.testing.assert_allclose(pr["conic"][0], [1.0 / s00, 0.0, 1.0 / s11], rtol=1e-12, atol=1e-15)
+
+    jac, _ = oracle.project_jacobian(sc, cam, 0)
+    A_row = 2 if axis == 0 else 4        # the conic entry 1 / Sigma'_lat
+    mu_row = 0 if axis == 0 else 1
+    wsign = 1.0 if axis == 0 else -1.0   # d t_lat / d world mean
+    # d mu2D / d mean: fx / d (camera y = -world y), clamped or not
+    assert jac[mu_row, axis] == pytest.approx(wsign * f / d, rel=1e-12)
+    dlat_dt = 0.0 if clamped else s2 * (f / d) ** 2 * 2.0 * uc / d * math.copysign(1.0, P[axis])
+    expect = -dlat_dt / lat ** 2 * wsign
+    if clamped:
+        assert jac[A_row, axis] == 0.0
+        assert jac[3, axis] == 0.0
+    else:
+        assert abs(expect) > 1e-3
+        assert jac[A_row, axis] == pytest.approx(expect, rel=1e-10)
+    # the depth derivative keeps the clamped slope fixed: Sigma'_lat - 0.3 ~ 1 / t_z^2
+    dlat_dz = 2.0 * s2 * (f / d) ** 2 * (1.0 + uc * uc) / d
+    if not clamped:
+        # u = t / t_z also moves with t_z: d(u^2)/d t_z = -2 u^2 / t_z
+        dlat_dz += s2 * (f / d) ** 2 * 2.0 * uc * uc / d
+    assert jac[A_row, 2] == pytest.approx(-dlat_dz / lat ** 2, rel=1e-10)
+
+
 # ---------------------------------------------------------------- derivatives
 
 def test_projection_jacobian_matches_finite_differences(oracle):
