@@ -251,15 +251,31 @@ def render_targets(ctx, scene, cams, B, batches, device):
 
 
 # Algorithmic work per launch: bytes for the HBM-bound kernels, FP32
-# operations for the compositing kernels (the operations the method needs
-# at one (pixel, Gaussian) pair, not the issued instructions).
-RASTER_OPS_FWD = 24   # FP32 ops per evaluated (pixel, Gaussian) pair, forward
-RASTER_OPS_BWD = 60   # FP32 ops per evaluated pair, backward
+# operations (an FMA counts 2) for the compositing kernels: the operations the
+# method needs at one (pixel, Gaussian) pair, not the issued instructions.
+# Every list entry up to a pixel's last contributor needs the alpha test
+# (offset, quadratic form, opacity times ex2: 10 operations); a contributing
+# pair (power <= 0, alpha >= 1/255) also needs the compositing arithmetic
+# (forward: transmittance update and colour, 9 more; backward: recovered
+# transmittance, dL/dalpha and the nine gradient terms, 30 more).  ex2 and
+# the reciprocal run on the special-function unit and are not counted.
+RASTER_OPS_TEST = 10
+RASTER_OPS_FWD = 19   # per contributing pair, forward
+RASTER_OPS_BWD = 40   # per contributing pair, backward
+
+
+def raster_work(kind, entries, contributing):
+    """FP32 operations of one compositing launch: contributing pairs at the
+    full per-pair count, the other entries up to each pixel's last
+    contributor at the alpha-test count."""
+    full = RASTER_OPS_FWD if kind == "fwd" else RASTER_OPS_BWD
+    return full * contributing + RASTER_OPS_TEST * (entries - contributing)
 
 
 def algorithmic_work(name, n, P, B, I, pairs, pixels):
     """(bound, work per launch scope): bytes for the HBM-bound kernels, FP32
-    operations for the compositing kernels.  I = tile instances."""
+    operations for the compositing kernels.  I = tile instances; pairs =
+    (entries up to each pixel's last contributor, contributing pairs)."""
     if name == "project_fwd":
         # parameters once; per (view, Gaussian) the 48-byte record, the
         # 16-byte (radius, tiles, rect) entry and the (tiles, depth) pair
@@ -279,35 +295,10 @@ def algorithmic_work(name, n, P, B, I, pairs, pixels):
     if name == "tile_ranges":
         return "hbm", 8.0 * I
     if name == "raster_fwd":
-        return "alu", RASTER_OPS_FWD * pairs
+        return "alu", raster_work("fwd", *pairs)
     if name == "raster_bwd":
-        return "alu", RASTER_OPS_BWD * pairs
+        return "alu", raster_work("bwd", *pairs)
     return None, None
-
-
-def recorded_traffic(kernel, variant):
-    """DRAM bytes per launch of a compositing kernel variant from the ncu
-    summary in profiles/, or None when that summary was taken on another
-    version of the kernel source (its sha1 is recorded beside the numbers)."""
-    import hashlib
-    src = os.path.join(ROOT, "paper_2509_05216_gb300", "csrc", "raster.cu")
-    summary = os.path.join(ROOT, "profiles", "raster_traffic_blobs4M_2048sq_B16.md")
-    try:
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        text = open(summary).read()
-    except OSError:
-        return None
-    if ("raster.cu sha1 %s" % sha) not in text:
-        return None
-    tag = "%s_kernel<%d>:" % (kernel, variant)
-    for line in text.splitlines():
-        line = line.strip().strip("|").strip()
-        if line.startswith(tag):
-            try:
-                return float(line[len(tag):].split()[0])
-            except ValueError:
-                return None
-    return None
 
 
 def gpu_arm(args):
@@ -324,6 +315,7 @@ def gpu_arm(args):
     dev = torch.device("cuda", local)
     torch.zeros(1, device=dev)
     free0, hbm_total = torch.cuda.mem_get_info(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     scene, trained, cams = workload(args, device=dev)
     torch.cuda.empty_cache()
     B = args.batch
@@ -425,10 +417,10 @@ def gpu_arm(args):
     kstats = ctx.profile_read()
     ctx.gs_sync()
 
-    # work counters of one batched step (for the roofline)
+    # work counters of one batched step (for the roofline): list entries up
+    # to each pixel's last contributor and the contributing pairs among them
     inst, bins, pixels = ctx.gs_get_counts()
-    nl = ctx.gs_get_buffer(gs.GS_BUF_NLAST)
-    pairs = float(nl.to(torch.float64).sum().item())
+    pairs = ctx.gs_pair_stats()
     P = tr.p.shape[0]
     dom = max(kstats, key=lambda k: k["total_ms"])
     per_kernel = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
@@ -465,13 +457,17 @@ def gpu_arm(args):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     else:
         clk_max = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = 152 * 128 * 2 * clk_max * 1e6 / 1e12  # FP32 TFLOP/s, FMA = 2
+        peak = sms * 128 * 2 * clk_max * 1e6 / 1e12  # FP32 TFLOP/s, FMA = 2
         achieved = work / (avg_ms / 1e3) / 1e12
         variant = tuned.get(gs.GS_OPT_RASTER_BWD if dom["name"] == "raster_bwd" else gs.GS_OPT_RASTER_FWD, 2)
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom["name"], variant),
+                "frac": round(achieved / peak, 4), "traffic": None,
                 "kernel": "%s<%d>" % (dom["name"], variant),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"}
+                "work": "%d FP32 ops per contributing pair x %d contributing + %d per other entry up to the "
+                        "last contributor x %d" % (RASTER_OPS_BWD if dom["name"] == "raster_bwd" else RASTER_OPS_FWD,
+                                                   pairs[1], RASTER_OPS_TEST, pairs[0] - pairs[1]),
+                "peak_source": "%d SMs (device attribute) x 128 FP32 lanes x 2 x max SM clock "
+                               "(MEASURED_PEAKS sm_max_mhz)" % sms}
 
     # plain path: one view per launch, Adam after each view
     ctx2 = gs.Context(local)
@@ -537,7 +533,8 @@ def gpu_arm(args):
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
         "graph": "each timed step is one CUDA-graph launch of the whole step; per-kernel times and the roofline "
                  "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
-        "instances_per_step": int(inst), "pairs_per_step": pairs, "sort_passes_executed": executed,
+        "instances_per_step": int(inst), "pair_entries_per_step": int(pairs[0]),
+        "contributing_pairs_per_step": int(pairs[1]), "sort_passes_executed": executed,
         "kernels": per_kernel,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
         "memory": memory,

@@ -367,6 +367,17 @@ gs_status gs_get_buffer(gs_ctx* ctx, int32_t which, void** ptr, int64_t* count);
  * Synchronises the stream to read the device-side instance count. */
 gs_status gs_get_counts(gs_ctx* ctx, int64_t* instances, int64_t* bins, int64_t* pixels);
 
+/* Work counters of the last forward pass, for the compositing roofline (not
+ * part of the training step; one extra pass over the lists, then a stream
+ * synchronisation).  *entries = sum over pixels of the list entries up to and
+ * including the pixel's last contributor (what the backward walks; a lower
+ * bound of what the forward walks); *contributing = the pairs among them with
+ * power <= 0 and alpha >= 1/255 (the pairs that change the pixel; the
+ * compositing rule of step 3), decided with the compositing kernels' own FP32
+ * instruction sequence.  Errors: GS_EINVAL, GS_ESTATE (no forward pass, or
+ * inside a graph capture), GS_ENOMEM, GS_ECUDA. */
+gs_status gs_pair_stats(gs_ctx* ctx, int64_t* entries, int64_t* contributing);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Per-kernel accounting: every launch the library makes is counted; while

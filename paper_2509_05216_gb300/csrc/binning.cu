@@ -555,9 +555,7 @@ __global__ void sort_control_kernel(SortArgs a, int items) {
 }
 
 void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, int items, cudaStream_t s) {
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   // about 8 blocks per SM over all views, at least one per view
   int64_t want = (grid_hint + 4095) / 4096;
   want = want < 1 ? 1 : (want > (int64_t)sms * 8 ? (int64_t)sms * 8 : want);
@@ -616,7 +614,8 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __r
 
 void launch_tile_ranges(const SortArgs& a, int64_t grid_hint, uint2* ranges, cudaStream_t s) {
   int64_t blocks = (grid_hint + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  const int64_t most = (int64_t)sm_count() * 32;
+  if (blocks > most) blocks = most;
   if (blocks < 1) blocks = 1;
   tile_ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, ranges);
 }

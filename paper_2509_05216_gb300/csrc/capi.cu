@@ -70,7 +70,7 @@ struct gs_ctx {
 
   DevBuf views, rec, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
-      target_slot, host_tgt0, host_tgt1;
+      target_slot, host_tgt0, host_tgt1, pair_stats;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -307,7 +307,8 @@ void gs_destroy(gs_ctx* c) {
   DevBuf* bufs[] = {&c->views, &c->rec, &c->rec3, &c->tiles, &c->block_sums, &c->block_offsets,
                     &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->hist_scan,
                     &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
-                    &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1};
+                    &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1,
+                    &c->pair_stats};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -744,6 +745,25 @@ gs_status gs_get_counts(gs_ctx* c, int64_t* instances, int64_t* bins, int64_t* p
   if (instances) *instances = c->sorted ? (int64_t)cnt : -1;
   if (bins) *bins = c->bins;
   if (pixels) *pixels = c->pixels;
+  return GS_OK;
+}
+
+gs_status gs_pair_stats(gs_ctx* c, int64_t* entries, int64_t* contributing) {
+  if (!c || !entries || !contributing) return GS_EINVAL;
+  if (!c->rastered) return fail(c, GS_ESTATE, "gs_pair_stats needs gs_raster_fwd first");
+  if (c->capturing) return fail(c, GS_ESTATE, "gs_pair_stats cannot be captured");
+  set_device(c);
+  GS_TRY(ensure(c, c->pair_stats, 2 * sizeof(unsigned long long)));
+  GS_CUDA(c, cudaMemsetAsync(c->pair_stats.p, 0, 2 * sizeof(unsigned long long), c->stream));
+  {
+    LaunchScope ls(c, "pair_stats");
+    launch_pair_stats(raster_args(c), c->bins, P<unsigned long long>(c->pair_stats), c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  GS_CUDA(c, cudaMemcpyAsync(c->pinned, c->pair_stats.p, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  *entries = (int64_t)c->pinned[0];
+  *contributing = (int64_t)c->pinned[1];
   return GS_OK;
 }
 

@@ -70,6 +70,9 @@ struct RasterArgs {
   float inv_count;
 };
 
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
+
 int project_fwd_block();
 void launch_project_fwd(const ProjectArgs& a, int deg, cudaStream_t s);
 void launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t s);
@@ -121,6 +124,8 @@ int64_t l1_finish_scratch_bytes();
 void launch_l1_finish(const float* partial, int64_t nparts, double* scratch, double inv_count, float* loss,
                       cudaStream_t s);
 void launch_raster_bwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s);
+// out[0] += list entries up to each pixel's last contributor, out[1] += contributing pairs
+void launch_pair_stats(const RasterArgs& a, int64_t bins, unsigned long long* out, cudaStream_t s);
 
 void launch_l1(const float* x, const float* y, const float* const* y_slot, int64_t count, float* partial,
                int nparts, float* loss, float* grad, cudaStream_t s);

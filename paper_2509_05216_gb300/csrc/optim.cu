@@ -11,10 +11,25 @@ namespace gs {
 
 constexpr int kL1Threads = 256;
 
+int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    (void)cudaGetLastError();
+    sms = 1;  // only sizes grids; any positive value is correct
+  }
+  if (dev >= 0 && dev < 64) cached[dev] = sms;
+  return sms;
+}
+
 int l1_parts(int64_t count) {
   int64_t parts = (count + kL1Threads * 16 - 1) / (kL1Threads * 16);
   if (parts < 1) parts = 1;
-  if (parts > 152 * 8) parts = 152 * 8;
+  const int64_t most = (int64_t)sm_count() * 8;
+  if (parts > most) parts = most;
   return (int)parts;
 }
 
@@ -94,7 +109,8 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
 void launch_adam(const AdamArgs& a, cudaStream_t s) {
   const int64_t n4 = (int64_t)a.planes * a.stride / 4;
   int64_t blocks = (n4 + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const int64_t most = (int64_t)sm_count() * 16;
+  if (blocks > most) blocks = most;
   if (blocks < 1) blocks = 1;
   adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
 }

@@ -862,6 +862,54 @@ void launch_l1_finish(const float* partial, int64_t nparts, double* scratch, dou
   l1_finish_tree_kernel<<<1, 256, 0, s>>>(scratch, inv_count, loss);
 }
 
+// Work counters of the last forward pass (inspection, outside the training
+// step): per pixel, the list entries up to and including its last
+// contributor (n_last: what the backward walks, and a lower bound of what
+// the forward walks) and, among them, the pairs that pass the power <= 0
+// and alpha >= 1/255 tests (the contributing pairs), evaluated with the
+// compositing kernels' own instruction sequence.  One block per tile, one
+// thread per pixel; out[0] += entries, out[1] += contributing pairs.
+__global__ void __launch_bounds__(256) pair_stats_kernel(RasterArgs a, unsigned long long* out) {
+  const int bin = (int)blockIdx.x;
+  const int v = view_of_bin(a.views, a.B, bin);
+  const ViewRec& V = a.views[v];
+  const int tile = bin - V.tile_offset;
+  const int px = (tile % V.gw) * kTile + (int)(threadIdx.x & 15);
+  const int py = (tile / V.gw) * kTile + (int)(threadIdx.x >> 4);
+  const uint2 rg = a.ranges[bin];
+  const uint32_t* __restrict__ vals = *a.vals;
+  uint32_t nl = 0;
+  if (px < V.W && py < V.H) nl = a.nlast[V.pix_offset + (int64_t)py * V.W + px];
+  nl = min(nl, rg.y - rg.x);
+  unsigned long long entries = nl, contrib = 0;
+  const float fpx = (float)px, fpy = (float)py;
+  for (uint32_t i = 0; i < nl; i++) {
+    float4 r0, r1, r2;
+    stage_one(a, v, vals[rg.x + i], r0, r1, r2);
+    const float dx = __fsub_rn(r0.x, fpx);
+    const float a0 = __fmul_rn(r0.z, __fmul_rn(dx, dx));
+    const float a1 = __fmul_rn(r0.w, dx);
+    const float p2 = splat_p2(r1.x, a1, a0, __fsub_rn(r0.y, fpy));
+    float G;
+    const float alpha = splat_alpha2(r1.y, p2, G);
+    contrib += (!(p2 > 0.f) && !(alpha < kAlphaSkip)) ? 1ull : 0ull;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    entries += __shfl_down_sync(0xffffffffu, entries, off);
+    contrib += __shfl_down_sync(0xffffffffu, contrib, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, entries);
+    atomicAdd(out + 1, contrib);
+  }
+}
+
+void launch_pair_stats(const RasterArgs& a, int64_t bins, unsigned long long* out, cudaStream_t s) {
+  if (bins == 0) return;
+  pair_stats_kernel<<<(unsigned)bins, 256, 0, s>>>(a, out);
+}
+
 void launch_raster_fwd(const RasterArgs& a, int64_t bins, int ppt, cudaStream_t s) {
   if (bins == 0) return;
   switch (ppt) {

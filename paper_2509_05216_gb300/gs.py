@@ -82,7 +82,7 @@ class gs_serve_cfg(ctypes.Structure):
 EXPORTS = ["gs_raster_fwd_l1", "gs_train_graph_capture", "gs_train_graph_launch", "gs_train_graph_launch_host", "gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
            "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
-           "gs_get_counts"]
+           "gs_get_counts", "gs_pair_stats"]
 
 
 def load(path: str | None = None):
@@ -127,6 +127,7 @@ def load(path: str | None = None):
     L.gs_profile_enable.argtypes = [vp, i32]
     L.gs_profile_read.argtypes = [vp, P(gs_kernel_stat), i32, P(i32)]
     L.gs_profile_reset.argtypes = [vp]
+    L.gs_pair_stats.argtypes = [vp, P(i64), P(i64)]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int:
@@ -314,6 +315,14 @@ class Context:
         self._check(self.L.gs_get_counts(self.h, ctypes.byref(i), ctypes.byref(b), ctypes.byref(p)),
                     "gs_get_counts")
         return i.value, b.value, p.value
+
+    def gs_pair_stats(self):
+        """(list entries up to each pixel's last contributor, contributing
+        pairs) of the last forward pass."""
+        self._bind_stream()
+        e, c = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.L.gs_pair_stats(self.h, ctypes.byref(e), ctypes.byref(c)), "gs_pair_stats")
+        return e.value, c.value
 
     def gs_get_buffer(self, which: int) -> torch.Tensor:
         """Copy of an intermediate buffer as a torch tensor."""

@@ -29,6 +29,27 @@ def mixed_cams():
             inputs.pinhole(inputs.look_at((-1.5, 2.0, 1.9)), 97, 131, bg=(0.2, 0.4, 0.1))]
 
 
+def stack_scene():
+    """40 near-isotropic Gaussians stacked along the view axis of the axis
+    camera (same screen centre, increasing depth), each with alpha >= 0.6 on
+    the centre pixels: without the transmittance stop all 40 would
+    contribute there; with it T falls below 1e-4 after about eight."""
+    rng = np.random.default_rng(31)
+    k = 40
+    means = np.stack([rng.uniform(-0.02, 0.02, k), rng.uniform(-0.02, 0.02, k), np.linspace(-0.5, 0.5, k)], 1)
+    ls = np.full((k, 3), -1.6) + rng.uniform(-0.1, 0.1, (k, 3))
+    q = np.tile([1.0, 0.0, 0.0, 0.0], (k, 1)) + rng.normal(0.0, 0.1, (k, 4))
+    o = rng.uniform(0.8, 1.4, k)
+    sh = np.zeros((k, 4, 3))
+    sh[:, 0, :] = rng.uniform(-1.0, 1.5, (k, 3))
+    sh[:, 1:, :] = rng.normal(0.0, 0.3, (k, 3, 3))
+    return inputs.pack_params(means, ls, q, o, sh)
+
+
+def stack_camera():
+    return inputs.pinhole(inputs.look_at((0.0, 0.0, 3.0), up=(0.0, 1.0, 0.0)), 64, 48, bg=(0.2, 0.2, 0.5))
+
+
 SCENES = {
     "sphere_c1": lambda: (inputs.sphere_scene(), [inputs.sphere_camera()]),
     "random_deg3_mixed": lambda: (inputs.random_scene(20000, 3, 11, extent=0.8), mixed_cams()),
@@ -38,7 +59,57 @@ SCENES = {
     # is tested where the ellipse and its bounding box differ most
     "needles_deg0": lambda: (inputs.random_scene(4000, 0, 13, extent=0.7, log_scale=(-6.0, -1.5)),
                              [inputs.pinhole(inputs.look_at((1.9, -1.6, 1.3)), 192, 160)]),
+    # opacity logits 5..8 (opacity 0.9933..0.9997): the 0.99 alpha clamp
+    # holds on thousands of (pixel, Gaussian) pairs, and its zero gradient
+    # is taken in the backward
+    "opaque_deg2": lambda: (inputs.random_scene(3000, 2, 21, extent=0.7, log_scale=(-2.6, -1.6), opacity=(5.0, 8.0)),
+                            [inputs.pinhole(inputs.look_at((1.2, -2.2, 1.0)), 160, 128, bg=(0.1, 0.3, 0.2))]),
+    # Gaussians far outside the field of view whose splats still reach the
+    # image: the slope clamp of J (1.3 half fields of view) is taken by
+    # hundreds of visible Gaussians, with its zero derivative
+    "guard_band_deg1": lambda: (inputs.random_scene(3000, 1, 22, extent=1.6, log_scale=(-2.0, -0.8),
+                                                    opacity=(-1.0, 2.0)),
+                                [inputs.pinhole(inputs.look_at((0.3, -2.2, 0.4)), 144, 112)]),
+    "stack_deg1": lambda: (stack_scene(), [stack_camera()]),
 }
+
+
+def clamped_alpha_pairs(oracle, scene, cam):
+    """(pixel, Gaussian) pairs near each visible mean with opacity G > 0.99."""
+    pr = oracle.project(scene, cam)
+    count = 0
+    for g in np.nonzero((pr["flags"] & oracle.G_VISIBLE) != 0)[0]:
+        mx, my = pr["mean2d"][g]
+        A, B, C = pr["conic"][g]
+        X, Y = np.meshgrid(np.arange(int(mx) - 6, int(mx) + 7), np.arange(int(my) - 6, int(my) + 7))
+        inside = (X >= 0) & (X < cam["width"]) & (Y >= 0) & (Y < cam["height"])
+        dx, dy = X - mx, Y - my
+        G = np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)
+        count += int(((pr["opacity"][g] * G > 0.99) & inside).sum())
+    return count
+
+
+def slope_clamped_visible(oracle, scene, cam):
+    """Visible Gaussians whose image-plane slope lies beyond the guard band
+    (and not at its edge)."""
+    pr = oracle.project(scene, cam)
+    P = scene["params"].astype(np.float64)
+    n = scene["n"]
+    V = np.asarray(cam["viewmat"], np.float64).reshape(4, 4)
+    t = V[:3, :3] @ P[0:3, :n] + V[:3, 3:4]
+    limx = 1.3 * cam["width"] / (2.0 * cam["fx"])
+    limy = 1.3 * cam["height"] / (2.0 * cam["fy"])
+    clamped = (np.abs(t[0] / t[2]) > limx) | (np.abs(t[1] / t[2]) > limy)
+    ok = ((pr["flags"] & oracle.G_VISIBLE) != 0) & ((pr["flags"] & oracle.G_MARG_GUARD) == 0)
+    return int((clamped & ok).sum())
+
+
+def test_edge_case_scenes_reach_their_branches(oracle):
+    """The edge-case scenes do take the branches they are there for."""
+    sc, cams = SCENES["opaque_deg2"]()
+    assert clamped_alpha_pairs(oracle, sc, cams[0]) > 1000
+    sc, cams = SCENES["guard_band_deg1"]()
+    assert slope_clamped_visible(oracle, sc, cams[0]) > 200
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -208,7 +279,11 @@ def test_gradient_matches_oracle(ctx, oracle, name, fwd, bwd):
     g = grads.cpu().numpy().astype(np.float64)
     assert rel_l2(g[:, :n][:, keep], ref[:, :n][:, keep]) <= 1e-3
     # per-plane check of the larger groups, so no group hides behind another
-    for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14)]:
+    # (SH bands 1, 2, 3 each on their own: planes 14-22, 23-37, 38-58)
+    P = ref.shape[0]
+    for lo, hi in [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14), (14, 23), (23, 38), (38, 59)]:
+        if hi > P:
+            continue
         r = ref[lo:hi, :n][:, keep]
         if np.linalg.norm(r) > 0:
             assert rel_l2(g[lo:hi, :n][:, keep], r) <= 1e-3, (lo, hi)
@@ -216,6 +291,65 @@ def test_gradient_matches_oracle(ctx, oracle, name, fwd, bwd):
     for v in range(len(cams)):
         got = g2d[v * stride: v * stride + n][keep]
         assert rel_l2(got, ref2d[v][keep]) <= 1e-3
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_transmittance_stop_fires_on_dense_stack(ctx, oracle, variant):
+    """On the centre pixels of the stack every one of the 40 Gaussians has
+    alpha >= 0.6, so without the stop all 40 would contribute (n_last = 40);
+    with it the last contributor comes far earlier, T_final stays >= 1e-4,
+    and one more layer would take it below 1e-4."""
+    scene, cams = SCENES["stack_deg1"]()
+    cam = cams[0]
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, variant)
+    run_forward(ctx, scene, cams)
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, 2)
+    nl = ctx.gs_get_buffer(gs.GS_BUF_NLAST).cpu().numpy().reshape(cam["height"], cam["width"])
+    tf = ctx.gs_get_buffer(gs.GS_BUF_TFINAL).cpu().numpy().reshape(cam["height"], cam["width"])
+    ranges = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
+    vals = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64)
+    pr = oracle.project(scene, cam)
+    A, B, C = pr["conic"].T
+    gw = (cam["width"] + 15) // 16
+    cx, cy = int(round(cam["cx"])), int(round(cam["cy"]))
+    checked = 0
+    for y in range(cy - 1, cy + 2):
+        for x in range(cx - 1, cx + 2):
+            dx, dy = x - pr["mean2d"][:, 0], y - pr["mean2d"][:, 1]
+            alpha = pr["opacity"] * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)
+            if alpha.min() < 0.6:
+                continue
+            t = (y // 16) * gw + (x // 16)
+            length = ranges[t, 1] - ranges[t, 0]
+            assert length == 40
+            assert 1 <= nl[y, x] <= 20 < length
+            # the entry right after the last contributor is the one the stop excluded
+            nxt = vals[ranges[t, 0] + nl[y, x]]
+            assert tf[y, x] >= np.float32(1e-4)
+            assert tf[y, x] * (1.0 - alpha[nxt]) < 1e-4 * (1.0 + 1e-3)
+            checked += 1
+    assert checked >= 4
+
+
+def test_pair_stats_count_entries_and_contributions(ctx, oracle):
+    """gs_pair_stats: the entries equal the sum of n_last exactly; the
+    contributing pairs equal the oracle's count of (pixel, Gaussian)
+    contributions up to the pixels where FP32 and FP64 may decide a
+    threshold differently."""
+    scene, cams = SCENES["random_deg3_mixed"]()
+    run_forward(ctx, scene, cams)
+    entries, contrib = ctx.gs_pair_stats()
+    nl = ctx.gs_get_buffer(gs.GS_BUF_NLAST).cpu().numpy().astype(np.int64)
+    assert entries == int(nl.sum())
+    ref, marginal = 0, 0
+    for cam in cams:
+        _, _, marg, pairs = oracle.render(scene, cam)
+        ref += pairs
+        marginal += int(marg.sum())
+    assert 0 < contrib <= entries
+    # a marginal pixel can differ by a few contributions
+    assert abs(contrib - ref) <= 4 * marginal + 1, (contrib, ref, marginal)
+    assert abs(contrib - ref) <= 1e-3 * ref
 
 
 def test_raster_variants_agree(ctx, oracle):

@@ -113,23 +113,15 @@ def test_autotuner_keeps_the_fastest_value_of_each_option_and_caches(tmp_path, m
     assert calls == [] and ctx2.options == {1: 8, 2: 2}
 
 
-def test_recorded_traffic_is_used_only_for_the_profiled_source(tmp_path, monkeypatch):
-    src = tmp_path / "paper_2509_05216_gb300" / "csrc"
-    src.mkdir(parents=True)
-    (src / "raster.cu").write_text("// kernel source\n")
-    sha = hashlib.sha1(b"// kernel source\n").hexdigest()
-    prof = tmp_path / "profiles"
-    prof.mkdir()
-    table = ("| kernel: DRAM bytes per launch | read | write |\n|---|---|---|\n"
-             "| raster_bwd_kernel<2>: 6.5e+09 bytes per launch | read 5.3e+09 | write 1.2e+09 |\n")
-    summary = prof / "raster_traffic_blobs4M_2048sq_B16.md"
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    summary.write_text("raster.cu sha1 %s\n\n%s" % (sha, table))
-    assert bench.recorded_traffic("raster_bwd", 2) == 6.5e9
-    assert bench.recorded_traffic("raster_fwd", 2) is None
-    # another version of the kernel source: no recorded traffic
-    summary.write_text("raster.cu sha1 %s\n\n%s" % ("0" * 40, table))
-    assert bench.recorded_traffic("raster_bwd", 2) is None
+def test_compositing_work_counts_contributing_pairs_at_full_cost():
+    """The compositing roofline charges the full per-pair arithmetic only to
+    contributing pairs and the alpha test to the other walked entries."""
+    assert bench.raster_work("bwd", 100, 30) == bench.RASTER_OPS_BWD * 30 + bench.RASTER_OPS_TEST * 70
+    assert bench.raster_work("fwd", 100, 30) == bench.RASTER_OPS_FWD * 30 + bench.RASTER_OPS_TEST * 70
+    assert bench.raster_work("bwd", 50, 50) == bench.RASTER_OPS_BWD * 50
+    kind, work = bench.algorithmic_work("raster_bwd", 10, 59, 2, 100, (1000, 200), 64)
+    assert kind == "alu" and work == bench.raster_work("bwd", 1000, 200)
+    assert bench.RASTER_OPS_TEST < bench.RASTER_OPS_FWD < bench.RASTER_OPS_BWD
 
 
 def test_cpu_binning_reference_equals_brute_force():
