@@ -118,7 +118,14 @@ const char* gs_last_error(const gs_ctx* ctx);
 gs_status gs_set_stream(gs_ctx* ctx, void* stream);
 
 /* Wait for the context's stream; return the device status word (GS_OK,
- * GS_ECAPACITY or GS_ETIMEOUT) and clear it. */
+ * GS_ECAPACITY or GS_ETIMEOUT) and clear it.  After GS_ETIMEOUT or
+ * GS_ECAPACITY the sorted keys, values and ranges of the batches since the
+ * previous gs_sync, and everything computed from them (images, T_final,
+ * gradients, an Adam step taken on those gradients), are undefined; every
+ * kernel stays within its buffers on such data, and the next sort that
+ * completes is correct again.  A sort partition that gives up its bounded
+ * look-back marks itself failed, and every later partition of the same pass
+ * gives up on seeing that mark instead of scattering with a partial offset. */
 gs_status gs_sync(gs_ctx* ctx);
 
 /* Tunable options of a context (the autotuner sets these). */
@@ -291,24 +298,41 @@ gs_status gs_train_graph_launch_host(gs_ctx* ctx, const gs_camera* cams, int32_t
  * any resolution are batched continuously (the paper's goal is interactive
  * visualisation of the trained model, Sections I and V).  A worker thread
  * forms a batch from the oldest pending requests whenever a slot is free and
- * the batch's memory estimate (per-view workspace + output) fits the budget,
- * and renders it (projection, binning, forward compositing) on the slot's own
+ * renders it (projection, binning, forward compositing) on the slot's own
  * context and stream, so batches overlap on the device.  Each result is the
- * same whether rendered alone or in a mix. */
+ * same whether rendered alone or in a mix.
+ *
+ * Memory: at creation every slot reserves, once, the workspaces of its
+ * largest batch -- max_batch_views views of max_view_pixels, i.e. per view 72
+ * bytes per resident Gaussian (stride), 20 bytes per pixel and 8 bytes per
+ * 16x16 tile (max_view_pixels / 128 + 64 tiles) -- and the rest of its share
+ * of the budget (memory_budget_bytes / slots, less 1 MiB) as room for tile
+ * instances at 26 bytes each (at most 2^30 - 2).  Nothing is allocated or
+ * waited for while batches are launched.  A batch is admitted into a slot by
+ * that room: each request is charged an instance estimate (1.25 x the most a
+ * view of its pixel count has needed so far; for a size not seen yet, two
+ * per resident Gaussian plus four per pixel), and a batch takes the oldest
+ * pending requests while their estimates fit.  A batch whose instances
+ * exceed its estimate is rendered again (its requests go back to the front
+ * of the queue; the estimates have learnt the true counts); a request that
+ * alone overflows the whole room, or overflows 5 times, completes with
+ * GS_ECAPACITY.  A bounded device wait that runs out completes the batch's
+ * requests with GS_ETIMEOUT. */
 typedef struct gs_server gs_server;
 
 typedef struct {
   int32_t slots;               /* batches in flight, 1..16 (default 2) */
   int32_t max_batch_views;     /* views per batch, 1..64 (default 16) */
   int32_t max_queue;           /* pending requests before GS_EBUSY (default 4096) */
-  int32_t reserved;
-  int64_t memory_budget_bytes; /* estimate of running batches (default 16 GiB) */
+  int32_t max_view_pixels;     /* largest width x height of a request (default 3840 x 2160) */
+  int64_t memory_budget_bytes; /* reservation of all slots (default 16 GiB); see above */
   int64_t output_pool_bytes;   /* server-owned output pool; 0 = callers pass outputs */
 } gs_serve_cfg;
 
 /* Start a server on `device` for the resident set (device memory owned by
  * the caller, unchanged while the server lives).  cfg may be NULL.
- * Errors: GS_EINVAL, GS_ENOMEM, GS_ECUDA. */
+ * Errors: GS_EINVAL (bad cfg, or a budget that leaves a slot room for fewer
+ * than 65,536 instances), GS_ENOMEM, GS_ECUDA. */
 gs_status gs_serve_create(gs_server** out, int device, const gs_params* resident, const gs_serve_cfg* cfg);
 
 /* Stop the worker, wait for running batches and free the server. */
@@ -317,8 +341,9 @@ void gs_serve_destroy(gs_server* srv);
 /* Queue one camera.  out_device: device buffer of 3*W*H floats (planar RGB)
  * that receives the image, or NULL to use the server's output pool (then
  * gs_serve_release frees the region).  *ticket identifies the request.
- * Errors: GS_EINVAL (bad camera, NULL output without a pool), GS_EBUSY
- * (queue full, output pool full, or the request alone exceeds the budget). */
+ * Errors: GS_EINVAL (bad camera, W*H above max_view_pixels or more tiles
+ * than max_view_pixels / 128 + 64, NULL output without a pool), GS_EBUSY
+ * (queue full or output pool full). */
 gs_status gs_serve_submit(gs_server* srv, const gs_camera* cam, float* out_device, uint64_t* ticket);
 
 /* Wait up to timeout_us (0 = do not wait, negative = no limit) for a request.  On completion
@@ -331,8 +356,18 @@ gs_status gs_serve_poll(gs_server* srv, uint64_t ticket, int64_t timeout_us, con
  * still pending or running. */
 gs_status gs_serve_release(gs_server* srv, uint64_t ticket);
 
-/* Counters: batches launched, views rendered, requests pending. */
+/* Counters: batches launched (re-renders after a capacity overflow
+ * included), requests completed with GS_OK, requests pending. */
 gs_status gs_serve_stats(gs_server* srv, int64_t* batches, int64_t* rendered, int64_t* pending);
+
+/* Device timeline of the most recent retired batches (up to 4096 kept):
+ * start_end_ms (host, 2 x cap doubles) receives, oldest first, each batch's
+ * start and end in milliseconds since the server was created (CUDA events on
+ * the slots' streams, so intervals of different slots are comparable and
+ * overlap when their batches ran at the same time); *count = pairs written;
+ * *retried (may be NULL) = batches rendered again after a capacity overflow.
+ * Errors: GS_EINVAL. */
+gs_status gs_serve_timeline(gs_server* srv, double* start_end_ms, int32_t cap, int32_t* count, int64_t* retried);
 
 /* ---------------------------------------------------------------- inspection */
 

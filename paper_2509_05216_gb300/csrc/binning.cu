@@ -190,6 +190,10 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kFlagAggregate = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
+// a partition that gave up its look-back publishes this instead of a prefix,
+// so that the partitions after it give up too instead of scattering with a
+// wrong offset
+constexpr uint32_t kFlagFailed = 3u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
 constexpr int kLookWindow = 16;       // statuses read per look-back round
 
@@ -407,11 +411,12 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   uint32_t excl = 0;
   if (lp0 > 0 && a.wait_rounds <= 0) {
     sm.timed_out = 1;  // give up without looking (exercises the timeout path)
+    lb[(int64_t)part * kRadix + d] = kFlagFailed;
   } else if (lp0 > 0) {
     const int64_t first = (int64_t)sm.first_part;
     int64_t j = (int64_t)part - 1;
     int rounds = 0;
-    bool found = false;
+    bool found = false, failed = false;
     while (!found) {
       uint32_t w[kLookWindow];
 #pragma unroll
@@ -427,17 +432,22 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
           stalled = true;
           continue;
         }
+        if (flag == kFlagFailed) {  // an earlier partition gave up: so does this one
+          failed = found = true;
+          continue;
+        }
         excl += w[t] & kValueMask;
         used++;
         if (flag == kFlagPrefix) found = true;
       }
       j -= used;
       if (!found && ++rounds > a.wait_rounds) {
-        sm.timed_out = 1;
+        failed = true;
         break;
       }
     }
-    lb[(int64_t)part * kRadix + d] = kFlagPrefix | ((excl + tile_count) & kValueMask);
+    if (failed) sm.timed_out = 1;
+    lb[(int64_t)part * kRadix + d] = failed ? kFlagFailed : (kFlagPrefix | ((excl + tile_count) & kValueMask));
   }
   sm.global_base[d] = sm.seg_lo + hist_pass[d] + excl;
   __syncthreads();

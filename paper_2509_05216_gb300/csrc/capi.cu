@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/gs.h: context, workspaces,
 // argument checks and the launch sequence of each step.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -8,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "ctx_internal.h"
 #include "gs_internal.cuh"
 #include "launch.h"
 
@@ -61,6 +63,7 @@ struct gs_ctx {
   int sort_passes = 0;  // LSD passes of the last sort
   int sort_items = 16;  // keys per thread of a sort partition
   int sort_wait = 1 << 20;  // look-back rounds before a sort gives up
+  int64_t batch_cap = 0;    // instance capacity of the next sorts (0: cfg.instance_capacity)
 
   // last batch
   int B = 0, deg = 0;
@@ -118,10 +121,10 @@ gs_status fail(gs_ctx* c, gs_status st, const char* fmt, ...) {
                   __LINE__);                                                                    \
   } while (0)
 
-gs_status ensure(gs_ctx* c, DevBuf& b, size_t bytes) {
+gs_status ensure(gs_ctx* c, DevBuf& b, size_t bytes, bool exact = false) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return GS_OK;
-  size_t want = bytes + bytes / 8;
+  size_t want = exact ? bytes : bytes + bytes / 8;
   if (b.p) {
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     GS_CUDA(c, cudaFree(b.p));
@@ -266,6 +269,59 @@ void adam_constants(const gs_adam_hp* hp, int planes, int64_t step, int B, float
 }
 
 }  // namespace
+
+namespace gs {
+
+gs_status ctx_reserve(gs_ctx* c, int64_t stride, int B, int64_t bins, int64_t pixels, int64_t view_tiles) {
+  if (!c || stride <= 0 || B < 1 || B > kMaxViews || bins < 1 || pixels < 1 || view_tiles < 1)
+    return GS_EINVAL;
+  if (c->cfg.instance_capacity <= 0) return fail(c, GS_EINVAL, "ctx_reserve needs a fixed instance capacity");
+  set_device(c);
+  auto ensure_exact = [](gs_ctx* cc, DevBuf& b, size_t bytes) { return ensure(cc, b, bytes, true); };
+  const int64_t cap = c->cfg.instance_capacity;
+  const int64_t nb = (stride + project_fwd_block() - 1) / project_fwd_block();
+  int tile_bits = 0;
+  while (((int64_t)1 << tile_bits) < view_tiles) tile_bits++;
+  const int npass = (32 + tile_bits + 7) / 8;
+  GS_TRY(ensure_exact(c, c->views, sizeof(ViewRec) * B));
+  GS_TRY(ensure_exact(c, c->rec, sizeof(float4) * kRecStride * B * stride));
+  GS_TRY(ensure_exact(c, c->rec3, sizeof(int4) * B * stride));
+  GS_TRY(ensure_exact(c, c->tiles, sizeof(uint2) * B * stride));
+  GS_TRY(ensure_exact(c, c->block_sums, sizeof(uint32_t) * B * nb));
+  GS_TRY(ensure_exact(c, c->block_offsets, sizeof(uint32_t) * B * nb));
+  GS_TRY(ensure_exact(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
+                                 sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
+  GS_TRY(ensure_exact(c, c->keys0, sizeof(uint64_t) * cap));
+  GS_TRY(ensure_exact(c, c->keys1, sizeof(uint64_t) * cap));
+  GS_TRY(ensure_exact(c, c->vals0, sizeof(uint32_t) * cap));
+  GS_TRY(ensure_exact(c, c->vals1, sizeof(uint32_t) * cap));
+  GS_TRY(ensure_exact(c, c->ranges, sizeof(uint2) * bins));
+  GS_TRY(ensure_exact(c, c->hist, sizeof(uint32_t) * (size_t)B * 8 * 256));
+  GS_TRY(ensure_exact(c, c->hist_scan, sizeof(uint32_t) * (size_t)B * 8 * 256));
+  GS_TRY(ensure_exact(c, c->lookback, sort_lookback_bytes(cap, c->sort_items, B) * npass));
+  GS_TRY(ensure_exact(c, c->counters, sizeof(uint32_t) * 8));
+  GS_TRY(ensure_exact(c, c->sorted_slots, 2 * sizeof(void*)));
+  GS_TRY(ensure_exact(c, c->tfinal, sizeof(float) * pixels));
+  GS_TRY(ensure_exact(c, c->nlast, sizeof(uint32_t) * pixels));
+  return GS_OK;
+}
+
+void ctx_set_batch_capacity(gs_ctx* c, int64_t cap) {
+  if (c) c->batch_cap = cap > 0 ? cap : 0;
+}
+
+gs_status ctx_read_status_async(gs_ctx* c, int* status_host, uint64_t* view_totals_host, int B) {
+  if (!c || !status_host || !view_totals_host || B < 1 || B > kMaxViews) return GS_EINVAL;
+  if (!c->sorted) return fail(c, GS_ESTATE, "no sort to read");
+  set_device(c);
+  GS_CUDA(c, cudaMemcpyAsync(status_host, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
+  GS_CUDA(c, cudaMemcpyAsync(view_totals_host, P<uint64_t>(c->total) + 1, sizeof(uint64_t) * B,
+                             cudaMemcpyDeviceToHost, c->stream));
+  return GS_OK;
+}
+
+}  // namespace gs
 
 extern "C" {
 
@@ -432,7 +488,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   // sequence can be captured in a CUDA graph; overflow -> GS_ECAPACITY)
   int64_t cap;
   if (c->cfg.instance_capacity > 0) {
-    cap = c->cfg.instance_capacity;
+    cap = c->batch_cap > 0 ? std::min(c->batch_cap, c->cfg.instance_capacity) : c->cfg.instance_capacity;
     c->instances = -1;
   } else {
     GS_CUDA(c, cudaMemcpyAsync(c->pinned, c->total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));

@@ -75,14 +75,14 @@ GS_OPT_RASTER_FWD, GS_OPT_RASTER_BWD, GS_OPT_BWD_DIRECT, GS_OPT_SORT_ITEMS, GS_O
 
 class gs_serve_cfg(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch_views", ctypes.c_int32), ("max_queue", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("memory_budget_bytes", ctypes.c_int64),
+                ("max_view_pixels", ctypes.c_int32), ("memory_budget_bytes", ctypes.c_int64),
                 ("output_pool_bytes", ctypes.c_int64)]
 
 
 EXPORTS = ["gs_raster_fwd_l1", "gs_train_graph_capture", "gs_train_graph_launch", "gs_train_graph_launch_host", "gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
            "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
-           "gs_get_counts", "gs_pair_stats"]
+           "gs_get_counts", "gs_pair_stats", "gs_serve_timeline"]
 
 
 def load(path: str | None = None):
@@ -128,6 +128,7 @@ def load(path: str | None = None):
     L.gs_profile_read.argtypes = [vp, P(gs_kernel_stat), i32, P(i32)]
     L.gs_profile_reset.argtypes = [vp]
     L.gs_pair_stats.argtypes = [vp, P(i64), P(i64)]
+    L.gs_serve_timeline.argtypes = [vp, P(ctypes.c_double), i32, P(i32), P(i64)]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int:
@@ -364,12 +365,13 @@ class Server:
 
     def __init__(self, params: torch.Tensor, n: int, deg: int, device: int = 0, slots: int = 2,
                  max_batch_views: int = 16, max_queue: int = 4096, memory_budget_bytes: int = 16 << 30,
-                 output_pool_bytes: int = 1 << 30):
+                 output_pool_bytes: int = 1 << 30, max_view_pixels: int = 0):
         self.L = load()
         self.params = params  # keep alive
         self.device = device
         p = params_struct(params, n, deg)
-        cfg = gs_serve_cfg(slots, max_batch_views, max_queue, 0, memory_budget_bytes, output_pool_bytes)
+        cfg = gs_serve_cfg(slots, max_batch_views, max_queue, max_view_pixels, memory_budget_bytes,
+                           output_pool_bytes)
         h = ctypes.c_void_p()
         st = self.L.gs_serve_create(ctypes.byref(h), device, ctypes.byref(p), ctypes.byref(cfg))
         if st != GS_OK:
@@ -417,6 +419,17 @@ class Server:
         self._shape.pop(ticket, None)
         if st != GS_OK:
             raise GsError(st, "gs_serve_release(%d)" % ticket)
+
+    def gs_serve_timeline(self, cap: int = 4096):
+        """((start_ms, end_ms) of the most recent retired batches on the
+        device timeline, oldest first; batches rendered again after a
+        capacity overflow)."""
+        buf = (ctypes.c_double * (2 * cap))()
+        cnt, retried = ctypes.c_int32(), ctypes.c_int64()
+        st = self.L.gs_serve_timeline(self.h, buf, cap, ctypes.byref(cnt), ctypes.byref(retried))
+        if st != GS_OK:
+            raise GsError(st, "gs_serve_timeline")
+        return [(buf[2 * i], buf[2 * i + 1]) for i in range(cnt.value)], retried.value
 
     def gs_serve_stats(self):
         b, r, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
