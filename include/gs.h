@@ -186,8 +186,9 @@ gs_status gs_bin_sort(gs_ctx* ctx);
  * alpha = min(0.99, opacity * exp(power)), skip if power > 0 or
  * alpha < 1/255, stop before a Gaussian that would bring T below 1e-4,
  * C += rgb alpha T, T *= 1 - alpha; output C + T bg.  images: device,
- * [B][3][H][W] as above.  Also keeps T_final and the index of the last
- * contributor per pixel for the backward pass.
+ * [B][3][H][W] as above.  Also keeps, for the backward pass, T_final and the
+ * index of the last contributor per pixel, and per tile instance (4 bytes)
+ * the 2x4-pixel cells of its tile where it contributed to some pixel.
  * Errors: GS_ESTATE (no gs_bin_sort), GS_EINVAL (images NULL), GS_ECUDA. */
 gs_status gs_raster_fwd(gs_ctx* ctx, float* images);
 
@@ -202,9 +203,10 @@ gs_status gs_raster_fwd(gs_ctx* ctx, float* images);
  * dL_dimages), GS_ECUDA. */
 gs_status gs_raster_fwd_l1(gs_ctx* ctx, float* images, const float* targets, float* loss, float* dL_dimages);
 
-/* Step 4, backward.  Given dL/dimages (device, image layout), walks every
- * tile list in reverse from each pixel's last contributor, recovering T by
- * division, and writes dL/dparams into grads->data (device, overwritten;
+/* Step 4, backward.  Given dL/dimages (device, image layout), walks each
+ * pixel's tile list in reverse from its last contributor -- only the entries
+ * the forward pass recorded as contributing to the pixel's 2x4-pixel cell --
+ * recovering T by division, and writes dL/dparams into grads->data (device, overwritten;
  * same n, stride and degree as params).  The derivative is the exact one of
  * step 3 where it exists: zero through a clamped alpha (opacity * G > 0.99),
  * the slope clamp and the colour clamp.  params must be the set given to

@@ -64,6 +64,8 @@ struct gs_ctx {
   int sort_items = 16;  // keys per thread of a sort partition
   int sort_wait = 1 << 20;  // look-back rounds before a sort gives up
   int64_t batch_cap = 0;    // instance capacity of the next sorts (0: cfg.instance_capacity)
+  bool forward_only = false;  // no contribution cells: gs_raster_bwd unavailable (render server)
+  bool cells_ready = false;   // the last forward recorded contribution cells
 
   // last batch
   int B = 0, deg = 0;
@@ -73,7 +75,7 @@ struct gs_ctx {
 
   DevBuf views, rec, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
-      target_slot, host_tgt0, host_tgt1, pair_stats;
+      target_slot, host_tgt0, host_tgt1, pair_stats, cells;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -310,6 +312,10 @@ void ctx_set_batch_capacity(gs_ctx* c, int64_t cap) {
   if (c) c->batch_cap = cap > 0 ? cap : 0;
 }
 
+void ctx_set_forward_only(gs_ctx* c, bool on) {
+  if (c) c->forward_only = on;
+}
+
 gs_status ctx_read_status_async(gs_ctx* c, int* status_host, uint64_t* view_totals_host, int B) {
   if (!c || !status_host || !view_totals_host || B < 1 || B > kMaxViews) return GS_EINVAL;
   if (!c->sorted) return fail(c, GS_ESTATE, "no sort to read");
@@ -364,7 +370,7 @@ void gs_destroy(gs_ctx* c) {
                     &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->hist_scan,
                     &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
                     &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1,
-                    &c->pair_stats};
+                    &c->pair_stats, &c->cells};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -416,7 +422,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   if (!cams) return fail(c, GS_EINVAL, "cams is NULL");
   if (B < 1 || B > c->cfg.max_views) return fail(c, GS_EINVAL, "B must be in 1..%d", c->cfg.max_views);
   set_device(c);
-  c->projected = c->sorted = c->rastered = false;
+  c->projected = c->sorted = c->rastered = c->cells_ready = false;
   int64_t tile_off = 0, pix_off = 0;
   GS_TRY(build_views(c, cams, B, &tile_off, &pix_off));
   if (tile_off >= ((int64_t)1 << 31)) return fail(c, GS_EINVAL, "too many tiles in the batch");
@@ -465,7 +471,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   if (!c) return GS_EINVAL;
   if (!c->projected) return fail(c, GS_ESTATE, "gs_bin_sort needs gs_project first");
   set_device(c);
-  c->sorted = c->rastered = false;
+  c->sorted = c->rastered = c->cells_ready = false;
   const int B = c->B;
   GS_TRY(ensure(c, c->block_offsets, sizeof(uint32_t) * B * c->nblocks));
   // device words: total (u64) | view totals (u64 x 64) | seg (u32 x 65) | part_off (u32 x 65) | ctrl (u32 x 16)
@@ -516,6 +522,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   GS_TRY(ensure(c, c->lookback, lb * npass));
   GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
   GS_TRY(ensure(c, c->sorted_slots, 2 * sizeof(void*)));
+  if (!c->forward_only) GS_TRY(ensure(c, c->cells, sizeof(uint32_t) * cap));
 
   DuplicateArgs d{};
   d.n = c->n;
@@ -560,6 +567,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   sa.status = c->status_d;
   sa.sorted_keys = reinterpret_cast<const uint64_t**>(c->sorted_slots.p);
   sa.sorted_vals = reinterpret_cast<const uint32_t**>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
+  sa.cells = c->forward_only ? nullptr : P<uint32_t>(c->cells);
   GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * (size_t)B * npass * 256, c->stream));
   GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * 8, c->stream));
   GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * npass, c->stream));
@@ -596,6 +604,7 @@ static RasterArgs raster_args(gs_ctx* c) {
   r.rec2 = P<float4>(c->rec) + 2;
   r.tfinal = P<float>(c->tfinal);
   r.nlast = P<uint32_t>(c->nlast);
+  r.cells = c->forward_only ? nullptr : P<uint32_t>(c->cells);
   return r;
 }
 
@@ -614,6 +623,7 @@ gs_status gs_raster_fwd(gs_ctx* c, float* images) {
   }
   GS_CHECK_LAUNCH(c);
   c->rastered = true;
+  c->cells_ready = !c->forward_only;
   return GS_OK;
 }
 
@@ -649,12 +659,14 @@ gs_status gs_raster_fwd_l1(gs_ctx* c, float* images, const float* targets, float
   }
   GS_CHECK_LAUNCH(c);
   c->rastered = true;
+  c->cells_ready = !c->forward_only;
   return GS_OK;
 }
 
 gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dimages, gs_params* grads) {
   if (!c) return GS_EINVAL;
   if (!c->rastered) return fail(c, GS_ESTATE, "gs_raster_bwd needs gs_raster_fwd first");
+  if (!c->cells_ready) return fail(c, GS_ESTATE, "the last forward pass of this context is forward-only");
   GS_TRY(check_params(c, params, "params"));
   GS_TRY(check_params(c, grads, "grads"));
   if (!dL_dimages) return fail(c, GS_EINVAL, "dL_dimages is NULL");
@@ -959,6 +971,7 @@ gs_status gs_train_graph_launch(gs_ctx* c, const gs_camera* cams, int32_t B, con
     GS_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
   }
   c->projected = c->sorted = c->rastered = true;
+  c->cells_ready = !c->forward_only;
   return GS_OK;
 }
 

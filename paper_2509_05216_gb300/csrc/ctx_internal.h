@@ -21,6 +21,11 @@ gs_status ctx_reserve(gs_ctx* c, int64_t stride, int B, int64_t bins, int64_t pi
 // grid; more instances than this set GS_ECAPACITY in the status word.
 void ctx_set_batch_capacity(gs_ctx* c, int64_t cap);
 
+// Forward-only context (render server): the forward pass records no
+// contribution cells (no per-instance buffer, no zeroing) and gs_raster_bwd
+// returns GS_ESTATE.
+void ctx_set_forward_only(gs_ctx* c, bool on);
+
 // Enqueue on the context's stream: copy the status word and the per-view
 // instance counts of the last sort (B of them) into host memory (page-locked
 // for an asynchronous copy), then clear the status word.

@@ -57,6 +57,11 @@ struct RasterArgs {
   float* image;         // [B][3][H][W] concatenated (forward: may be NULL when fused with the L1 loss)
   float* tfinal;        // [pixels]
   uint32_t* nlast;      // [pixels]
+  // per sorted instance, bit c = the instance contributed to a pixel of cell
+  // c of its tile (cells of 2 x 4 pixels, c = x / 2 + 8 (y / 4) in tile
+  // coordinates): OR-ed by the forward (zeroed before it; NULL: not
+  // recorded), read by the backward, which walks only those instances
+  uint32_t* cells;
   const float* dimage;  // backward only
   float* g2d;           // backward only: 9 planes of [B][stride]
   int direct_max;       // backward only: at most this many contributing lanes -> per-lane atomics
@@ -108,6 +113,7 @@ struct SortArgs {
   int* status;
   const uint64_t** sorted_keys;  // device slots: where the sorted list ends up
   const uint32_t** sorted_vals;
+  uint32_t* cells;               // per-instance contribution cells, zeroed by tile_ranges (NULL: none)
 };
 
 size_t sort_lookback_bytes(int64_t count, int items, int segments);

@@ -298,7 +298,7 @@ __device__ __forceinline__ bool bwd_pair(bool live, const float4& q0, const floa
 
 // One forward (pixel, Gaussian) pair, branch-free.  bit = this pixel's bit in
 // `done`; idx = 1 + the pair's list position.
-__device__ __forceinline__ void fwd_pair(const float4& q1, float blue, float a0, float a1, float dy, uint32_t bit,
+__device__ __forceinline__ bool fwd_pair(const float4& q1, float blue, float a0, float a1, float dy, uint32_t bit,
                                          uint32_t idx, uint32_t& done, float& T, float (&C)[3], uint32_t& last) {
   const float p2 = splat_p2(q1.x, a1, a0, dy);
   float G;
@@ -314,6 +314,7 @@ __device__ __forceinline__ void fwd_pair(const float4& q1, float blue, float a0,
   C[2] = fmaf(blue, wgt, C[2]);
   T = acc ? Tn : T;
   last = acc ? idx : last;
+  return acc;
 }
 
 // ---------------------------------------------------------------- pixel pairs
@@ -328,7 +329,7 @@ __device__ __forceinline__ void fwd_pair(const float4& q1, float blue, float a0,
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
 // Forward of one pixel pair (bits bitx, bitx << 1 of `done`).
-__device__ __forceinline__ void fwd_pair2(const float2& cC, const float2& a1, const float2& a0, const float2& op,
+__device__ __forceinline__ bool fwd_pair2(const float2& cC, const float2& a1, const float2& a0, const float2& op,
                                           const float2& r, const float2& g, const float2& b, float2 dy,
                                           uint32_t bitx, uint32_t idx, uint32_t& done, float2& T, float2 (&C)[3],
                                           uint32_t& lastx, uint32_t& lasty) {
@@ -350,6 +351,7 @@ __device__ __forceinline__ void fwd_pair2(const float2& cC, const float2& a1, co
   T = make_float2(accx ? Tn.x : T.x, accy ? Tn.y : T.y);
   lastx = accx ? idx : lastx;
   lasty = accy ? idx : lasty;
+  return accx || accy;
 }
 
 // Backward of one pixel pair.  Per (thread, Gaussian) it accumulates the
@@ -471,12 +473,30 @@ struct Geo {
   }
 };
 
+// Contribution cells: a tile is 8 x 4 cells of 2 x 4 pixels, cell
+// c = x / 2 + 8 (y / 4) in tile coordinates.  The forward ORs, per sorted
+// instance, the cells of the pixels it contributed to; the backward walks an
+// instance only where one of its pixels' cells is set.
+__device__ __forceinline__ uint32_t cell_bit(int px, int py) {
+  return 1u << (((px & (kTile - 1)) >> 1) + 8 * ((py & (kTile - 1)) >> 2));
+}
+
+// Cells of the pixel rectangle [x0, x0 + w) x [y0, y0 + h) (tile
+// coordinates, even x0 and w, y0 and h multiples of 4).
+__device__ __forceinline__ uint32_t rect_cells(int x0, int y0, int w, int h) {
+  const uint32_t row = ((1u << (w >> 1)) - 1u) << ((x0 & (kTile - 1)) >> 1);
+  uint32_t m = 0;
+  for (int r = ((y0 & (kTile - 1)) >> 2); r < ((y0 & (kTile - 1)) >> 2) + (h >> 2); r++) m |= row << (8 * r);
+  return m;
+}
+
 template <int PPT>
 __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArgs a, int64_t bins) {
   using G = Geo<PPT, LaneGroups<PPT>::FWD>;
   constexpr int NWB = G::NW * G::TPB;  // warps per block
   constexpr int NP = PPT / 2;          // pixel pairs per thread
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
+  __shared__ uint32_t s_cells[NWB][32];  // contribution cells of the batch's entries
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   G geo;
   if (!geo.init(a, bins, w, lane)) {
@@ -511,11 +531,18 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   }
   const uint32_t all_done = (1u << PPT) - 1u;
   const float fpx = (float)px, fpy = (float)py0;
+  // cell of each pixel pair (both pixels of a pair share one: py0 is even)
+  // or of the single pixel
+  uint32_t cbit[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int j = 0; j < (NP > 0 ? NP : 1); j++) cbit[j] = cell_bit(px, py0 + 2 * j);
+  uint32_t* __restrict__ cells = a.cells;
   for (int b0 = 0; b0 < n; b0 += 32) {
     if (__all_sync(0xffffffffu, done == all_done)) break;
     const int i = b0 + lane;
     bool hit = false;
     __syncwarp();
+    s_cells[w][lane] = 0u;
     uint32_t gbits = 0;
     if (i < n) {
       float4 r0, r1, r2;
@@ -554,10 +581,12 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
       const float a0 = __fmul_rn(q0.z, __fmul_rn(dx, dx));
       const float a1 = __fmul_rn(q0.w, dx);
       const uint32_t idx = (uint32_t)(b0 + j + 1);
+      uint32_t mine = 0;  // cells this lane's pixels contributed to
       if constexpr (NP == 0) {
 #pragma unroll
         for (int k = 0; k < PPT; k++)
-          fwd_pair(q1, q2.x, a0, a1, __fsub_rn(q0.y, fpy + (float)k), 1u << k, idx, done, T[k], C[k], last[k]);
+          mine |= fwd_pair(q1, q2.x, a0, a1, __fsub_rn(q0.y, fpy + (float)k), 1u << k, idx, done, T[k], C[k],
+                           last[k]) ? cbit[0] : 0u;
       } else {
         const float2 cC = bc2(q1.x), A1 = bc2(a1), A0 = bc2(a0), op = bc2(q1.y);
         const float2 r = bc2(q1.z), g = bc2(q1.w), b = bc2(q2.x), qy = bc2(q0.y);
@@ -565,11 +594,15 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
         uint32_t dn = act ? done : all_done;
 #pragma unroll
         for (int jp = 0; jp < NP; jp++)
-          fwd_pair2(cC, A1, A0, op, r, g, b, __fadd2_rn(qy, nfy[jp]), 1u << (2 * jp), idx, dn, T2[jp], C2[jp],
-                    last[2 * jp], last[2 * jp + 1]);
+          mine |= fwd_pair2(cC, A1, A0, op, r, g, b, __fadd2_rn(qy, nfy[jp]), 1u << (2 * jp), idx, dn, T2[jp],
+                            C2[jp], last[2 * jp], last[2 * jp + 1]) ? cbit[jp] : 0u;
         done = act ? dn : done;
       }
+      if (mine) atomicOr(&s_cells[w][j], mine);
     }
+    // the batch's contribution cells, OR-ed with the other warps' of the tile
+    __syncwarp();
+    if (cells && i < n && s_cells[w][lane]) atomicOr(cells + rg.x + i, s_cells[w][lane]);
   }
   if constexpr (NP > 0) {
 #pragma unroll
@@ -683,67 +716,47 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
   }
   // this warp only walks the entries before its pixels' last contributors
   const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
-  // the same over the lane group
-  int gmax = (int)mymax;
-#pragma unroll
-  for (int off = G::GW / 2; off >= 1 && G::GW < 32; off >>= 1) gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, off));
   const float fpx = (float)px, fpy = (float)py0;
   const int64_t gplane = (int64_t)a.B * a.stride;
-  // with 4+ pixels per thread, lane j's record of the next batch (towards
-  // the front) is loaded while the warp walks this one (measured faster
-  // there; slower with 1-2 pixels per thread, where the extra registers cost
-  // occupancy)
-  constexpr bool kPrefetch = PPT >= 4;
-  float4 n0, n1, n2;
-  uint32_t ng = 0;
-  if constexpr (kPrefetch) {
-    const int i = max(0, total - 32) + lane;
-    if (i < total) {
-      ng = vals[rg.x + i];
-      stage_one(a, v, ng, n0, n1, n2);
-    }
-  }
+  // contribution cells of the warp's rectangle and of each lane group's
+  // (the forward recorded, per instance, the cells it contributed to): an
+  // entry is walked only by the groups where it contributed to some pixel
+  const int lx0 = (int)geo.wx0 & (kTile - 1), ly0 = (int)geo.wy0 & (kTile - 1);
+  const uint32_t wcells = rect_cells(lx0, ly0, G::RW, G::RH);
+  uint32_t gcells[G::NG];
+#pragma unroll
+  for (int g = 0; g < G::NG; g++)
+    gcells[g] = rect_cells(lx0 + (g % G::NGX) * G::GCW, ly0 + (g / G::NGX) * G::GRH, G::GCW, G::GRH);
+  const uint32_t* __restrict__ cells = a.cells;
   for (int bend = total; bend > 0; bend -= 32) {
     const int bstart = max(0, bend - 32);
     const int i = bstart + lane;
-    bool hit = false;
+    const uint32_t word = i < bend ? cells[rg.x + i] & wcells : 0u;
+    // a batch where no entry contributed to the warp's pixels is skipped
+    // without loading its records
+    if (__ballot_sync(0xffffffffu, word != 0u) == 0u) continue;
     uint32_t gbits = 0;
     __syncwarp();
-    if (i < bend) {
-      if constexpr (!kPrefetch) {
-        ng = vals[rg.x + i];
-        stage_one(a, v, ng, n0, n1, n2);
-      }
+    if (word) {
+      const uint32_t ng = vals[rg.x + i];
+      float4 n0, n1, n2;
+      stage_one(a, v, ng, n0, n1, n2);
       s0[w][lane] = n0;
       s1[w][lane] = n1;
       s2[w][lane] = n2;
       sg[w][lane] = ng;
-      if constexpr (G::NG > 1) gbits = box_group_bits(n0, n1, n2, geo);
-      else hit = ellipse_hits(n0, n1, n2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
-    }
-    uint32_t mask = __ballot_sync(0xffffffffu, hit);
-    int iters = 32;
-    if constexpr (G::NG > 1) {
 #pragma unroll
-      for (int g = 0; g < G::NG; g++) {
-        const uint32_t m = __ballot_sync(0xffffffffu, (gbits >> g) & 1u);
-        mask = g == geo.grp ? m : mask;
-      }
-      // entries at or past the group's last contributor change nothing
-      const int lim = gmax - bstart;
-      mask = lim <= 0 ? 0u : (lim >= 32 ? mask : mask & ((1u << lim) - 1u));
-      iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mask));
+      for (int g = 0; g < G::NG; g++) gbits |= (word & gcells[g]) ? 1u << g : 0u;
     }
+    uint32_t mask = 0;
+#pragma unroll
+    for (int g = 0; g < G::NG; g++) {
+      const uint32_t m = __ballot_sync(0xffffffffu, (gbits >> g) & 1u);
+      mask = g == geo.grp ? m : mask;
+    }
+    int iters = 32;
+    if constexpr (G::NG > 1) iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mask));
     __syncwarp();
-    if constexpr (kPrefetch) {
-      if (bstart > 0) {
-        const int k = max(0, bstart - 32) + lane;
-        if (k < bstart) {
-          ng = vals[rg.x + k];
-          stage_one(a, v, ng, n0, n1, n2);
-        }
-      }
-    }
     for (int it = 0; G::NG > 1 ? it < iters : mask != 0u; it++) {  // back to front
       const bool act = mask != 0u;
       const int j = act ? 31 - __clz(mask) : 0;

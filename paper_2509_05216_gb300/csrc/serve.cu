@@ -364,6 +364,7 @@ gs_status gs_serve_create(gs_server** out, int device, const gs_params* resident
       return GS_ECUDA;
     }
     gs_set_stream(sl.ctx, sl.stream);
+    gs::ctx_set_forward_only(sl.ctx, true);
     // every workspace of the largest admissible batch, once
     const gs_status rs = gs::ctx_reserve(sl.ctx, resident->stride, (int)B, B * max_view_tiles(c), B * px,
                                          max_view_tiles(c));
