@@ -477,26 +477,23 @@ struct Geo {
 // c = x / 2 + 8 (y / 4) in tile coordinates.  The forward ORs, per sorted
 // instance, the cells of the pixels it contributed to; the backward walks an
 // instance only where one of its pixels' cells is set.
-__device__ __forceinline__ uint32_t cell_bit(int px, int py) {
-  return 1u << (((px & (kTile - 1)) >> 1) + 8 * ((py & (kTile - 1)) >> 2));
-}
-
-// Cells of the pixel rectangle [x0, x0 + w) x [y0, y0 + h) (tile
-// coordinates, even x0 and w, y0 and h multiples of 4).
-__device__ __forceinline__ uint32_t rect_cells(int x0, int y0, int w, int h) {
-  const uint32_t row = ((1u << (w >> 1)) - 1u) << ((x0 & (kTile - 1)) >> 1);
+// Cells of a w x h pixel rectangle (w even, h a multiple of 4) whose first
+// cell is cell 0; shifted left by a rectangle's first cell index it gives
+// that rectangle's cells.
+__host__ __device__ constexpr uint32_t rect_cells_rel(int w, int h) {
   uint32_t m = 0;
-  for (int r = ((y0 & (kTile - 1)) >> 2); r < ((y0 & (kTile - 1)) >> 2) + (h >> 2); r++) m |= row << (8 * r);
+  for (int r = 0; r < h / 4; r++) m |= (w >= 16 ? 0xffu : ((1u << (w / 2)) - 1u)) << (8 * r);
   return m;
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArgs a, int64_t bins) {
+__global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 9 : 1) raster_fwd_kernel(RasterArgs a, int64_t bins) {
   using G = Geo<PPT, LaneGroups<PPT>::FWD>;
   constexpr int NWB = G::NW * G::TPB;  // warps per block
   constexpr int NP = PPT / 2;          // pixel pairs per thread
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
-  __shared__ uint32_t s_cells[NWB][32];  // contribution cells of the batch's entries
+  // per tile cell: the batch entries that contributed to a pixel of the cell
+  __shared__ uint32_t s_cm[NWB][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   G geo;
   if (!geo.init(a, bins, w, lane)) {
@@ -531,18 +528,21 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   }
   const uint32_t all_done = (1u << PPT) - 1u;
   const float fpx = (float)px, fpy = (float)py0;
-  // cell of each pixel pair (both pixels of a pair share one: py0 is even)
-  // or of the single pixel
-  uint32_t cbit[NP > 0 ? NP : 1];
-#pragma unroll
-  for (int j = 0; j < (NP > 0 ? NP : 1); j++) cbit[j] = cell_bit(px, py0 + 2 * j);
-  uint32_t* __restrict__ cells = a.cells;
+  // contribution cells: a lane's pixels lie in NSL cells (one per 4 rows;
+  // py0 is even, and a multiple of 4 with 4+ pixels per thread); per batch
+  // a lane keeps, per cell, the mask of the entries it contributed to
+  constexpr int NSL = PPT >= 4 ? PPT / 4 : 1;
+  // the warp's cells: NCX x NCY from its first cell
+  constexpr int NCX = G::RW / 2, NCY = G::RH / 4;
   for (int b0 = 0; b0 < n; b0 += 32) {
     if (__all_sync(0xffffffffu, done == all_done)) break;
     const int i = b0 + lane;
     bool hit = false;
     __syncwarp();
-    s_cells[w][lane] = 0u;
+    s_cm[w][lane] = 0u;
+    uint32_t cm[NSL];
+#pragma unroll
+    for (int sl = 0; sl < NSL; sl++) cm[sl] = 0u;
     uint32_t gbits = 0;
     if (i < n) {
       float4 r0, r1, r2;
@@ -581,12 +581,12 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
       const float a0 = __fmul_rn(q0.z, __fmul_rn(dx, dx));
       const float a1 = __fmul_rn(q0.w, dx);
       const uint32_t idx = (uint32_t)(b0 + j + 1);
-      uint32_t mine = 0;  // cells this lane's pixels contributed to
+      const uint32_t jbit = 1u << j;
       if constexpr (NP == 0) {
 #pragma unroll
         for (int k = 0; k < PPT; k++)
-          mine |= fwd_pair(q1, q2.x, a0, a1, __fsub_rn(q0.y, fpy + (float)k), 1u << k, idx, done, T[k], C[k],
-                           last[k]) ? cbit[0] : 0u;
+          cm[0] |= fwd_pair(q1, q2.x, a0, a1, __fsub_rn(q0.y, fpy + (float)k), 1u << k, idx, done, T[k], C[k],
+                            last[k]) ? jbit : 0u;
       } else {
         const float2 cC = bc2(q1.x), A1 = bc2(a1), A0 = bc2(a0), op = bc2(q1.y);
         const float2 r = bc2(q1.z), g = bc2(q1.w), b = bc2(q2.x), qy = bc2(q0.y);
@@ -594,15 +594,30 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
         uint32_t dn = act ? done : all_done;
 #pragma unroll
         for (int jp = 0; jp < NP; jp++)
-          mine |= fwd_pair2(cC, A1, A0, op, r, g, b, __fadd2_rn(qy, nfy[jp]), 1u << (2 * jp), idx, dn, T2[jp],
-                            C2[jp], last[2 * jp], last[2 * jp + 1]) ? cbit[jp] : 0u;
+          cm[jp / 2 < NSL ? jp / 2 : 0] |= fwd_pair2(cC, A1, A0, op, r, g, b, __fadd2_rn(qy, nfy[jp]), 1u << (2 * jp),
+                                                   idx, dn, T2[jp], C2[jp], last[2 * jp], last[2 * jp + 1]) ? jbit : 0u;
         done = act ? dn : done;
       }
-      if (mine) atomicOr(&s_cells[w][j], mine);
     }
-    // the batch's contribution cells, OR-ed with the other warps' of the tile
-    __syncwarp();
-    if (cells && i < n && s_cells[w][lane]) atomicOr(cells + rg.x + i, s_cells[w][lane]);
+    // the batch's contribution cells: per cell the OR of its lanes' entry
+    // masks, transposed into one word per entry (lane j: entry b0 + j),
+    // OR-ed with the other warps' cells of the tile
+    if (a.cells) {
+#pragma unroll
+      for (int sl = 0; sl < NSL; sl++)
+        if (cm[sl]) atomicOr(&s_cm[w][((px & (kTile - 1)) >> 1) + 8 * (((py0 + 4 * sl) & (kTile - 1)) >> 2)], cm[sl]);
+      __syncwarp();
+      const int c00 = (((int)geo.wx0 & (kTile - 1)) >> 1) + 8 * (((int)geo.wy0 & (kTile - 1)) >> 2);
+      uint32_t word = 0;
+#pragma unroll
+      for (int cy = 0; cy < NCY; cy++)
+#pragma unroll
+        for (int cx = 0; cx < NCX; cx++) {
+          const int c = c00 + cx + 8 * cy;
+          word |= ((s_cm[w][c] >> lane) & 1u) << c;
+        }
+      if (word && i < n) atomicOr(a.cells + rg.x + i, word);
+    }
   }
   if constexpr (NP > 0) {
 #pragma unroll
@@ -721,17 +736,14 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
   // contribution cells of the warp's rectangle and of each lane group's
   // (the forward recorded, per instance, the cells it contributed to): an
   // entry is walked only by the groups where it contributed to some pixel
-  const int lx0 = (int)geo.wx0 & (kTile - 1), ly0 = (int)geo.wy0 & (kTile - 1);
-  const uint32_t wcells = rect_cells(lx0, ly0, G::RW, G::RH);
-  uint32_t gcells[G::NG];
-#pragma unroll
-  for (int g = 0; g < G::NG; g++)
-    gcells[g] = rect_cells(lx0 + (g % G::NGX) * G::GCW, ly0 + (g / G::NGX) * G::GRH, G::GCW, G::GRH);
+  // (cell masks relative to the warp's first cell c00)
+  const int c00 = (((int)geo.wx0 & (kTile - 1)) >> 1) + 8 * (((int)geo.wy0 & (kTile - 1)) >> 2);
+  constexpr uint32_t kWarpCells = rect_cells_rel(G::RW, G::RH);
   const uint32_t* __restrict__ cells = a.cells;
   for (int bend = total; bend > 0; bend -= 32) {
     const int bstart = max(0, bend - 32);
     const int i = bstart + lane;
-    const uint32_t word = i < bend ? cells[rg.x + i] & wcells : 0u;
+    const uint32_t word = i < bend ? (cells[rg.x + i] >> c00) & kWarpCells : 0u;
     // a batch where no entry contributed to the warp's pixels is skipped
     // without loading its records
     if (__ballot_sync(0xffffffffu, word != 0u) == 0u) continue;
@@ -746,7 +758,9 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
       s2[w][lane] = n2;
       sg[w][lane] = ng;
 #pragma unroll
-      for (int g = 0; g < G::NG; g++) gbits |= (word & gcells[g]) ? 1u << g : 0u;
+      for (int g = 0; g < G::NG; g++)
+        gbits |= (word & (rect_cells_rel(G::GCW, G::GRH) << ((g % G::NGX) * G::GCW / 2 + 8 * ((g / G::NGX) * G::GRH / 4))))
+                     ? 1u << g : 0u;
     }
     uint32_t mask = 0;
 #pragma unroll
