@@ -578,8 +578,7 @@ void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, int items, cud
 // ---------------------------------------------------------------- tile ranges
 
 // ranges[bin] = [first, last + 1) of the bin in the sorted keys; block 0
-// also records which buffers hold the sorted list, and every instance's
-// contribution-cell word is zeroed for the forward pass.  Each key is loaded once:
+// also records which buffers hold the sorted list.  Each key is loaded once:
 // a lane compares its bin with its neighbours' through shuffles (the warp's
 // edge lanes load one neighbour each).
 __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __restrict__ ranges) {
@@ -598,14 +597,12 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __r
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint32_t* __restrict__ hi32 = reinterpret_cast<const uint32_t*>(keys) + 1;  // bin = upper half
-  uint32_t* __restrict__ cells = a.cells;
   for (int64_t w0 = warp * 32 * U; w0 < count; w0 += nwarps * 32 * U) {
     uint32_t bin[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t i = w0 + 32 * u + lane;
       bin[u] = i < count ? hi32[2 * i] : none;
-      if (cells && i < count) cells[i] = 0u;
     }
     const uint32_t before = (lane == 0 && w0 > 0) ? hi32[2 * (w0 - 1)] : none;
     const uint32_t after = (lane == 31 && w0 + 32 * U < count) ? hi32[2 * (w0 + 32 * U)] : none;

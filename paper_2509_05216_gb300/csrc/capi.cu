@@ -522,7 +522,8 @@ gs_status gs_bin_sort(gs_ctx* c) {
   GS_TRY(ensure(c, c->lookback, lb * npass));
   GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
   GS_TRY(ensure(c, c->sorted_slots, 2 * sizeof(void*)));
-  if (!c->forward_only) GS_TRY(ensure(c, c->cells, sizeof(uint32_t) * cap));
+  // contribution masks: every tile's region padded to whole batches of 32
+  if (!c->forward_only) GS_TRY(ensure(c, c->cells, sizeof(uint32_t) * (cap + 32 * c->bins)));
 
   DuplicateArgs d{};
   d.n = c->n;
@@ -567,7 +568,6 @@ gs_status gs_bin_sort(gs_ctx* c) {
   sa.status = c->status_d;
   sa.sorted_keys = reinterpret_cast<const uint64_t**>(c->sorted_slots.p);
   sa.sorted_vals = reinterpret_cast<const uint32_t**>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
-  sa.cells = c->forward_only ? nullptr : P<uint32_t>(c->cells);
   GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * (size_t)B * npass * 256, c->stream));
   GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * 8, c->stream));
   GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * npass, c->stream));

@@ -57,10 +57,10 @@ struct RasterArgs {
   float* image;         // [B][3][H][W] concatenated (forward: may be NULL when fused with the L1 loss)
   float* tfinal;        // [pixels]
   uint32_t* nlast;      // [pixels]
-  // per sorted instance, bit c = the instance contributed to a pixel of cell
-  // c of its tile (cells of 2 x 4 pixels, c = x / 2 + 8 (y / 4) in tile
-  // coordinates): OR-ed by the forward (zeroed before it; NULL: not
-  // recorded), read by the backward, which walks only those instances
+  // contribution masks: per tile, per batch of 32 list entries and per cell
+  // of 2 x 4 pixels, the entries that contributed to a pixel of the cell
+  // (instances + 32 bins words; written by the forward, NULL: not recorded;
+  // read by the backward, which walks only those entries)
   uint32_t* cells;
   const float* dimage;  // backward only
   float* g2d;           // backward only: 9 planes of [B][stride]
@@ -113,7 +113,6 @@ struct SortArgs {
   int* status;
   const uint64_t** sorted_keys;  // device slots: where the sorted list ends up
   const uint32_t** sorted_vals;
-  uint32_t* cells;               // per-instance contribution cells, zeroed by tile_ranges (NULL: none)
 };
 
 size_t sort_lookback_bytes(int64_t count, int items, int segments);

@@ -474,18 +474,16 @@ struct Geo {
 };
 
 // Contribution cells: a tile is 8 x 4 cells of 2 x 4 pixels, cell
-// c = x / 2 + 8 (y / 4) in tile coordinates.  The forward ORs, per sorted
-// instance, the cells of the pixels it contributed to; the backward walks an
-// instance only where one of its pixels' cells is set.
-// Cells of a w x h pixel rectangle (w even, h a multiple of 4) whose first
-// cell is cell 0; shifted left by a rectangle's first cell index it gives
-// that rectangle's cells.
-__host__ __device__ constexpr uint32_t rect_cells_rel(int w, int h) {
-  uint32_t m = 0;
-  for (int r = 0; r < h / 4; r++) m |= (w >= 16 ? 0xffu : ((1u << (w / 2)) - 1u)) << (8 * r);
-  return m;
-}
-
+// c = x / 2 + 8 (y / 4) in tile coordinates.  For every batch of 32 list
+// entries (entries 32 k .. 32 k + 31 of the tile's list) the forward stores,
+// per cell, the mask of the entries that contributed to a pixel of the cell:
+// word cells_offset(start, bin) + 32 k + c, start = the tile's first sorted
+// instance.  The offset pads every tile's region to whole batches (a buffer
+// of instances + 32 bins words), so tiles never share a word, and each cell
+// belongs to one warp of the forward, which writes every batch of its
+// tile's list (zero after its pixels stopped).  The backward walks an entry
+// only in the lane groups whose cell it contributed to.
+__device__ __forceinline__ int64_t cells_offset(uint32_t start, int64_t bin) { return (int64_t)start + 32 * bin; }
 template <int PPT>
 __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 9 : 1) raster_fwd_kernel(RasterArgs a, int64_t bins) {
   using G = Geo<PPT, LaneGroups<PPT>::FWD>;
@@ -534,7 +532,13 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 9 : 1) raster_fw
   constexpr int NSL = PPT >= 4 ? PPT / 4 : 1;
   // the warp's cells: NCX x NCY from its first cell
   constexpr int NCX = G::RW / 2, NCY = G::RH / 4;
-  for (int b0 = 0; b0 < n; b0 += 32) {
+  // the warp's cells (NCX x NCY from cell c00) and where the tile's batch
+  // masks start; lane k < NCX NCY stores the mask of the warp's k-th cell
+  const int c00 = (((int)geo.wx0 & (kTile - 1)) >> 1) + 8 * (((int)geo.wy0 & (kTile - 1)) >> 2);
+  const int kcell = c00 + lane % NCX + 8 * (lane / NCX);
+  uint32_t* const cell_base = a.cells ? a.cells + cells_offset(rg.x, geo.bin) + kcell : nullptr;
+  int b0 = 0;
+  for (; b0 < n; b0 += 32) {
     if (__all_sync(0xffffffffu, done == all_done)) break;
     const int i = b0 + lane;
     bool hit = false;
@@ -599,26 +603,19 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 9 : 1) raster_fw
         done = act ? dn : done;
       }
     }
-    // the batch's contribution cells: per cell the OR of its lanes' entry
-    // masks, transposed into one word per entry (lane j: entry b0 + j),
-    // OR-ed with the other warps' cells of the tile
-    if (a.cells) {
+    // the batch's contribution masks: per cell of the warp, the OR of its
+    // lanes' entry masks (each cell belongs to one warp: plain stores)
+    if (cell_base) {
 #pragma unroll
       for (int sl = 0; sl < NSL; sl++)
         if (cm[sl]) atomicOr(&s_cm[w][((px & (kTile - 1)) >> 1) + 8 * (((py0 + 4 * sl) & (kTile - 1)) >> 2)], cm[sl]);
       __syncwarp();
-      const int c00 = (((int)geo.wx0 & (kTile - 1)) >> 1) + 8 * (((int)geo.wy0 & (kTile - 1)) >> 2);
-      uint32_t word = 0;
-#pragma unroll
-      for (int cy = 0; cy < NCY; cy++)
-#pragma unroll
-        for (int cx = 0; cx < NCX; cx++) {
-          const int c = c00 + cx + 8 * cy;
-          word |= ((s_cm[w][c] >> lane) & 1u) << c;
-        }
-      if (word && i < n) atomicOr(a.cells + rg.x + i, word);
+      if (lane < NCX * NCY) cell_base[b0] = s_cm[w][kcell];
     }
   }
+  // batches after the warp's pixels all stopped: nothing contributed
+  if (cell_base && lane < NCX * NCY)
+    for (; b0 < n; b0 += 32) cell_base[b0] = 0u;
   if constexpr (NP > 0) {
 #pragma unroll
     for (int jp = 0; jp < NP; jp++) {
@@ -683,7 +680,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 9 : 1) raster_fw
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArgs a, int64_t bins) {
+__global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 8 : 1) raster_bwd_kernel(RasterArgs a, int64_t bins) {
   using G = Geo<PPT, LaneGroups<PPT>::BWD>;
   constexpr int NWB = G::NW * G::TPB;
   constexpr int NP = PPT / 2;  // pixel pairs per thread (0: the scalar one-pixel path)
@@ -733,23 +730,27 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
   const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
   const float fpx = (float)px, fpy = (float)py0;
   const int64_t gplane = (int64_t)a.B * a.stride;
-  // contribution cells of the warp's rectangle and of each lane group's
-  // (the forward recorded, per instance, the cells it contributed to): an
-  // entry is walked only by the groups where it contributed to some pixel
-  // (cell masks relative to the warp's first cell c00)
+  // contribution masks of the forward (batches of 32 entries from the
+  // front of the list, one mask per cell): lane k < NCX NCY loads the mask
+  // of the warp's k-th cell; the warp walks the union, each lane group the
+  // mask of its own cell
+  constexpr int NCX = G::RW / 2, NCY = G::RH / 4;
+  static_assert(G::NG == 1 || (G::GCW == 2 && G::GRH == 4 && G::NGX == NCX), "one contribution cell per lane group");
   const int c00 = (((int)geo.wx0 & (kTile - 1)) >> 1) + 8 * (((int)geo.wy0 & (kTile - 1)) >> 2);
-  constexpr uint32_t kWarpCells = rect_cells_rel(G::RW, G::RH);
-  const uint32_t* __restrict__ cells = a.cells;
-  for (int bend = total; bend > 0; bend -= 32) {
-    const int bstart = max(0, bend - 32);
+  const uint32_t* __restrict__ cell_base =
+      a.cells + cells_offset(rg.x, geo.bin) + c00 + lane % NCX + 8 * (lane / NCX);
+  for (int bstart = ((total - 1) >> 5) << 5; bstart >= 0 && total > 0; bstart -= 32) {
     const int i = bstart + lane;
-    const uint32_t word = i < bend ? (cells[rg.x + i] >> c00) & kWarpCells : 0u;
-    // a batch where no entry contributed to the warp's pixels is skipped
+    // entries at or past the warp's last contributor change nothing
+    const int nb = min(32, total - bstart);
+    const uint32_t lim = nb >= 32 ? 0xffffffffu : (1u << nb) - 1u;
+    const uint32_t cm = lane < NCX * NCY ? cell_base[bstart] & lim : 0u;
+    const uint32_t any = __reduce_or_sync(0xffffffffu, cm);
+    // a batch where nothing contributed to the warp's pixels is skipped
     // without loading its records
-    if (__ballot_sync(0xffffffffu, word != 0u) == 0u) continue;
-    uint32_t gbits = 0;
+    if (any == 0u) continue;
     __syncwarp();
-    if (word) {
+    if ((any >> lane) & 1u) {
       const uint32_t ng = vals[rg.x + i];
       float4 n0, n1, n2;
       stage_one(a, v, ng, n0, n1, n2);
@@ -757,17 +758,9 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_bwd_kernel(RasterArg
       s1[w][lane] = n1;
       s2[w][lane] = n2;
       sg[w][lane] = ng;
-#pragma unroll
-      for (int g = 0; g < G::NG; g++)
-        gbits |= (word & (rect_cells_rel(G::GCW, G::GRH) << ((g % G::NGX) * G::GCW / 2 + 8 * ((g / G::NGX) * G::GRH / 4))))
-                     ? 1u << g : 0u;
     }
-    uint32_t mask = 0;
-#pragma unroll
-    for (int g = 0; g < G::NG; g++) {
-      const uint32_t m = __ballot_sync(0xffffffffu, (gbits >> g) & 1u);
-      mask = g == geo.grp ? m : mask;
-    }
+    // group g's cell is the warp's cell g (groups of 2 x 4 pixels)
+    uint32_t mask = G::NG > 1 ? __shfl_sync(0xffffffffu, cm, geo.grp) : any;
     int iters = 32;
     if constexpr (G::NG > 1) iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mask));
     __syncwarp();
