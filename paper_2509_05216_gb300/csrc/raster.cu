@@ -484,14 +484,16 @@ struct Geo {
 // tile's list (zero after its pixels stopped).  The backward walks an entry
 // only in the lane groups whose cell it contributed to.
 __device__ __forceinline__ int64_t cells_offset(uint32_t start, int64_t bin) { return (int64_t)start + 32 * bin; }
+
+__device__ __forceinline__ int cell_index(int px, int py) {
+  return ((px & (kTile - 1)) >> 1) + 8 * ((py & (kTile - 1)) >> 2);
+}
 template <int PPT>
-__global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 9 : 1) raster_fwd_kernel(RasterArgs a, int64_t bins) {
+__global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArgs a, int64_t bins) {
   using G = Geo<PPT, LaneGroups<PPT>::FWD>;
   constexpr int NWB = G::NW * G::TPB;  // warps per block
   constexpr int NP = PPT / 2;          // pixel pairs per thread
   __shared__ float4 s0[NWB][32], s1[NWB][32], s2[NWB][32];
-  // per tile cell: the batch entries that contributed to a pixel of the cell
-  __shared__ uint32_t s_cm[NWB][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   G geo;
   if (!geo.init(a, bins, w, lane)) {
@@ -530,20 +532,19 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 9 : 1) raster_fw
   // py0 is even, and a multiple of 4 with 4+ pixels per thread); per batch
   // a lane keeps, per cell, the mask of the entries it contributed to
   constexpr int NSL = PPT >= 4 ? PPT / 4 : 1;
-  // the warp's cells: NCX x NCY from its first cell
-  constexpr int NCX = G::RW / 2, NCY = G::RH / 4;
-  // the warp's cells (NCX x NCY from cell c00) and where the tile's batch
-  // masks start; lane k < NCX NCY stores the mask of the warp's k-th cell
-  const int c00 = (((int)geo.wx0 & (kTile - 1)) >> 1) + 8 * (((int)geo.wy0 & (kTile - 1)) >> 2);
-  const int kcell = c00 + lane % NCX + 8 * (lane / NCX);
-  uint32_t* const cell_base = a.cells ? a.cells + cells_offset(rg.x, geo.bin) + kcell : nullptr;
+  // the lanes of a cell hold its mask after an OR over the lane bits that
+  // select the column within the pair (bit 0) and, with fewer than 4 pixels
+  // per thread, the row block within the cell (lane bits from GCW up); the
+  // lane whose bits there are 0 stores it (each cell belongs to one warp)
+  constexpr int RB = PPT < 4 ? 4 / PPT : 1;  // lane rows per cell
+  const bool owner = (lane & 1) == 0 && ((lane / G::GCW) % RB) == 0;
+  uint32_t* const cell_base = a.cells ? a.cells + cells_offset(rg.x, geo.bin) : nullptr;
   int b0 = 0;
   for (; b0 < n; b0 += 32) {
     if (__all_sync(0xffffffffu, done == all_done)) break;
     const int i = b0 + lane;
     bool hit = false;
     __syncwarp();
-    s_cm[w][lane] = 0u;
     uint32_t cm[NSL];
 #pragma unroll
     for (int sl = 0; sl < NSL; sl++) cm[sl] = 0u;
@@ -603,19 +604,22 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 9 : 1) raster_fw
         done = act ? dn : done;
       }
     }
-    // the batch's contribution masks: per cell of the warp, the OR of its
-    // lanes' entry masks (each cell belongs to one warp: plain stores)
+    // the batch's contribution masks: per cell, the OR of its lanes' entry masks
     if (cell_base) {
 #pragma unroll
-      for (int sl = 0; sl < NSL; sl++)
-        if (cm[sl]) atomicOr(&s_cm[w][((px & (kTile - 1)) >> 1) + 8 * (((py0 + 4 * sl) & (kTile - 1)) >> 2)], cm[sl]);
-      __syncwarp();
-      if (lane < NCX * NCY) cell_base[b0] = s_cm[w][kcell];
+      for (int sl = 0; sl < NSL; sl++) {
+        uint32_t e = cm[sl] | __shfl_xor_sync(0xffffffffu, cm[sl], 1);
+#pragma unroll
+        for (int x = G::GCW; x < G::GCW * RB; x <<= 1) e |= __shfl_xor_sync(0xffffffffu, e, x);
+        if (owner) cell_base[b0 + cell_index(px, py0 + 4 * sl)] = e;
+      }
     }
   }
   // batches after the warp's pixels all stopped: nothing contributed
-  if (cell_base && lane < NCX * NCY)
-    for (; b0 < n; b0 += 32) cell_base[b0] = 0u;
+  if (cell_base && owner)
+    for (; b0 < n; b0 += 32)
+#pragma unroll
+      for (int sl = 0; sl < NSL; sl++) cell_base[b0 + cell_index(px, py0 + 4 * sl)] = 0u;
   if constexpr (NP > 0) {
 #pragma unroll
     for (int jp = 0; jp < NP; jp++) {
