@@ -388,7 +388,8 @@ typedef enum {
   GS_BUF_RANGES = 5, /* uint32 [bins][2]: [start, end) per bin */
   GS_BUF_TFINAL = 6, /* float [pixels]: transmittance after the last contributor */
   GS_BUF_NLAST = 7,  /* uint32 [pixels]: 1 + list position of the last contributor */
-  GS_BUF_G2D = 8,    /* float [9][B][N] planes: dL/d(mu_x, mu_y, A, B, C, opacity, r, g, b) */
+  GS_BUF_G2D = 8,    /* float [B][N][8] records dL/d(mu_x, mu_y, A, B), dL/d(C, opacity), 0, 0,
+                        then [B][N][4] records dL/d(r, g, b), 0 */
   GS_BUF_REC3 = 9,   /* int4 [B][N]: radius, tiles touched (0: culled), tile rect
                         x0 | x1 << 16 and y0 | y1 << 16 (half-open) */
   GS_BUF_SORT_CTRL = 10 /* uint32 [npass + 1]: control word of each sort pass; bit 1

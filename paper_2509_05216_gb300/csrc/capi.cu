@@ -675,7 +675,7 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   if (grads->n != c->n || grads->stride != c->stride || grads->sh_degree != c->deg)
     return fail(c, GS_EINVAL, "grads must match params in n, stride and sh_degree");
   set_device(c);
-  const size_t g2d_bytes = sizeof(float) * 9 * c->B * c->stride;
+  const size_t g2d_bytes = sizeof(float) * (kG2dGeo + kG2dCol) * c->B * c->stride;
   GS_TRY(ensure(c, c->g2d, g2d_bytes));
   GS_CUDA(c, cudaMemsetAsync(c->g2d.p, 0, g2d_bytes, c->stream));
   RasterArgs r = raster_args(c);
@@ -792,7 +792,7 @@ gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
     case GS_BUF_RANGES: if (!c->sorted) return GS_ESTATE; *ptr = c->ranges.p; *count = c->bins; break;
     case GS_BUF_TFINAL: if (!c->rastered) return GS_ESTATE; *ptr = c->tfinal.p; *count = c->pixels; break;
     case GS_BUF_NLAST: if (!c->rastered) return GS_ESTATE; *ptr = c->nlast.p; *count = c->pixels; break;
-    case GS_BUF_G2D: if (!c->g2d.p) return GS_ESTATE; *ptr = c->g2d.p; *count = 9 * bn; break;
+    case GS_BUF_G2D: if (!c->g2d.p) return GS_ESTATE; *ptr = c->g2d.p; *count = (kG2dGeo + kG2dCol) * bn; break;
     case GS_BUF_SORT_CTRL:
       if (!c->sorted) return GS_ESTATE;
       *ptr = reinterpret_cast<uint32_t*>(P<uint64_t>(c->total) + 1 + kMaxViews) + 2 * (kMaxViews + 1);

@@ -22,6 +22,12 @@ constexpr float kLog2e = 1.4426950408889634f;
 // 32-byte sectors instead of three.  Record k of entry o is rec[kRecStride * o + k].
 constexpr int kRecStride = 3;
 
+// 2D gradients per (view, Gaussian), two arrays of records: geometry
+// (kG2dGeo floats: dL/d(mu_x, mu_y, A, B), dL/d(C, opacity), 0, 0) for all
+// B x stride entries, then colour (kG2dCol floats: dL/d(r, g, b), 0).
+constexpr int kG2dGeo = 8;
+constexpr int kG2dCol = 4;
+
 // Device status word bits.
 constexpr int kStatusCapacity = 1;
 constexpr int kStatusTimeout = 2;

@@ -26,7 +26,7 @@ struct ProjectBwdArgs {
   int64_t n, stride;
   const ViewRec* views;
   int B;
-  const float* g2d;   // 9 planes of [B][stride]: dL/d(mu_x, mu_y, A, B, C, opacity, r, g, b)
+  const float* g2d;   // [B][stride] geometry records (kG2dGeo floats), then [B][stride] colour records (kG2dCol)
   float* grads;       // [P][stride]
 };
 
@@ -63,7 +63,7 @@ struct RasterArgs {
   // read by the backward, which walks only those entries)
   uint32_t* cells;
   const float* dimage;  // backward only
-  float* g2d;           // backward only: 9 planes of [B][stride]
+  float* g2d;           // backward only: [B][stride] geometry records, then [B][stride] colour records
   int direct_max;       // backward only: at most this many contributing lanes -> per-lane atomics
   // forward fused with the L1 loss (target non-NULL or read from target_slot):
   // writes dL/dimage = sign(image - target) * inv_count and one partial sum

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(96) project_bwd_color_kernel(ProjectBwdArgs a)
   const int64_t g = (int64_t)blockIdx.x * 32 + lane;
   const bool live = g < a.n;
   const float* P = a.params;
-  const int64_t S = a.stride, plane = (int64_t)a.B * S;
+  const int64_t S = a.stride;
   float mean[3] = {0.f, 0.f, 0.f}, sh[K], gsh[K];
 #pragma unroll
   for (int k = 0; k < K; k++) {
@@ -294,12 +294,14 @@ __global__ void __launch_bounds__(96) project_bwd_color_kernel(ProjectBwdArgs a)
     for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
   }
   float gm[3] = {0.f, 0.f, 0.f};
-  const float* gch = a.g2d + (6 + c) * plane;
+  // dL/d(channel c) in the colour record of (view v, Gaussian g)
+  const float* gch = a.g2d + kG2dGeo * (int64_t)a.B * S + kG2dCol * g + c;
+  const int64_t vstep = kG2dCol * S;
   // the next view's gradient is loaded while this view is processed
-  float nxt = live ? __ldg(gch + g) : 0.f;
+  float nxt = live ? __ldg(gch) : 0.f;
   for (int v = 0; v < a.B; v++) {
     const float gc_in = nxt;
-    if (live && v + 1 < a.B) nxt = __ldg(gch + (int64_t)(v + 1) * S + g);
+    if (live && v + 1 < a.B) nxt = __ldg(gch + (int64_t)(v + 1) * vstep);
     if (gc_in == 0.f) continue;
     const ViewRec& V = a.views[v];
     // rgb_c = max(0, 0.5 + sum_k sh_kc Y_k(d)), d = (mu - campos) / |mu - campos|
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.n) return;
   const float* P = a.params;
-  const int64_t S = a.stride, plane = (int64_t)a.B * S;
+  const int64_t S = a.stride;
   float mean[3], lsc[3], quat[4];
 #pragma unroll
   for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
@@ -362,15 +364,18 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
   // dL/dSigma summed over the views: the chain from Sigma to the scale and
   // rotation is linear in it, so it runs once per Gaussian after the loop
   float gm[3] = {0.f, 0.f, 0.f}, gSig[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gop = 0.f;
-  // prefetch the first view's six gradient values
+  // prefetch the first view's six gradient values (the geometry record's
+  // first float4 and the float2 after it)
+  auto load6 = [&](int v, float (&q)[6]) {
+    const float* r = a.g2d + kG2dGeo * ((int64_t)v * S + g);
+    const float4 x = __ldg(reinterpret_cast<const float4*>(r));
+    const float2 y = __ldg(reinterpret_cast<const float2*>(r + 4));
+    q[0] = x.x; q[1] = x.y; q[2] = x.z; q[3] = x.w; q[4] = y.x; q[5] = y.y;
+  };
   float cur[6], nxt[6];
-#pragma unroll
-  for (int q = 0; q < 6; q++) cur[q] = __ldg(a.g2d + q * plane + g);
+  load6(0, cur);
   for (int v = 0; v < a.B; v++) {
-    if (v + 1 < a.B) {
-#pragma unroll
-      for (int q = 0; q < 6; q++) nxt[q] = __ldg(a.g2d + q * plane + (int64_t)(v + 1) * S + g);
-    }
+    if (v + 1 < a.B) load6(v + 1, nxt);
     const float gmx = cur[0], gmy = cur[1], gA = cur[2], gB = cur[3], gC = cur[4], gsig = cur[5];
 #pragma unroll
     for (int q = 0; q < 6; q++) cur[q] = nxt[q];

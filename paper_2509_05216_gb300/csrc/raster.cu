@@ -153,57 +153,39 @@ __device__ __forceinline__ float grad_scale(int q) {
   return q < 2 ? (1.f / kLog2e) : (q == 2 || q == 4) ? -0.5f : (q == 3 ? -1.f : 1.f);
 }
 
-// Apply a warp's gradient of one Gaussian.  `contrib`: ballot of the lanes
-// whose pixels contributed.  With few such lanes each adds its own 9 values
-// (9 atomic instructions for the warp); otherwise the 9 values are summed
-// over the warp (14 shuffles) and one lane per value adds the total.
-__device__ __forceinline__ void push_grad(float* g2d, int64_t plane, int64_t rec, float (&acc)[16], int lane,
-                                          uint32_t contrib, int direct_max) {
-  if (__popc(contrib) <= direct_max) {
-    if (contrib & (1u << lane)) {
-#pragma unroll
-      for (int q = 0; q < 9; q++) atomicAdd(g2d + q * plane + rec, acc[q] * grad_scale(q));
-    }
-    return;
-  }
-  // values 0..7: reduce-scatter over three levels, then two butterfly steps
-  // (lanes 4q hold value q); value 8: a full butterfly (14 shuffles in all)
-#pragma unroll
-  for (int off = 16, half = 4; off >= 4; off >>= 1, half >>= 1) {
-    const bool up = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < half; i++) {
-      const float send = up ? acc[i] : acc[i + half];
-      const float keep = up ? acc[i + half] : acc[i];
-      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  float t8 = acc[8];
-  float t = acc[0];
-  t += __shfl_xor_sync(0xffffffffu, t, 2);
-  t += __shfl_xor_sync(0xffffffffu, t, 1);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) t8 += __shfl_xor_sync(0xffffffffu, t8, off);
-  if ((lane & 3) == 0) atomicAdd(g2d + (lane >> 2) * plane + rec, t * grad_scale(lane >> 2));
-  if (lane == 1) atomicAdd(g2d + 8 * plane + rec, t8 * grad_scale(8));
+// The 2D gradient of a (view, Gaussian) pair is a 32-byte geometry record
+// dL/d(mu_x, mu_y, A, B), dL/d(C, opacity), 0, 0 and a 16-byte colour
+// record dL/d(r, g, b), 0, added with vector reductions (one L2 request per
+// 16 or 8 bytes instead of one per value).
+__device__ __forceinline__ void red_v4(float* p, float x, float y, float z, float w) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
+__device__ __forceinline__ void red_v2(float* p, float x, float y) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
+}
+__device__ __forceinline__ void push_record(float* geo, float* col, const float (&acc)[16]) {
+  red_v4(geo, acc[0] * grad_scale(0), acc[1] * grad_scale(1), acc[2] * grad_scale(2), acc[3] * grad_scale(3));
+  red_v2(geo + 4, acc[4] * grad_scale(4), acc[5] * grad_scale(5));
+  red_v4(col, acc[6], acc[7], acc[8], 0.f);
 }
 
-// The same for groups of GW lanes that each walk their own Gaussian (lane
-// groups aligned to GW; contrib is the warp's ballot): the direct path is
-// taken when it holds for every group; otherwise each group sums its 9
-// values over its lanes (up to 3 reduce-scatter levels for values 0..7,
-// then butterflies; a butterfly for value 8) and adds the totals.
+// Apply the gradient of one Gaussian from lane groups of GW lanes that each
+// walk their own Gaussian (lane groups aligned to GW; `contrib` is the
+// warp's ballot of the lanes whose pixels contributed).  When every group
+// has at most direct_max such lanes, those lanes add their own values (3
+// reductions each); otherwise each group sums its 9 values over its lanes
+// (reduce-scatter for values 0..7, a butterfly for value 8), gathers them
+// into two lanes and adds the totals (3 reductions per group).
 template <int GW>
-__device__ __forceinline__ void push_grad_group(float* g2d, int64_t plane, int64_t rec, float (&acc)[16], int lane,
+__device__ __forceinline__ void push_grad_group(float* g2d, int64_t entries, int64_t rec, float (&acc)[16], int lane,
                                                 uint32_t contrib, int direct_max) {
   static_assert(GW == 4 || GW == 8 || GW == 16 || GW == 32, "lane groups of 4, 8, 16 or 32");
+  float* const r = g2d + kG2dGeo * rec;                         // geometry record
+  float* const rc = g2d + kG2dGeo * entries + kG2dCol * rec;    // colour record
   const int gl = lane % GW;
   const uint32_t gbits = GW == 32 ? contrib : (contrib >> (lane - gl)) & ((1u << (GW % 32)) - 1u);
   if (__all_sync(0xffffffffu, __popc(gbits) <= direct_max)) {
-    if (contrib & (1u << lane)) {
-#pragma unroll
-      for (int q = 0; q < 9; q++) atomicAdd(g2d + q * plane + rec, acc[q] * grad_scale(q));
-    }
+    if (contrib & (1u << lane)) push_record(r, rc, acc);
     return;
   }
   if constexpr (GW == 4) {
@@ -222,11 +204,15 @@ __device__ __forceinline__ void push_grad_group(float* g2d, int64_t plane, int64
     float t8 = acc[8];
     t8 += __shfl_xor_sync(0xffffffffu, t8, 2);
     t8 += __shfl_xor_sync(0xffffffffu, t8, 1);
+    // lanes 0 and 2 of the group take their right neighbour's pair
+    const float h0 = __shfl_down_sync(0xffffffffu, acc[0], 1);
+    const float h1 = __shfl_down_sync(0xffffffffu, acc[1], 1);
     if (gbits) {
-      const int q = 4 * ((gl >> 1) & 1) + 2 * (gl & 1);
-      atomicAdd(g2d + q * plane + rec, acc[0] * grad_scale(q));
-      atomicAdd(g2d + (q + 1) * plane + rec, acc[1] * grad_scale(q + 1));
-      if (gl == 0) atomicAdd(g2d + 8 * plane + rec, t8 * grad_scale(8));
+      if (gl == 0) red_v4(r, acc[0] * grad_scale(0), acc[1] * grad_scale(1), h0 * grad_scale(2), h1 * grad_scale(3));
+      if (gl == 2) {
+        red_v2(r + 4, acc[0] * grad_scale(4), acc[1] * grad_scale(5));
+        red_v4(rc, h0, h1, t8, 0.f);
+      }
     }
   } else {
 #pragma unroll
@@ -245,9 +231,17 @@ __device__ __forceinline__ void push_grad_group(float* g2d, int64_t plane, int64
     for (int off = S / 2; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
 #pragma unroll
     for (int off = GW / 2; off >= 1; off >>= 1) t8 += __shfl_xor_sync(0xffffffffu, t8, off);
+    // lane 0 of the group gathers values 0..3, lane 4 S values 4..7
+    const int src = (lane - gl) + (gl >= 4 * S ? 4 * S : 0);
+    float x[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) x[k] = __shfl_sync(0xffffffffu, t, src + k * S);
     if (gbits) {
-      if (gl % S == 0) atomicAdd(g2d + (gl / S) * plane + rec, t * grad_scale(gl / S));
-      if (gl == 1) atomicAdd(g2d + 8 * plane + rec, t8 * grad_scale(8));
+      if (gl == 0) red_v4(r, x[0] * grad_scale(0), x[1] * grad_scale(1), x[2] * grad_scale(2), x[3] * grad_scale(3));
+      if (gl == 4 * S) {
+        red_v2(r + 4, x[0] * grad_scale(4), x[1] * grad_scale(5));
+        red_v4(rc, x[2], x[3], t8, 0.f);
+      }
     }
   }
 }
@@ -733,7 +727,6 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 8 : 1) raster_bw
   // this warp only walks the entries before its pixels' last contributors
   const int total = (int)__reduce_max_sync(0xffffffffu, mymax);
   const float fpx = (float)px, fpy = (float)py0;
-  const int64_t gplane = (int64_t)a.B * a.stride;
   // contribution masks of the forward (batches of 32 entries from the
   // front of the list, one mask per cell): lane k < NCX NCY loads the mask
   // of the warp's k-th cell; the warp walks the union, each lane group the
@@ -813,12 +806,9 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 8 : 1) raster_bw
         for (int c = 0; c < 3; c++) acc[6 + c] = racc[c].x + racc[c].y;
       }
       const uint32_t contrib = __ballot_sync(0xffffffffu, any);
-      if (contrib) {
-        if constexpr (G::NG > 1)
-          push_grad_group<G::GW>(a.g2d, gplane, (int64_t)v * a.stride + sg[w][j], acc, lane, contrib, a.direct_max);
-        else
-          push_grad(a.g2d, gplane, (int64_t)v * a.stride + sg[w][j], acc, lane, contrib, a.direct_max);
-      }
+      if (contrib)
+        push_grad_group<G::GW>(a.g2d, (int64_t)a.B * a.stride, (int64_t)v * a.stride + sg[w][j], acc, lane, contrib,
+                               a.direct_max);
     }
   }
 }

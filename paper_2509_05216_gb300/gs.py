@@ -332,7 +332,7 @@ class Context:
         n = cnt.value
         spec = {GS_BUF_REC0: ((n, 4), "<f4"), GS_BUF_REC1: ((n, 4), "<f4"), GS_BUF_REC2: ((n, 4), "<f4"),
                 GS_BUF_KEYS: ((n,), "<i8"), GS_BUF_VALS: ((n,), "<i4"), GS_BUF_RANGES: ((n, 2), "<i4"),
-                GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((9, n // 9), "<f4"), GS_BUF_REC3: ((n, 4), "<i4"),
+                GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((n,), "<f4"), GS_BUF_REC3: ((n, 4), "<i4"),
                 GS_BUF_SORT_CTRL: ((n,), "<i4")}[which]
         if n == 0:
             return torch.empty(spec[0], device="cuda:%d" % self.device,

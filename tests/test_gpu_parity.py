@@ -287,7 +287,10 @@ def test_gradient_matches_oracle(ctx, oracle, name, fwd, bwd):
         r = ref[lo:hi, :n][:, keep]
         if np.linalg.norm(r) > 0:
             assert rel_l2(g[lo:hi, :n][:, keep], r) <= 1e-3, (lo, hi)
-    g2d = ctx.gs_get_buffer(gs.GS_BUF_G2D).cpu().numpy().astype(np.float64).T  # [B*stride][9]
+    # [B*stride][8] records (mu_x, mu_y, A, B), (C, opacity), -, -, then [B*stride][4] records (r, g, b), -
+    flat = ctx.gs_get_buffer(gs.GS_BUF_G2D).cpu().numpy().astype(np.float64)
+    bn = flat.size // 12
+    g2d = np.concatenate([flat[:8 * bn].reshape(bn, 8)[:, :6], flat[8 * bn:].reshape(bn, 4)[:, :3]], axis=1)
     for v in range(len(cams)):
         got = g2d[v * stride: v * stride + n][keep]
         assert rel_l2(got, ref2d[v][keep]) <= 1e-3
