@@ -36,7 +36,9 @@
  *            with S_i the colour composited behind i (explicit suffix sums);
  *            the projection part is differentiated by the complex-step method
  *            (one complex evaluation of the projection per parameter).
- *  adam, l1  textbook Adam with bias correction; mean absolute error.
+ *  adam, l1  textbook Adam with bias correction; mean absolute error.  The
+ *            visible-only variant leaves Gaussians that touch no tile in any
+ *            view of the batch (and their moments) unchanged.
  *
  * Decisions taken by comparing floating-point numbers (the skip / clamp /
  * stop thresholds, the radius ceil, the rect floors, depth order) are
@@ -724,6 +726,24 @@ void or_adam(double* p, const double* g, double* m, double* v, int P, long n, lo
   double bc1 = 1.0 - pow(b1, (double)step), bc2 = 1.0 - pow(b2, (double)step);
   for (int pl = 0; pl < P; pl++)
     for (long i = 0; i < n; i++) {
+      long k = (long)pl * stride + i;
+      m[k] = b1 * m[k] + (1.0 - b1) * g[k];
+      v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
+      double mh = m[k] / bc1, vh = v[k] / bc2;
+      p[k] -= lr[pl] * mh / (sqrt(vh) + eps);
+    }
+}
+
+/* Visible-only Adam: the sparse variant of the same update, in which a
+ * Gaussian that touches no tile in any view of the batch (visible[i] == 0)
+ * keeps its parameters and both moments unchanged, and every other Gaussian
+ * takes the Adam step above, bias-corrected by the global step count. */
+void or_adam_visible(double* p, const double* g, double* m, double* v, int P, long n, long stride,
+                     const double* lr, double b1, double b2, double eps, long step, const uint8_t* visible) {
+  double bc1 = 1.0 - pow(b1, (double)step), bc2 = 1.0 - pow(b2, (double)step);
+  for (int pl = 0; pl < P; pl++)
+    for (long i = 0; i < n; i++) {
+      if (!visible[i]) continue;
       long k = (long)pl * stride + i;
       m[k] = b1 * m[k] + (1.0 - b1) * g[k];
       v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];

@@ -63,6 +63,8 @@ def lib():
             L.or_l1.restype = ctypes.c_double
             L.or_adam.argtypes = [dp, dp, dp, dp, ci, cl, cl, dp, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, cl]
+            L.or_adam_visible.argtypes = [dp, dp, dp, dp, ci, cl, cl, dp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, cl, up]
             L.or_sh_basis.argtypes = [ci, dp, cl, dp]
             L.or_num_threads.restype = ci
             _lib = L
@@ -189,6 +191,28 @@ def adam(p, g, m, v, lr_planes, step, b1=0.9, b2=0.999, eps=1e-15, n=None):
     for a in (p, g, m, v):
         assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"] and a.shape == (P, stride)
     lib().or_adam(_p(p), _p(g), _p(m), _p(v), P, n, stride, _p(lr), b1, b2, eps, int(step))
+
+
+def adam_visible(p, g, m, v, lr_planes, step, visible, b1=0.9, b2=0.999, eps=1e-15, n=None):
+    """In-place FP64 visible-only Adam: Gaussians with visible[i] == 0 keep
+    p, m and v; the others take the Adam step."""
+    P, stride = p.shape
+    n = stride if n is None else n
+    lr = np.ascontiguousarray(lr_planes, dtype=np.float64)
+    vis = np.ascontiguousarray(np.asarray(visible)[:n], dtype=np.uint8)
+    assert lr.shape == (P,) and vis.shape == (n,)
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"] and a.shape == (P, stride)
+    lib().or_adam_visible(_p(p), _p(g), _p(m), _p(v), P, n, stride, _p(lr), b1, b2, eps, int(step),
+                          _p(vis, ctypes.c_uint8))
+
+
+def visible_in_batch(scene, cams):
+    """1 for each Gaussian that touches at least one tile in some view."""
+    vis = np.zeros(scene["n"], dtype=np.uint8)
+    for cam in cams:
+        vis |= (project(scene, cam)["tiles"] > 0).astype(np.uint8)
+    return vis
 
 
 def sh_basis(deg, dirs):

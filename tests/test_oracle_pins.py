@@ -10,6 +10,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 from paper_2509_05216_gb300 import inputs as I
 
@@ -544,3 +545,35 @@ def test_adam_matches_torch_over_steps(oracle):
         opt.step()
         oracle.adam(p, g, m, v, np.array(lr), step)
     np.testing.assert_allclose(p, np.stack([t.detach().numpy() for t in tp]), rtol=1e-12, atol=1e-15)
+
+
+def test_visible_only_adam_matches_torch_sparse_adam(oracle):
+    """Visible-only Adam: invisible Gaussians keep parameters and moments
+    exactly; visible ones equal torch.optim.SparseAdam's lazy update (moments
+    touched only where the gradient is present, bias correction by the
+    global step) and the dense step of the same state."""
+    rng = np.random.default_rng(11)
+    P, n = 14, 37
+    lr = rng.uniform(1e-4, 1e-2, size=P)
+    p = rng.normal(size=(P, n))
+    m = np.zeros((P, n))
+    v = np.zeros((P, n))
+    tp = [torch.tensor(p[k].copy(), requires_grad=True) for k in range(P)]
+    opts = [torch.optim.SparseAdam([tp[k]], lr=float(lr[k]), betas=(0.9, 0.999), eps=1e-15) for k in range(P)]
+    for step in range(1, 5):
+        vis = (rng.uniform(size=n) < 0.6).astype(np.uint8)
+        g = rng.normal(size=(P, n)) * vis
+        before = (p.copy(), m.copy(), v.copy())
+        dense = (p.copy(), g.copy(), m.copy(), v.copy())
+        oracle.adam(dense[0], dense[1], dense[2], dense[3], lr, step)
+        oracle.adam_visible(p, g, m, v, lr, step, vis)
+        hid = vis == 0
+        assert np.array_equal(p[:, hid], before[0][:, hid])
+        assert np.array_equal(m[:, hid], before[1][:, hid]) and np.array_equal(v[:, hid], before[2][:, hid])
+        np.testing.assert_allclose(p[:, ~hid], dense[0][:, ~hid], rtol=1e-14, atol=1e-15)
+        idx = np.nonzero(vis)[0]
+        for k in range(P):
+            tp[k].grad = torch.sparse_coo_tensor(torch.tensor(idx)[None], torch.tensor(g[k, idx]), (n,))
+            opts[k].step()
+    for k in range(P):
+        np.testing.assert_allclose(p[k], tp[k].detach().numpy(), rtol=1e-9, atol=1e-12)
