@@ -205,14 +205,14 @@ class Trainer:
         self.loss = torch.zeros(1, device=device)
         self.t = 0
 
-    def step(self, cams, target, img, dimg):
+    def step(self, cams, target, img, dimg, hp=HP):
         c = self.ctx
         c.gs_project(self.p, self.n, self.deg, cams)
         c.gs_bin_sort()
         c.gs_raster_fwd_l1(img, target, self.loss, dimg)
         c.gs_raster_bwd(self.p, self.n, self.deg, dimg, self.g)
         self.t += 1
-        c.gs_adam(self.p, self.g, self.m, self.v, self.n, self.deg, HP, self.t)
+        c.gs_adam(self.p, self.g, self.m, self.v, self.n, self.deg, hp, self.t)
 
 
 def replica_batches(rank, world, nbatch, count):
@@ -471,6 +471,27 @@ def gpu_arm(args):
                 "peak_source": "%d SMs (device attribute) x 128 FP32 lanes x 2 x max SM clock "
                                "(MEASURED_PEAKS sm_max_mhz)" % sms}
 
+    # the visible-only Adam variant (off by default: it changes the
+    # optimisation): the same steps call by call, with the fraction of
+    # Gaussians that touch a tile in some view of the batch
+    ctx.profile_reset()
+    ctx.profile_enable(True)
+    vis_frac = []
+    for i in range(args.steps):
+        tr.step(*batch(args.warmup + i), img, dimg, hp=dict(HP, visible_only=True))
+        vm = ctx.gs_get_buffer(gs.GS_BUF_VISMASK)
+        vis_frac.append(float((vm != 0).float().mean().item()))
+    ctx.profile_enable(False)
+    vk = {k["name"]: k for k in ctx.profile_read()}
+    ctx.gs_sync()
+    visible_only = {"visible_fraction": round(statistics.mean(vis_frac), 4),
+                    "adam_ms": round(vk["adam"]["total_ms"] / args.steps, 3),
+                    "project_bwd_ms": round(vk["project_bwd"]["total_ms"] / args.steps, 3),
+                    "dense_adam_ms": round(per_kernel["adam"]["ms"] / args.steps, 3),
+                    "dense_project_bwd_ms": round(per_kernel["project_bwd"]["ms"] / args.steps, 3),
+                    "note": "per B-view step; the projection backward reads only the views where a Gaussian "
+                            "touches a tile in both modes"}
+
     # plain path: one view per launch, Adam after each view
     ctx2 = gs.Context(local)
     tr2 = Trainer(ctx2, trained, dev)
@@ -537,7 +558,7 @@ def gpu_arm(args):
                  "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
         "instances_per_step": int(inst), "pair_entries_per_step": int(pairs[0]),
         "contributing_pairs_per_step": int(pairs[1]), "sort_passes_executed": executed,
-        "kernels": per_kernel,
+        "kernels": per_kernel, "visible_only_adam": visible_only,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
         "memory": memory,
     }

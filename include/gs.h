@@ -90,14 +90,19 @@ typedef struct {
 /* Adam hyper-parameters: one learning rate per parameter group.  flags:
  * GS_ADAM_SQRT_BATCH_LR multiplies every learning rate by sqrt(B), B = views
  * of the context's last projected batch (the learning-rate scaling batched
- * 3D-GS trainers such as Grendel-GS apply; off by default). */
+ * 3D-GS trainers such as Grendel-GS apply; off by default).
+ * GS_ADAM_VISIBLE_ONLY is the sparse (visible-only) variant 3D-GS trainers
+ * use: a Gaussian that touches no tile in any view of the context's last
+ * projected batch keeps its parameters and both moments unchanged (no decay);
+ * every other Gaussian takes the usual step, bias-corrected by the global
+ * step count.  Off by default: it changes the optimisation trajectory. */
 typedef struct {
   float lr_mean, lr_scale, lr_quat, lr_opacity, lr_sh_dc, lr_sh_rest;
   float beta1, beta2, eps;
   int32_t flags;
 } gs_adam_hp;
 
-enum { GS_ADAM_SQRT_BATCH_LR = 1 };
+enum { GS_ADAM_SQRT_BATCH_LR = 1, GS_ADAM_VISIBLE_ONLY = 2 };
 
 /* ---------------------------------------------------------------- context */
 
@@ -248,9 +253,11 @@ gs_status gs_l1_loss_noalloc(const float* x, const float* y, int64_t count, floa
                              void* stream);
 
 /* Step 5, Adam with bias correction (torch.optim.Adam semantics), dense over
- * all planes, per-group learning rate; step counts from 1.  p, m, v are
- * updated in place; g is read.  All four share n, stride and degree.
- * Errors: GS_EINVAL (mismatched sets, step < 1), GS_ECUDA. */
+ * all planes (or visible-only, see gs_adam_hp), per-group learning rate;
+ * step counts from 1.  p, m, v are updated in place; g is read.  All four
+ * share n, stride and degree.  Errors: GS_EINVAL (mismatched sets,
+ * step < 1), GS_ESTATE (visible-only without a gs_project of a set of the
+ * same n and stride), GS_ECUDA. */
 gs_status gs_adam(gs_ctx* ctx, gs_params* p, const gs_params* g, gs_params* m, gs_params* v,
                   const gs_adam_hp* hp, int64_t step);
 
@@ -392,9 +399,11 @@ typedef enum {
                         then [B][N][4] records dL/d(r, g, b), 0 */
   GS_BUF_REC3 = 9,   /* int4 [B][N]: radius, tiles touched (0: culled), tile rect
                         x0 | x1 << 16 and y0 | y1 << 16 (half-open) */
-  GS_BUF_SORT_CTRL = 10 /* uint32 [npass + 1]: control word of each sort pass; bit 1
+  GS_BUF_SORT_CTRL = 10, /* uint32 [npass + 1]: control word of each sort pass; bit 1
                         set = pass skipped (its digit is the same for every key),
                         bit 0 = source buffer */
+  GS_BUF_VISMASK = 11 /* uint64 [N]: bit v = the Gaussian touches a tile of view v
+                        of the last projected batch */
 } gs_buffer;
 
 /* *ptr = device pointer of the buffer, *count = number of elements (of the

@@ -75,7 +75,7 @@ struct gs_ctx {
 
   DevBuf views, rec, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
-      target_slot, host_tgt0, host_tgt1, pair_stats, cells;
+      target_slot, host_tgt0, host_tgt1, pair_stats, cells, vismask;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -290,6 +290,7 @@ gs_status ctx_reserve(gs_ctx* c, int64_t stride, int B, int64_t bins, int64_t pi
   GS_TRY(ensure_exact(c, c->rec3, sizeof(int4) * B * stride));
   GS_TRY(ensure_exact(c, c->tiles, sizeof(uint2) * B * stride));
   GS_TRY(ensure_exact(c, c->block_sums, sizeof(uint32_t) * B * nb));
+  GS_TRY(ensure_exact(c, c->vismask, sizeof(uint64_t) * stride));
   GS_TRY(ensure_exact(c, c->block_offsets, sizeof(uint32_t) * B * nb));
   GS_TRY(ensure_exact(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
                                  sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
@@ -370,7 +371,7 @@ void gs_destroy(gs_ctx* c) {
                     &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->hist_scan,
                     &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
                     &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1,
-                    &c->pair_stats, &c->cells};
+                    &c->pair_stats, &c->cells, &c->vismask};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -433,6 +434,8 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   GS_TRY(ensure(c, c->rec3, sizeof(int4) * B * stride));
   GS_TRY(ensure(c, c->tiles, sizeof(uint2) * B * stride));
   GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * B * nb));
+  GS_TRY(ensure(c, c->vismask, sizeof(uint64_t) * stride));
+  GS_CUDA(c, cudaMemsetAsync(c->vismask.p, 0, sizeof(uint64_t) * stride, c->stream));
   if (c->capturing) {
     // a captured step copies the cameras from the pinned staging area at its start
   } else {
@@ -451,6 +454,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   a.rec3 = P<int4>(c->rec3);
   a.tiles = P<uint2>(c->tiles);
   a.block_sums = P<uint32_t>(c->block_sums);
+  a.vismask = P<uint64_t>(c->vismask);
   {
     LaunchScope ls(c, "project_fwd");
     launch_project_fwd(a, params->sh_degree, c->stream);
@@ -695,6 +699,7 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   b.B = c->B;
   b.g2d = P<float>(c->g2d);
   b.grads = grads->data;
+  b.vismask = P<uint64_t>(c->vismask);
   if (grads->stride > grads->n) {
     // padding columns are not written by the kernel; keep them zero
     GS_CUDA(c, cudaMemsetAsync(grads->data, 0, sizeof(float) * n_planes(c->deg) * grads->stride, c->stream));
@@ -757,6 +762,12 @@ gs_status gs_adam(gs_ctx* c, gs_params* p, const gs_params* g, gs_params* m, gs_
   a.beta1 = hp->beta1;
   a.beta2 = hp->beta2;
   a.eps = hp->eps;
+  if (hp->flags & GS_ADAM_VISIBLE_ONLY) {
+    // the visibility of the context's last projected batch
+    if (!c->vismask.p || c->n != p->n || c->stride != p->stride)
+      return fail(c, GS_ESTATE, "visible-only Adam needs gs_project of the same set first");
+    a.vismask = P<uint64_t>(c->vismask);
+  }
   {
     LaunchScope ls(c, "adam");
     launch_adam(a, c->stream);
@@ -793,6 +804,7 @@ gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
     case GS_BUF_TFINAL: if (!c->rastered) return GS_ESTATE; *ptr = c->tfinal.p; *count = c->pixels; break;
     case GS_BUF_NLAST: if (!c->rastered) return GS_ESTATE; *ptr = c->nlast.p; *count = c->pixels; break;
     case GS_BUF_G2D: if (!c->g2d.p) return GS_ESTATE; *ptr = c->g2d.p; *count = (kG2dGeo + kG2dCol) * bn; break;
+    case GS_BUF_VISMASK: if (!c->projected) return GS_ESTATE; *ptr = c->vismask.p; *count = c->n; break;
     case GS_BUF_SORT_CTRL:
       if (!c->sorted) return GS_ESTATE;
       *ptr = reinterpret_cast<uint32_t*>(P<uint64_t>(c->total) + 1 + kMaxViews) + 2 * (kMaxViews + 1);

@@ -19,6 +19,7 @@ struct ProjectArgs {
   int4* rec3;            // (radius, tiles, x0 | x1 << 16, y0 | y1 << 16) per (view, Gaussian)
   uint2* tiles;          // [B][stride]: (tiles touched, bits of the depth)
   uint32_t* block_sums;  // [B][ceil(n / block)] instance counts per view and block
+  uint64_t* vismask;     // [stride]: bit v = the Gaussian touches a tile of view v
 };
 
 struct ProjectBwdArgs {
@@ -28,6 +29,7 @@ struct ProjectBwdArgs {
   int B;
   const float* g2d;   // [B][stride] geometry records (kG2dGeo floats), then [B][stride] colour records (kG2dCol)
   float* grads;       // [P][stride]
+  const uint64_t* vismask;  // [stride] views where the Gaussian touches a tile (others: zero 2D gradient)
 };
 
 struct DuplicateArgs {
@@ -145,6 +147,7 @@ struct AdamArgs {
   int planes;
   const float* consts;  // device: [64] per-plane lr / (1 - beta1^t), [64] = 1 / sqrt(1 - beta2^t)
   float beta1, beta2, eps;
+  const uint64_t* vismask;  // visible-only update: Gaussians with mask 0 keep p, m, v (NULL: dense)
 };
 void launch_adam(const AdamArgs& a, cudaStream_t s);
 

@@ -72,8 +72,12 @@ void launch_l1(const float* x, const float* y, const float* const* y_slot, int64
   if (loss) l1_finish_kernel<<<1, 32, 0, s>>>(partial, nparts, 1.0 / (double)count, loss);
 }
 
-// Adam over [planes][stride] float planes, float4 at a time (stride % 4 == 0,
-// so a vector never straddles two planes).
+// Adam over [planes][stride] float planes.  A thread owns one float4 column
+// (4 consecutive Gaussians) and walks the planes, so the per-plane learning
+// rate is uniform across the warp and, in the visible-only variant, the
+// column's visibility is read once: a column of 4 invisible Gaussians reads
+// and writes nothing; otherwise invisible lanes write their values back
+// unchanged.
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   // step-dependent constants come from device memory, so the launch can be
   // captured once and replayed for any step
@@ -83,32 +87,47 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   if (threadIdx.x == 0) isb2_s = a.consts[64];
   __syncthreads();
   const float inv_sqrt_bc2 = isb2_s;
-  const int64_t n4 = (int64_t)a.planes * a.stride / 4;
-  const int64_t per_plane4 = a.stride / 4;
+  const int64_t cols = a.stride / 4;
   float4* p4 = reinterpret_cast<float4*>(a.p);
   const float4* g4 = reinterpret_cast<const float4*>(a.g);
   float4* m4 = reinterpret_cast<float4*>(a.m);
   float4* v4 = reinterpret_cast<float4*>(a.v);
   const float b1 = a.beta1, b2 = a.beta2, c1 = 1.f - a.beta1, c2 = 1.f - a.beta2;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-    const float lr = lr_s[i / per_plane4];
-    const float4 g = g4[i];
-    float4 m = m4[i], v = v4[i], p = p4[i];
-#define ADAM_LANE(f)                                                  \
+  for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    bool on[4] = {true, true, true, true};
+    if (a.vismask) {
+      const ulonglong2 q0 = reinterpret_cast<const ulonglong2*>(a.vismask)[2 * col];
+      const ulonglong2 q1 = reinterpret_cast<const ulonglong2*>(a.vismask)[2 * col + 1];
+      on[0] = q0.x != 0ull;
+      on[1] = q0.y != 0ull;
+      on[2] = q1.x != 0ull;
+      on[3] = q1.y != 0ull;
+      if (!(on[0] || on[1] || on[2] || on[3])) continue;
+    }
+    for (int pl = 0; pl < a.planes; pl++) {
+      const int64_t i = pl * cols + col;
+      const float lr = lr_s[pl];
+      const float4 g = g4[i];
+      const float4 m0 = m4[i], v0 = v4[i], p0 = p4[i];
+      float4 m = m0, v = v0, p = p0;
+#define ADAM_LANE(f, k)                                               \
   m.f = fmaf(b1, m.f, c1 * g.f);                                      \
   v.f = fmaf(b2, v.f, c2 * g.f * g.f);                                \
-  p.f -= lr * m.f / fmaf(sqrtf(v.f), inv_sqrt_bc2, a.eps);
-    ADAM_LANE(x) ADAM_LANE(y) ADAM_LANE(z) ADAM_LANE(w)
+  p.f -= lr * m.f / fmaf(sqrtf(v.f), inv_sqrt_bc2, a.eps);            \
+  if (!on[k]) { m.f = m0.f; v.f = v0.f; p.f = p0.f; }
+      ADAM_LANE(x, 0) ADAM_LANE(y, 1) ADAM_LANE(z, 2) ADAM_LANE(w, 3)
 #undef ADAM_LANE
-    m4[i] = m;
-    v4[i] = v;
-    p4[i] = p;
+      m4[i] = m;
+      v4[i] = v;
+      p4[i] = p;
+    }
   }
 }
 
 void launch_adam(const AdamArgs& a, cudaStream_t s) {
-  const int64_t n4 = (int64_t)a.planes * a.stride / 4;
-  int64_t blocks = (n4 + 255) / 256;
+  const int64_t cols = a.stride / 4;
+  int64_t blocks = (cols + 255) / 256;
   const int64_t most = (int64_t)sm_count() * 16;
   if (blocks > most) blocks = most;
   if (blocks < 1) blocks = 1;

@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
   __shared__ uint32_t s_bsum[kMaxViews];          // the block's instance count per view
   for (int i = threadIdx.x; i < a.B; i += blockDim.x) s_bsum[i] = 0;
   __syncthreads();
+  uint64_t vis = 0;  // views where the Gaussian touches a tile
   for (int v = 0; v < a.B; v++) {
     const ViewRec& V = a.views[v];
     const int64_t o = (int64_t)v * a.stride + g;
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
       }
       a.rec3[o] = make_int4(tiles ? radius : 0, (int)tiles, x0 | (x1 << 16), y0 | (y1 << 16));
       a.tiles[o] = make_uint2(tiles, __float_as_uint(depth));
+      vis |= tiles ? 1ull << v : 0ull;
     }
     // the warp's 32 records (48 bytes each) go out through shared memory as
     // 96 coalesced 16-byte stores instead of 3 x 32 stores at a 48-byte stride
@@ -258,6 +260,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
     const uint32_t wt = __reduce_add_sync(0xffffffffu, tiles);
     if (lane == 0 && wt) atomicAdd(&s_bsum[v], wt);
   }
+  if (live) a.vismask[g] = vis;
   // the block's instance count per view (for the per-view scans)
   __syncthreads();
   for (int i = threadIdx.x; i < a.B; i += blockDim.x)
@@ -283,13 +286,16 @@ __global__ void __launch_bounds__(96) project_bwd_color_kernel(ProjectBwdArgs a)
   const bool live = g < a.n;
   const float* P = a.params;
   const int64_t S = a.stride;
+  // only the views where the Gaussian touches a tile have a nonzero 2D
+  // gradient: the others (and Gaussians invisible in every view) read nothing
+  uint64_t vm = live ? a.vismask[g] : 0ull;
   float mean[3] = {0.f, 0.f, 0.f}, sh[K], gsh[K];
 #pragma unroll
   for (int k = 0; k < K; k++) {
-    sh[k] = live ? __ldg(P + (11 + 3 * k + c) * S + g) : 0.f;
+    sh[k] = vm ? __ldg(P + (11 + 3 * k + c) * S + g) : 0.f;
     gsh[k] = 0.f;
   }
-  if (live) {
+  if (vm) {
 #pragma unroll
     for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
   }
@@ -297,11 +303,15 @@ __global__ void __launch_bounds__(96) project_bwd_color_kernel(ProjectBwdArgs a)
   // dL/d(channel c) in the colour record of (view v, Gaussian g)
   const float* gch = a.g2d + kG2dGeo * (int64_t)a.B * S + kG2dCol * g + c;
   const int64_t vstep = kG2dCol * S;
-  // the next view's gradient is loaded while this view is processed
-  float nxt = live ? __ldg(gch) : 0.f;
-  for (int v = 0; v < a.B; v++) {
+  // the next visible view's gradient is loaded while this view is processed
+  int vn = vm ? __ffsll((long long)vm) - 1 : -1;
+  float nxt = vn >= 0 ? __ldg(gch + (int64_t)vn * vstep) : 0.f;
+  while (vn >= 0) {
+    const int v = vn;
     const float gc_in = nxt;
-    if (live && v + 1 < a.B) nxt = __ldg(gch + (int64_t)(v + 1) * vstep);
+    vm &= vm - 1;
+    vn = vm ? __ffsll((long long)vm) - 1 : -1;
+    if (vn >= 0) nxt = __ldg(gch + (int64_t)vn * vstep);
     if (gc_in == 0.f) continue;
     const ViewRec& V = a.views[v];
     // rgb_c = max(0, 0.5 + sum_k sh_kc Y_k(d)), d = (mu - campos) / |mu - campos|
@@ -349,6 +359,14 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
   if (g >= a.n) return;
   const float* P = a.params;
   const int64_t S = a.stride;
+  uint64_t vm = a.vismask[g];
+  float* G = a.grads;
+  if (!vm) {  // no tile in any view: every gradient of this Gaussian is zero
+    // (the mean planes were written by the colour part)
+#pragma unroll
+    for (int i = 3; i < 11; i++) G[i * S + g] = 0.f;
+    return;
+  }
   float mean[3], lsc[3], quat[4];
 #pragma unroll
   for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
@@ -373,9 +391,13 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
     q[0] = x.x; q[1] = x.y; q[2] = x.z; q[3] = x.w; q[4] = y.x; q[5] = y.y;
   };
   float cur[6], nxt[6];
-  load6(0, cur);
-  for (int v = 0; v < a.B; v++) {
-    if (v + 1 < a.B) load6(v + 1, nxt);
+  int vn = __ffsll((long long)vm) - 1;
+  load6(vn, cur);
+  while (vn >= 0) {  // the views where the Gaussian touches a tile
+    const int v = vn;
+    vm &= vm - 1;
+    vn = vm ? __ffsll((long long)vm) - 1 : -1;
+    if (vn >= 0) load6(vn, nxt);
     const float gmx = cur[0], gmy = cur[1], gA = cur[2], gB = cur[3], gC = cur[4], gsig = cur[5];
 #pragma unroll
     for (int q = 0; q < 6; q++) cur[q] = nxt[q];
@@ -466,7 +488,6 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
   gqn[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] +
                   y * gR[7]);
   const float dq = gqn[0] * gc.qn[0] + gqn[1] * gc.qn[1] + gqn[2] * gc.qn[2] + gqn[3] * gc.qn[3];
-  float* G = a.grads;
 #pragma unroll
   for (int i = 0; i < 3; i++) G[i * S + g] += gm[i];
 #pragma unroll

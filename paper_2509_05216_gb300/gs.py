@@ -22,7 +22,7 @@ _NAMES = ["GS_OK", "GS_EINVAL", "GS_ENOMEM", "GS_ECUDA", "GS_ECAPACITY", "GS_ETI
           "GS_EAGAIN", "GS_ESTATE"]
 
 (GS_BUF_REC0, GS_BUF_REC1, GS_BUF_REC2, GS_BUF_KEYS, GS_BUF_VALS, GS_BUF_RANGES, GS_BUF_TFINAL,
- GS_BUF_NLAST, GS_BUF_G2D, GS_BUF_REC3, GS_BUF_SORT_CTRL) = range(11)
+ GS_BUF_NLAST, GS_BUF_G2D, GS_BUF_REC3, GS_BUF_SORT_CTRL, GS_BUF_VISMASK) = range(12)
 LOG2E = 1.4426950408889634
 
 
@@ -56,15 +56,18 @@ class gs_adam_hp(ctypes.Structure):
 
 
 GS_ADAM_SQRT_BATCH_LR = 1
+GS_ADAM_VISIBLE_ONLY = 2
 
 
 def adam_hp_struct(hp: dict) -> gs_adam_hp:
     """hp: lr_mean, lr_scale, lr_quat, lr_opacity, lr_sh_dc, lr_sh_rest, and
-    optionally beta1, beta2, eps and sqrt_batch_lr (scale the rates by
-    sqrt(views per batch))."""
+    optionally beta1, beta2, eps, sqrt_batch_lr (scale the rates by
+    sqrt(views per batch)) and visible_only (the sparse, visible-only step)."""
+    flags = (GS_ADAM_SQRT_BATCH_LR if hp.get("sqrt_batch_lr", False) else 0) | \
+        (GS_ADAM_VISIBLE_ONLY if hp.get("visible_only", False) else 0)
     return gs_adam_hp(hp["lr_mean"], hp["lr_scale"], hp["lr_quat"], hp["lr_opacity"], hp["lr_sh_dc"],
                       hp["lr_sh_rest"], hp.get("beta1", 0.9), hp.get("beta2", 0.999), hp.get("eps", 1e-15),
-                      GS_ADAM_SQRT_BATCH_LR if hp.get("sqrt_batch_lr", False) else 0)
+                      flags)
 
 
 class gs_kernel_stat(ctypes.Structure):
@@ -333,7 +336,7 @@ class Context:
         spec = {GS_BUF_REC0: ((n, 4), "<f4"), GS_BUF_REC1: ((n, 4), "<f4"), GS_BUF_REC2: ((n, 4), "<f4"),
                 GS_BUF_KEYS: ((n,), "<i8"), GS_BUF_VALS: ((n,), "<i4"), GS_BUF_RANGES: ((n, 2), "<i4"),
                 GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((n,), "<f4"), GS_BUF_REC3: ((n, 4), "<i4"),
-                GS_BUF_SORT_CTRL: ((n,), "<i4")}[which]
+                GS_BUF_SORT_CTRL: ((n,), "<i4"), GS_BUF_VISMASK: ((n,), "<i8")}[which]
         if n == 0:
             return torch.empty(spec[0], device="cuda:%d" % self.device,
                                dtype={"<f4": torch.float32, "<i8": torch.int64, "<i4": torch.int32}[spec[1]])

@@ -525,6 +525,53 @@ def test_adam_matches_oracle(ctx, oracle):
     np.testing.assert_allclose(m.cpu().numpy(), m64, rtol=1e-5, atol=1e-7)
 
 
+def test_visible_only_adam_matches_oracle(ctx, oracle):
+    """Visible-only Adam after a narrow-field projection: Gaussians that touch
+    no tile in either view keep p, m and v; the others match the oracle's
+    Adam step.  The visibility mask equals the oracle's tile counts away from
+    marginal rects."""
+    rng = np.random.default_rng(14)
+    scene = inputs.random_scene(3001, 2, 17, extent=1.5)
+    P, stride = scene["params"].shape
+    n = scene["n"]
+    cams = [inputs.pinhole(inputs.look_at((2.5, 1.0, 0.5), target=(0.8, 0.6, 0.4)), 96, 80, fov_x_deg=25.0),
+            inputs.pinhole(inputs.look_at((-0.5, -2.6, 0.9), target=(-0.6, 0.5, -0.5)), 64, 64, fov_x_deg=25.0)]
+    p = torch.from_numpy(scene["params"]).cuda()
+    ctx.gs_project(p, n, scene["deg"], cams)
+    ctx.gs_sync()
+    vm = ctx.gs_get_buffer(gs.GS_BUF_VISMASK).cpu().numpy().astype(np.int64)
+    vis = (vm != 0).astype(np.uint8)
+    ref_vis = oracle.visible_in_batch(scene, cams)
+    marg = np.zeros(n, bool)
+    for c in cams:
+        marg |= (oracle.gaussian_flags(scene, c) & (oracle.G_MARG_RECT | oracle.G_MARG_ZNEAR)) != 0
+    assert np.array_equal(vis[~marg], ref_vis[~marg])
+    assert 0.1 < vis.mean() < 0.9
+    for v, c in enumerate(cams):  # bit v = touches a tile of view v
+        t = oracle.project(scene, c)["tiles"] > 0
+        assert np.array_equal(((vm >> v) & 1).astype(bool)[~marg], t[~marg])
+    hp = dict(lr_mean=1.6e-4, lr_scale=5e-3, lr_quat=1e-3, lr_opacity=0.05, lr_sh_dc=2.5e-3,
+              lr_sh_rest=2.5e-3 / 20, beta1=0.9, beta2=0.999, eps=1e-15, visible_only=True)
+    lr_planes = np.array([hp["lr_mean"]] * 3 + [hp["lr_scale"]] * 3 + [hp["lr_quat"]] * 4 + [hp["lr_opacity"]]
+                         + [hp["lr_sh_dc"]] * 3 + [hp["lr_sh_rest"]] * (P - 14))
+    m0 = rng.normal(size=(P, stride)).astype(np.float32) * 1e-3
+    v0 = np.abs(rng.normal(size=(P, stride))).astype(np.float32) * 1e-6
+    m, v = torch.from_numpy(m0).cuda(), torch.from_numpy(v0).cuda()
+    p64, m64, v64 = scene["params"].astype(np.float64), m0.astype(np.float64), v0.astype(np.float64)
+    for step in range(1, 4):
+        g = rng.normal(size=(P, stride)).astype(np.float32)
+        g[:, n:] = 0
+        ctx.gs_adam(p, torch.from_numpy(g).cuda(), m, v, n, scene["deg"], hp, step)
+        oracle.adam_visible(p64, g.astype(np.float64), m64, v64, lr_planes, step, vis, n=n)
+    ctx.gs_sync()
+    pg, mg, vg = p.cpu().numpy(), m.cpu().numpy(), v.cpu().numpy()
+    hid = vis == 0
+    assert np.array_equal(pg[:, :n][:, hid], scene["params"][:, :n][:, hid])
+    assert np.array_equal(mg[:, :n][:, hid], m0[:, :n][:, hid]) and np.array_equal(vg[:, :n][:, hid], v0[:, :n][:, hid])
+    np.testing.assert_allclose(pg[:, :n], p64[:, :n], rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(mg[:, :n], m64[:, :n], rtol=1e-5, atol=1e-8)
+
+
 def test_adam_sqrt_batch_lr_scaling(ctx, oracle):
     """The optional sqrt(B) learning-rate scaling of batched training: after a
     3-view projection the step equals plain Adam with the rates times sqrt 3."""
