@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2509_05216_gb300 import gs, inputs
+from paper_2509_05216_gb300 import autograd, gs, inputs
 from tests.gpu_helpers import expected_binning, rel_l2, to_dev_images
 
 pytestmark = pytest.mark.gpu
@@ -124,3 +124,68 @@ def test_fullsize_sampled_gradient_matches_oracle(c3, oracle):
     others = np.ones(n, bool)
     others[touched] = False
     assert np.abs(g[:, :n][:, others]).max() == 0.0
+
+
+def test_fullsize_autograd_central_differences_on_32_parameters(c3, oracle):
+    """The autograd backward at the benchmark's scale (4M Gaussians, two
+    2048 x 2048 views) against FP32 central differences of the CUDA forward on
+    32 sampled parameters of Gaussians visible and non-marginal in both
+    views; the weighted image difference is summed in FP64."""
+    scene, p0 = c3["scene"], c3["p"]
+    cams = [c3["cams"][2], c3["cams"][9]]
+    n = scene["n"]
+    ctx = gs.Context(0)
+    try:
+        p = p0.detach().clone().requires_grad_(True)
+        rng = np.random.default_rng(21)
+        _, total = gs.image_offsets(cams)
+        w = torch.from_numpy(rng.normal(size=total).astype(np.float32)).cuda()
+        img = autograd.rasterize(p, n, scene["deg"], cams, ctx)
+        (img * w).sum().backward()
+        g = p.grad.cpu().numpy()
+        vm = ctx.gs_get_buffer(gs.GS_BUF_VISMASK).cpu().numpy().astype(np.int64)
+        cand = rng.choice(np.nonzero(vm == 3)[0], size=1500, replace=False)
+        sub = {"params": np.ascontiguousarray(scene["params"][:, cand]), "n": cand.size, "deg": scene["deg"]}
+        ok = np.ones(cand.size, bool)
+        for cam in cams:
+            f = oracle.gaussian_flags(sub, cam)
+            ok &= ((f & oracle.G_VISIBLE) != 0) & ((f & oracle.G_MARG_ANY_GRAD) == 0)
+        # Gaussians that reach some pixel: a nonzero gradient in the colour planes
+        cand = [int(c) for c in cand[ok] if np.abs(g[11:14, c]).sum() > 0]
+        assert len(cand) >= 32
+        planes = [0, 1, 2, 3, 5, 6, 8, 10, 11, 13, 20, 40]
+        picks = [(planes[i % len(planes)], cand[i]) for i in range(32)]
+        w64 = w.double()
+
+        def fd(pl, gi, h):
+            base = float(p[pl, gi])
+            outs = []
+            for sgn in (1.0, -1.0):
+                q = p.detach().clone()
+                q[pl, gi] = base + sgn * h
+                ctx.gs_project(q, n, scene["deg"], cams)
+                ctx.gs_bin_sort()
+                o = torch.empty(total, device="cuda")
+                ctx.gs_raster_fwd(o)
+                outs.append(o)
+            return float(((outs[0].double() - outs[1].double()) * w64).sum()) / (2 * h)
+
+        errs, kept = [], 0
+        with torch.no_grad():
+            for pl, gi in picks:
+                h = 1e-3 * max(1.0, abs(float(p[pl, gi])))
+                f1, f2 = fd(pl, gi, h), fd(pl, gi, h / 2)
+                scale = max(abs(f1), abs(f2), 1e-2)
+                # a step that crosses a rect, skip or stop decision shows as
+                # disagreement between h and h / 2
+                if abs(f1 - f2) > 0.05 * scale:
+                    continue
+                kept += 1
+                an = float(g[pl, gi])
+                errs.append(abs(f2 - an) / max(abs(an), abs(f2), 1e-2))
+        errs = np.array(errs)
+        assert kept >= 24
+        assert np.median(errs) <= 1e-2
+        assert np.mean(errs <= 5e-2) >= 0.9
+    finally:
+        ctx.close()

@@ -1,0 +1,137 @@
+"""The Miranda-scale configuration on one GPU (GPU only): 18,000,000 Gaussians
+on the zero level of 6-octave fractal noise, SH degree 3, B = 4 views of
+4096 x 4096 -- the size whose training does not fit a single A100 in the
+paper (Results, Table I).  Checks: the whole training step captured in a
+CUDA graph runs, and its device memory (cudaMemGetInfo deltas: parameters,
+gradients, Adam moments, the step's workspace and images) is reported and
+fits; binning is bit-exact on one whole view; sampled pixels and the
+gradient of a loss supported on a few tiles match the oracle."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_05216_gb300 import gs, inputs
+from tests.gpu_helpers import expected_binning, rel_l2, to_dev_images
+
+pytestmark = pytest.mark.gpu
+
+N = 18_000_000
+B = 4
+RES = 4096
+HP = dict(lr_mean=1.6e-4, lr_scale=5e-3, lr_quat=1e-3, lr_opacity=0.05, lr_sh_dc=2.5e-3,
+          lr_sh_rest=2.5e-3 / 20, beta1=0.9, beta2=0.999, eps=1e-15)
+
+
+@pytest.fixture(scope="module")
+def c4():
+    cache = os.environ.get("GS_SCENE_CACHE", "/tmp/gs_scene_cache")
+    os.makedirs(cache, exist_ok=True)
+    path = os.path.join(cache, "noise_scene_n%d_s5.npz" % N)
+    if os.path.exists(path):
+        z = np.load(path)
+        scene = {"params": z["params"], "n": int(z["n"]), "deg": int(z["deg"])}
+    else:
+        scene = inputs.noise_scene(N, seed=5, deg=3, res=256)
+        tmp = path + ".%d.tmp.npz" % os.getpid()
+        np.savez(tmp, params=scene["params"], n=scene["n"], deg=scene["deg"])
+        os.replace(tmp, path)
+    trained = inputs.perturb(scene, 105)
+    cams = inputs.orbit_cameras(16, 16, 4.0, RES, RES)[7 * B:8 * B]
+    ctx = gs.Context(0)
+    p = torch.from_numpy(trained["params"]).cuda()
+    ctx.gs_project(p, trained["n"], trained["deg"], cams)
+    ctx.gs_bin_sort()
+    _, total = gs.image_offsets(cams)
+    img = torch.empty(total, device="cuda")
+    ctx.gs_raster_fwd(img)
+    ctx.gs_sync()
+    inst = ctx.gs_get_counts()[0]
+    yield {"scene": trained, "cams": cams, "ctx": ctx, "p": p, "img": img, "instances": inst, "total": total}
+    ctx.close()
+
+
+def test_c4_training_step_runs_in_a_graph_and_fits(c4):
+    scene, cams, total = c4["scene"], c4["cams"], c4["total"]
+    torch.cuda.synchronize()
+    free0, hbm = torch.cuda.mem_get_info()
+    p = c4["p"].clone()
+    g, m, v = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    tgt = c4["img"].clone()
+    img, dimg, loss = torch.empty(total, device="cuda"), torch.empty(total, device="cuda"), torch.zeros(1, device="cuda")
+    gctx = gs.Context(0, instance_capacity=int(c4["instances"] * 1.3) + (1 << 20))
+    try:
+        gctx.gs_train_graph_capture(p, g, m, v, scene["n"], scene["deg"], HP, cams, tgt, img, dimg, loss)
+        for step in (1, 2):
+            gctx.gs_train_graph_launch(cams, tgt, step)
+        gctx.gs_sync()
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        used = free0 - free1
+        state = 4 * p.numel() * 4
+        print("C4 one training step: %.1f GB on the device (%.1f GB parameters, gradients and Adam moments), "
+              "%d instances" % (used / 1e9, state / 1e9, c4["instances"]))
+        assert np.isfinite(loss.item()) and loss.item() > 0
+        assert state >= 16.9e9
+        assert used < 0.5 * hbm
+    finally:
+        gctx.close()
+
+
+def test_c4_binning_bit_exact_on_one_view(c4):
+    ctx, cams, n = c4["ctx"], c4["cams"], c4["scene"]["n"]
+    stride = c4["scene"]["params"].shape[1]
+    r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
+    r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+    r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
+    v = 1
+    sub = slice(v * stride, (v + 1) * stride)
+    keys, vals, ranges, _ = expected_binning(r0[sub], r2[sub], r3[sub], [cams[v]], n, stride)
+    del r0, r2, r3
+    tiles = (RES // 16) ** 2
+    keys = keys + (np.uint64(v * tiles) << np.uint64(32))
+    gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)[v * tiles:(v + 1) * tiles]
+    first = int(gr[gr[:, 1] > gr[:, 0], 0].min())
+    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)[first:first + keys.size]
+    assert np.array_equal(gk, keys)
+    del gk
+    gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy()[first:first + vals.size].astype(np.int64)
+    assert np.array_equal(gv, vals)
+    assert np.array_equal(gr, np.where(ranges[:, 1:] > ranges[:, :1], ranges + first, 0))
+
+
+def test_c4_sampled_pixels_and_gradient_match_oracle(c4, oracle):
+    ctx, cams, scene, p = c4["ctx"], c4["cams"], c4["scene"], c4["p"]
+    rng = np.random.default_rng(12)
+    views = gs.split_images(c4["img"], cams)
+    checked = 0
+    for v in (0, 3):
+        xs = rng.integers(0, RES, size=10)
+        ys = rng.integers(0, RES, size=10)
+        ref, _, marg = oracle.render_pixels(scene, cams[v], xs, ys)
+        got = views[v][:, ys, xs].T.cpu().numpy()
+        assert np.abs(got - ref)[~marg].max() <= 1e-4
+        checked += int((~marg).sum())
+    assert checked >= 15
+    # gradient of a loss on 3 tiles near the centre of view 2
+    v = 2
+    dimgs = [np.zeros((3, RES, RES), np.float32) for _ in cams]
+    for _ in range(3):
+        ty, tx = rng.integers(100, 156, size=2)
+        dimgs[v][:, 16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16] = rng.normal(size=(3, 16, 16))
+    yy, xx = np.nonzero(np.abs(dimgs[v]).sum(0) > 0)
+    _, _, mg = oracle.render_pixels(scene, cams[v], xx, yy)
+    dimgs[v][:, yy[mg], xx[mg]] = 0.0
+    grads = torch.zeros_like(p)
+    ctx.gs_raster_bwd(p, scene["n"], scene["deg"], to_dev_images(dimgs), grads)
+    ctx.gs_sync()
+    ref = oracle.render_grad(scene, [cams[v]], [dimgs[v].astype(np.float64)])
+    n = scene["n"]
+    touched = np.nonzero(np.abs(ref[:, :n]).sum(0) > 0)[0]
+    assert touched.size > 20
+    f = oracle.gaussian_flags({"params": np.ascontiguousarray(scene["params"][:, touched]), "n": touched.size,
+                               "deg": 3}, cams[v])
+    sel = touched[(f & oracle.G_MARG_ANY_GRAD) == 0]
+    g = grads[:, torch.from_numpy(sel).cuda()].cpu().numpy().astype(np.float64)
+    assert rel_l2(g, ref[:, sel]) <= 1e-3
