@@ -568,7 +568,9 @@ def test_visible_only_adam_matches_oracle(ctx, oracle):
     hid = vis == 0
     assert np.array_equal(pg[:, :n][:, hid], scene["params"][:, :n][:, hid])
     assert np.array_equal(mg[:, :n][:, hid], m0[:, :n][:, hid]) and np.array_equal(vg[:, :n][:, hid], v0[:, :n][:, hid])
-    np.testing.assert_allclose(pg[:, :n], p64[:, :n], rtol=1e-6, atol=1e-7)
+    # three steps of up to lr = 0.05 (opacity) each, every step rounded in
+    # FP32 (relative 2^-23 of the parameter and about 1e-6 of the step)
+    np.testing.assert_allclose(pg[:, :n], p64[:, :n], rtol=1e-6, atol=1e-6)
     np.testing.assert_allclose(mg[:, :n], m64[:, :n], rtol=1e-5, atol=1e-8)
 
 
