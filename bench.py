@@ -492,6 +492,24 @@ def gpu_arm(args):
                     "note": "per B-view step; the projection backward reads only the views where a Gaussian "
                             "touches a tile in both modes"}
 
+    # the D-SSIM loss term (optional; the default training loss is L1) and the
+    # paper's quality metrics on the last batch of those steps
+    _, last_t = batch(args.warmup + args.steps - 1)
+    dl = torch.zeros(1, device=dev)
+    ctx.gs_ssim_loss(img, last_t, 0.2, dl, dimg)
+    torch.cuda.synchronize(dev)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(5):
+        ctx.gs_ssim_loss(img, last_t, 0.2, dl, dimg)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    ssim_v, psnr_v = ctx.gs_image_metrics(img, last_t, B)
+    dssim = {"ms_per_step": round(s0.elapsed_time(s1) / 5, 3), "lambda": 0.2,
+             "ssim_mean": round(statistics.mean(ssim_v), 5), "psnr_mean_db": round(statistics.mean(psnr_v), 3),
+             "note": "D-SSIM loss and gradient over the B views (kernels ssim_fwd, finish, ssim_bwd); SSIM / PSNR "
+                     "of the trained set's render against the targets after the timed steps"}
+
     # plain path: one view per launch, Adam after each view
     ctx2 = gs.Context(local)
     tr2 = Trainer(ctx2, trained, dev)
@@ -558,7 +576,7 @@ def gpu_arm(args):
                  "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
         "instances_per_step": int(inst), "pair_entries_per_step": int(pairs[0]),
         "contributing_pairs_per_step": int(pairs[1]), "sort_passes_executed": executed,
-        "kernels": per_kernel, "visible_only_adam": visible_only,
+        "kernels": per_kernel, "visible_only_adam": visible_only, "dssim": dssim,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
         "memory": memory,
     }

@@ -252,6 +252,28 @@ gs_status gs_l1_loss(gs_ctx* ctx, const float* x, const float* y, int64_t count,
 gs_status gs_l1_loss_noalloc(const float* x, const float* y, int64_t count, float* loss, float* dL_dx,
                              void* stream);
 
+/* D-SSIM training loss of 3D-GS (the paper reports its renders by PSNR and
+ * SSIM, Results Tables II-III; the 3D-GS training it runs adds this term):
+ * over the views of the context's last projected batch (sizes as given to
+ * gs_project), with x = images and y = targets (device, image layout),
+ *   *loss = (1 - lambda) mean |x - y| + lambda (1 - mean SSIM)
+ * where SSIM is computed per channel with the 11 x 11 Gaussian window
+ * (sigma 1.5, zero padding at the image border, weights not renormalised),
+ * C1 = 0.01^2, C2 = 0.03^2, and both means run over every (view, channel,
+ * pixel).  dL_dimages (device, image layout, overwritten) receives the exact
+ * gradient of *loss (sign(0) = 0 in the L1 part).  Either output may be NULL
+ * (not both).  lambda = 0.2 is 3D-GS's choice.  Uses 12 bytes of scratch per
+ * image element.  Errors: GS_ESTATE (no gs_project), GS_EINVAL, GS_ENOMEM,
+ * GS_ECUDA. */
+gs_status gs_ssim_loss(gs_ctx* ctx, const float* images, const float* targets, float lambda, float* loss,
+                       float* dL_dimages);
+
+/* Quality metrics per view of the last projected batch: ssim[v] = mean SSIM
+ * (as in gs_ssim_loss) and psnr[v] = 10 log10(1 / mean (x - y)^2) over view
+ * v's channels and pixels (host arrays of B doubles; either may be NULL, not
+ * both).  Synchronises the stream.  Errors: as gs_ssim_loss. */
+gs_status gs_image_metrics(gs_ctx* ctx, const float* images, const float* targets, double* ssim, double* psnr);
+
 /* Step 5, Adam with bias correction (torch.optim.Adam semantics), dense over
  * all planes (or visible-only, see gs_adam_hp), per-group learning rate;
  * step counts from 1.  p, m, v are updated in place; g is read.  All four

@@ -75,7 +75,7 @@ struct gs_ctx {
 
   DevBuf views, rec, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
-      target_slot, host_tgt0, host_tgt1, pair_stats, cells, vismask;
+      target_slot, host_tgt0, host_tgt1, pair_stats, cells, vismask, ssim_table, ssim_partials, ssim_sums;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -371,7 +371,7 @@ void gs_destroy(gs_ctx* c) {
                     &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->hist_scan,
                     &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
                     &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1,
-                    &c->pair_stats, &c->cells, &c->vismask};
+                    &c->pair_stats, &c->cells, &c->vismask, &c->ssim_table, &c->ssim_partials, &c->ssim_sums};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -825,6 +825,71 @@ gs_status gs_get_counts(gs_ctx* c, int64_t* instances, int64_t* bins, int64_t* p
   if (instances) *instances = c->sorted ? (int64_t)cnt : -1;
   if (bins) *bins = c->bins;
   if (pixels) *pixels = c->pixels;
+  return GS_OK;
+}
+
+// SSIM forward (and backward) over the last projected batch's views.
+static gs_status run_ssim(gs_ctx* c, const float* images, const float* targets, float lambda, float* loss,
+                          float* dL_dimages) {
+  if (!c->projected) return fail(c, GS_ESTATE, "SSIM needs a projected batch (view sizes)");
+  if (!images || !targets) return fail(c, GS_EINVAL, "images and targets must not be NULL");
+  if (!(lambda >= 0.f && lambda <= 1.f)) return fail(c, GS_EINVAL, "lambda must be in [0, 1]");
+  set_device(c);
+  const int B = c->B;
+  std::vector<int> first(B + 1, 0);
+  for (int v = 0; v < B; v++) first[v + 1] = first[v] + ssim_blocks_of_view(c->views_h[v].W, c->views_h[v].H);
+  const int blocks = first[B];
+  const int64_t count = 3 * c->pixels;
+  GS_TRY(ensure(c, c->ssim_table, sizeof(int) * (B + 1)));
+  GS_TRY(ensure(c, c->ssim_partials, sizeof(float) * 3 * count));
+  GS_TRY(ensure(c, c->ssim_sums, sizeof(double) * (3 * (size_t)blocks + 3 * kMaxViews)));
+  GS_CUDA(c, cudaMemcpyAsync(c->ssim_table.p, first.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, c->stream));
+  SsimArgs a{};
+  a.views = P<ViewRec>(c->views);
+  a.B = B;
+  a.first_block = P<int>(c->ssim_table);
+  a.x = images;
+  a.y = targets;
+  a.count = count;
+  a.partials = P<float>(c->ssim_partials);
+  a.block_sums = P<double>(c->ssim_sums);
+  a.grad = dL_dimages;
+  ssim_window(a.win);
+  a.w_l1 = 1.f - lambda;
+  a.w_ssim = lambda;
+  a.inv_count = (float)(1.0 / (double)count);
+  a.w_l1_d = 1.0 - (double)lambda;
+  a.w_ssim_d = (double)lambda;
+  {
+    LaunchScope ls(c, "ssim", dL_dimages ? 3 : 2);
+    launch_ssim(a, blocks, dL_dimages != nullptr, P<double>(c->ssim_sums) + 3 * (size_t)blocks, loss, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  return GS_OK;
+}
+
+gs_status gs_ssim_loss(gs_ctx* c, const float* images, const float* targets, float lambda, float* loss,
+                       float* dL_dimages) {
+  if (!c) return GS_EINVAL;
+  if (!loss && !dL_dimages) return fail(c, GS_EINVAL, "loss and dL_dimages are both NULL");
+  return run_ssim(c, images, targets, lambda, loss, dL_dimages);
+}
+
+gs_status gs_image_metrics(gs_ctx* c, const float* images, const float* targets, double* ssim, double* psnr) {
+  if (!c) return GS_EINVAL;
+  if (!ssim && !psnr) return fail(c, GS_EINVAL, "ssim and psnr are both NULL");
+  GS_TRY(run_ssim(c, images, targets, 0.f, nullptr, nullptr));
+  std::vector<double> sums(3 * (size_t)c->B);
+  int blocks = 0;
+  for (int v = 0; v < c->B; v++) blocks += ssim_blocks_of_view(c->views_h[v].W, c->views_h[v].H);
+  GS_CUDA(c, cudaMemcpyAsync(sums.data(), P<double>(c->ssim_sums) + 3 * (size_t)blocks,
+                             sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int v = 0; v < c->B; v++) {
+    const double cnt = 3.0 * c->views_h[v].W * c->views_h[v].H;
+    if (ssim) ssim[v] = sums[3 * v] / cnt;
+    if (psnr) psnr[v] = 10.0 * std::log10(cnt / sums[3 * v + 2]);
+  }
   return GS_OK;
 }
 

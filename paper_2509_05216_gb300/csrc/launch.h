@@ -138,6 +138,27 @@ void launch_l1(const float* x, const float* y, const float* const* y_slot, int64
                int nparts, float* loss, float* grad, cudaStream_t s);
 int l1_parts(int64_t count);
 
+// SSIM / D-SSIM over a batch of views (ssim.cu).
+struct SsimArgs {
+  const ViewRec* views;
+  int B;
+  const int* first_block;  // [B + 1] first block of each view (3 channels x 32 x 16 tiles)
+  const float* x;          // images (batch layout)
+  const float* y;          // targets
+  int64_t count;           // 3 x pixels of the batch
+  float* partials;         // [3][count]: dSSIM/d(mx), dSSIM/dE[x^2], dSSIM/dE[xy] per pixel
+  double* block_sums;      // [blocks][3]: sums of the SSIM map, |x - y|, (x - y)^2
+  float* grad;             // dL/dx (backward)
+  float win[11];           // normalised Gaussian window (sigma 1.5)
+  float w_l1, w_ssim, inv_count;
+  double w_l1_d, w_ssim_d;
+};
+int ssim_blocks_of_view(int W, int H);
+void ssim_window(float* w);
+// forward (+ per-view sums into out_view[3 B] and the loss) and, if
+// backward, the gradient
+void launch_ssim(const SsimArgs& a, int blocks, bool backward, double* out_view, float* loss, cudaStream_t s);
+
 struct AdamArgs {
   float* p;
   const float* g;

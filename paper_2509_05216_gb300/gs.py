@@ -85,7 +85,8 @@ class gs_serve_cfg(ctypes.Structure):
 EXPORTS = ["gs_raster_fwd_l1", "gs_train_graph_capture", "gs_train_graph_launch", "gs_train_graph_launch_host", "gs_serve_create", "gs_serve_destroy", "gs_serve_submit", "gs_serve_poll", "gs_serve_release",
            "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
-           "gs_get_counts", "gs_pair_stats", "gs_serve_timeline"]
+           "gs_get_counts", "gs_pair_stats", "gs_serve_timeline", "gs_ssim_loss",
+           "gs_image_metrics"]
 
 
 def load(path: str | None = None):
@@ -131,6 +132,8 @@ def load(path: str | None = None):
     L.gs_profile_read.argtypes = [vp, P(gs_kernel_stat), i32, P(i32)]
     L.gs_profile_reset.argtypes = [vp]
     L.gs_pair_stats.argtypes = [vp, P(i64), P(i64)]
+    L.gs_ssim_loss.argtypes = [vp, vp, vp, ctypes.c_float, vp, vp]
+    L.gs_image_metrics.argtypes = [vp, vp, vp, P(ctypes.c_double), P(ctypes.c_double)]
     L.gs_serve_timeline.argtypes = [vp, P(ctypes.c_double), i32, P(i32), P(i64)]
     for name in EXPORTS:
         f = getattr(L, name)
@@ -286,6 +289,25 @@ class Context:
         arr = (gs_camera * len(cams))(*[camera_struct(c) for c in cams])
         self._check(self.L.gs_train_graph_launch_host(self.h, arr, len(cams), ctypes.c_void_p(host_targets.data_ptr()),
                                                       int(step), lp), "gs_train_graph_launch_host")
+
+    def gs_ssim_loss(self, images: torch.Tensor, targets: torch.Tensor, lam: float, loss=None, dimages=None):
+        """(1 - lam) L1 + lam (1 - SSIM) over the last projected batch's views."""
+        self._bind_stream()
+        for t in (images, targets):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        self._check(self.L.gs_ssim_loss(self.h, ctypes.c_void_p(images.data_ptr()), ctypes.c_void_p(targets.data_ptr()),
+                                        float(lam), ctypes.c_void_p(loss.data_ptr() if loss is not None else 0),
+                                        ctypes.c_void_p(dimages.data_ptr() if dimages is not None else 0)),
+                    "gs_ssim_loss")
+
+    def gs_image_metrics(self, images: torch.Tensor, targets: torch.Tensor, views: int):
+        """(SSIM per view, PSNR per view) of the last projected batch."""
+        self._bind_stream()
+        s = (ctypes.c_double * views)()
+        p = (ctypes.c_double * views)()
+        self._check(self.L.gs_image_metrics(self.h, ctypes.c_void_p(images.data_ptr()),
+                                            ctypes.c_void_p(targets.data_ptr()), s, p), "gs_image_metrics")
+        return list(s), list(p)
 
     def gs_sync(self):
         self._check(self.L.gs_sync(self.h), "gs_sync")
