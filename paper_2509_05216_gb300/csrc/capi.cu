@@ -861,7 +861,7 @@ static gs_status run_ssim(gs_ctx* c, const float* images, const float* targets, 
   a.w_l1_d = 1.0 - (double)lambda;
   a.w_ssim_d = (double)lambda;
   {
-    LaunchScope ls(c, "ssim", dL_dimages ? 3 : 2);
+    LaunchScope ls(c, "ssim", 2 + (loss ? 1 : 0) + (dL_dimages ? 1 : 0));
     launch_ssim(a, blocks, dL_dimages != nullptr, P<double>(c->ssim_sums) + 3 * (size_t)blocks, loss, c->stream);
   }
   GS_CHECK_LAUNCH(c);

@@ -202,29 +202,41 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(SsimArgs a) {
   }
 }
 
-// Per-view sums of the block sums (fixed order) and the loss of the batch.
+// Per-view sums of the block sums: block v of the grid adds view v's block
+// sums (a strided subset per thread, then a tree: a fixed order).
 // out_view[3 v + m]: view v's sums of the SSIM map (m = 0), |x - y| (1) and
-// (x - y)^2 (2); *loss = w_l1 sum|x - y| / count + w_ssim (1 - sum s / count).
-__global__ void ssim_finish_kernel(SsimArgs a, double* out_view, float* loss) {
-  __shared__ double tot[3];
-  if (threadIdx.x < 3) tot[threadIdx.x] = 0.0;
-  __syncthreads();
-  for (int v = threadIdx.x; v < a.B; v += blockDim.x) {
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int b = a.first_block[v]; b < a.first_block[v + 1]; b++)
-      for (int m = 0; m < 3; m++) s[m] += a.block_sums[3 * (int64_t)b + m];
-    for (int m = 0; m < 3; m++) out_view[3 * v + m] = s[m];
+// (x - y)^2 (2).
+__global__ void __launch_bounds__(256) ssim_view_sums_kernel(SsimArgs a, double* out_view) {
+  __shared__ double red[3][8];
+  const int v = blockIdx.x;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int b = a.first_block[v] + (int)threadIdx.x; b < a.first_block[v + 1]; b += blockDim.x)
+#pragma unroll
+    for (int m = 0; m < 3; m++) s[m] += a.block_sums[3 * (int64_t)b + m];
+#pragma unroll
+  for (int m = 0; m < 3; m++) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s[m] += __shfl_down_sync(0xffffffffu, s[m], off);
+    if ((threadIdx.x & 31) == 0) red[m][threadIdx.x >> 5] = s[m];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0, l1 = 0.0;
-    for (int v = 0; v < a.B; v++) {
-      s += out_view[3 * v];
-      l1 += out_view[3 * v + 1];
-    }
-    const double cnt = (double)a.count;
-    if (loss) *loss = (float)(a.w_l1_d * l1 / cnt + a.w_ssim_d * (1.0 - s / cnt));
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < 8; w++) t += red[threadIdx.x][w];
+    out_view[3 * v + threadIdx.x] = t;
   }
+}
+
+// *loss = w_l1 sum|x - y| / count + w_ssim (1 - sum s / count), views in order.
+__global__ void ssim_loss_kernel(SsimArgs a, const double* out_view, float* loss) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0, l1 = 0.0;
+  for (int v = 0; v < a.B; v++) {
+    s += out_view[3 * v];
+    l1 += out_view[3 * v + 1];
+  }
+  const double cnt = (double)a.count;
+  *loss = (float)(a.w_l1_d * l1 / cnt + a.w_ssim_d * (1.0 - s / cnt));
 }
 
 int ssim_blocks_of_view(int W, int H) { return 3 * ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH); }
@@ -242,7 +254,8 @@ void ssim_window(float* w) {
 void launch_ssim(const SsimArgs& a, int blocks, bool backward, double* out_view, float* loss, cudaStream_t s) {
   if (blocks <= 0) return;
   ssim_fwd_kernel<<<blocks, 256, 0, s>>>(a);
-  ssim_finish_kernel<<<1, 64, 0, s>>>(a, out_view, loss);
+  ssim_view_sums_kernel<<<a.B, 256, 0, s>>>(a, out_view);
+  if (loss) ssim_loss_kernel<<<1, 32, 0, s>>>(a, out_view, loss);
   if (backward) ssim_bwd_kernel<<<blocks, 256, 0, s>>>(a);
 }
 
