@@ -274,6 +274,41 @@ gs_status gs_ssim_loss(gs_ctx* ctx, const float* images, const float* targets, f
  * both).  Synchronises the stream.  Errors: as gs_ssim_loss. */
 gs_status gs_image_metrics(gs_ctx* ctx, const float* images, const float* targets, double* ssim, double* psnr);
 
+/* Point-cloud initialisation (the paper starts 3D-GS from the isosurface of
+ * a volume extracted as a point cloud instead of SfM points, Method
+ * Overview).  Isosurface edge crossings of volume (device, float
+ * [nz][ny][nx], sample (x, y, z) at origin + spacing * (x, y, z)): for every
+ * grid edge whose end values a, b lie on different sides of the level
+ * (a >= iso differs from b >= iso), the point at t = (iso - a) / (b - a)
+ * along the edge and the volume gradient (central differences, one-sided at
+ * the border) interpolated the same way and normalised (pointing towards
+ * larger values), in vertex order (x fastest, then y, then z; per vertex its
+ * +x, +y, +z edges).  Always sets *count (host) to the number of crossings;
+ * with points == normals == NULL it only counts; otherwise points and
+ * normals (device, float [capacity][3]) receive them.  Synchronises the
+ * stream.  Ends the context's current batch (gs_project must run again).
+ * Errors: GS_EINVAL, GS_ECAPACITY (more crossings than capacity; nothing
+ * written), GS_ENOMEM, GS_ECUDA. */
+gs_status gs_iso_crossings(gs_ctx* ctx, const float* volume, int32_t nx, int32_t ny, int32_t nz, float iso,
+                           const float* origin /* host [3] */, const float* spacing /* host [3] */, float* points,
+                           float* normals, int64_t capacity, int64_t* count);
+
+/* Initial Gaussians from a point cloud (device, float [m][3] points and unit
+ * normals): the n points select[0..n) (device int64 indices into the m, or
+ * select == NULL with n == m) become out's n Gaussians: mean = point,
+ * log-scales (s, s, s + log flatten) with s = log sqrt of the mean squared
+ * distance to the 3 nearest other selected points (exact; floored at 1e-14),
+ * the rotation taking +z onto the normal (quaternion (1 + n_z, -n_y, n_x, 0)
+ * normalised; (0, 1, 0, 0) for n = -z), opacity logit as given, SH DC
+ * 2 sqrt(pi) (c - 1/2) with the Lambertian grey c = 0.1 + 0.9 max(0,
+ * n . (1,1,1)/sqrt 3), higher SH 0.  The neighbours are found on the GPU with
+ * a uniform grid (points sorted by cell with the binning's radix sort).
+ * Synchronises the stream; ends the context's current batch.  Errors:
+ * GS_EINVAL (n < 4, n != out->n, m < n, flatten <= 0, points spanning no
+ * box), GS_ENOMEM, GS_ECUDA. */
+gs_status gs_init_gaussians(gs_ctx* ctx, const float* points, const float* normals, int64_t m, const int64_t* select,
+                            int64_t n, float flatten, float opacity_logit, gs_params* out);
+
 /* Step 5, Adam with bias correction (torch.optim.Adam semantics), dense over
  * all planes (or visible-only, see gs_adam_hp), per-group learning rate;
  * step counts from 1.  p, m, v are updated in place; g is read.  All four

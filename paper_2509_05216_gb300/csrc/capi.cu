@@ -75,7 +75,8 @@ struct gs_ctx {
 
   DevBuf views, rec, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
-      target_slot, host_tgt0, host_tgt1, pair_stats, cells, vismask, ssim_table, ssim_partials, ssim_sums;
+      target_slot, host_tgt0, host_tgt1, pair_stats, cells, vismask, ssim_table, ssim_partials, ssim_sums,
+      init_pts, init_scales, knn_part, knn_table;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -371,7 +372,8 @@ void gs_destroy(gs_ctx* c) {
                     &c->total, &c->keys0, &c->keys1, &c->vals0, &c->vals1, &c->hist, &c->hist_scan,
                     &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
                     &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1,
-                    &c->pair_stats, &c->cells, &c->vismask, &c->ssim_table, &c->ssim_partials, &c->ssim_sums};
+                    &c->pair_stats, &c->cells, &c->vismask, &c->ssim_table, &c->ssim_partials, &c->ssim_sums,
+                    &c->init_pts, &c->init_scales, &c->knn_part, &c->knn_table};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -890,6 +892,230 @@ gs_status gs_image_metrics(gs_ctx* c, const float* images, const float* targets,
     if (ssim) ssim[v] = sums[3 * v] / cnt;
     if (psnr) psnr[v] = 10.0 * std::log10(cnt / sums[3 * v + 2]);
   }
+  return GS_OK;
+}
+
+// ---------------------------------------------------------------- initialisation
+
+// Stable LSD sort of n (key, value) pairs on the low `bits` key bits with the
+// binning's onesweep (one segment), in the context's instance buffers;
+// *which = the buffer (0 / 1) holding the result.  Synchronises the stream.
+static gs_status sort_pairs(gs_ctx* c, int64_t n, int bits, int* which) {
+  const int npass = std::max(1, (bits + 7) / 8);
+  GS_TRY(ensure(c, c->views, sizeof(ViewRec)));
+  GS_TRY(ensure(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
+                                 sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
+  const size_t lb = sort_lookback_bytes(n, c->sort_items, 1);
+  GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
+  GS_TRY(ensure(c, c->hist_scan, sizeof(uint32_t) * 8 * 256));
+  GS_TRY(ensure(c, c->lookback, lb * npass));
+  GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
+  uint64_t* total = P<uint64_t>(c->total);
+  uint32_t* seg = reinterpret_cast<uint32_t*>(total + 1 + kMaxViews);
+  uint32_t* part_off = seg + kMaxViews + 1;
+  uint32_t* ctrl = part_off + kMaxViews + 1;
+  const uint64_t cnt = (uint64_t)n;
+  const uint32_t segs[2] = {0u, (uint32_t)n};
+  GS_CUDA(c, cudaMemsetAsync(c->views.p, 0, sizeof(ViewRec), c->stream));
+  GS_CUDA(c, cudaMemcpyAsync(total, &cnt, sizeof(cnt), cudaMemcpyHostToDevice, c->stream));
+  GS_CUDA(c, cudaMemcpyAsync(seg, segs, sizeof(segs), cudaMemcpyHostToDevice, c->stream));
+  SortArgs sa{};
+  sa.keys[0] = P<uint64_t>(c->keys0);
+  sa.keys[1] = P<uint64_t>(c->keys1);
+  sa.vals[0] = P<uint32_t>(c->vals0);
+  sa.vals[1] = P<uint32_t>(c->vals1);
+  sa.count = total;
+  sa.capacity = n;
+  sa.bins = 1;
+  sa.B = 1;
+  sa.views = P<ViewRec>(c->views);
+  sa.seg = seg;
+  sa.part_off = part_off;
+  sa.hist = P<uint32_t>(c->hist);
+  sa.hist_scan = P<uint32_t>(c->hist_scan);
+  sa.ctrl = ctrl;
+  sa.single = ctrl + 16;
+  sa.lookback = P<uint32_t>(c->lookback);
+  sa.lookback_stride = lb / sizeof(uint32_t);
+  sa.counters = P<uint32_t>(c->counters);
+  sa.npass = npass;
+  sa.wait_rounds = c->sort_wait;
+  sa.status = c->status_d;
+  GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * npass * 256, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * 8, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * npass, c->stream));
+  {
+    LaunchScope ls(c, "digit_histogram", 3);
+    launch_digit_histogram(sa, n, c->sort_items, c->stream);
+  }
+  for (int p = 0; p < npass; p++) {
+    LaunchScope ls(c, "onesweep_pass");
+    launch_onesweep_pass(sa, p, c->sort_items, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  uint32_t par = 0;
+  GS_CUDA(c, cudaMemcpyAsync(&par, ctrl + npass, sizeof(par), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  *which = (int)(par & 1u);
+  return GS_OK;
+}
+
+gs_status gs_iso_crossings(gs_ctx* c, const float* volume, int32_t nx, int32_t ny, int32_t nz, float iso,
+                           const float* origin, const float* spacing, float* points, float* normals, int64_t capacity,
+                           int64_t* count) {
+  if (!c) return GS_EINVAL;
+  if (!volume || !origin || !spacing || !count) return fail(c, GS_EINVAL, "NULL argument");
+  if (nx < 1 || ny < 1 || nz < 1) return fail(c, GS_EINVAL, "volume dimensions must be >= 1");
+  if ((points == nullptr) != (normals == nullptr)) return fail(c, GS_EINVAL, "points and normals go together");
+  set_device(c);
+  c->projected = c->sorted = c->rastered = c->cells_ready = false;
+  IsoArgs a{};
+  a.vol = volume;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.nverts = (int64_t)nx * ny * nz;
+  a.iso = iso;
+  for (int d = 0; d < 3; d++) {
+    a.origin[d] = origin[d];
+    a.h[d] = spacing[d];
+  }
+  const int64_t nb = (a.nverts + 255) / 256;
+  GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * nb));
+  GS_TRY(ensure(c, c->block_offsets, sizeof(uint32_t) * nb));
+  GS_TRY(ensure(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
+                                 sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
+  a.block_counts = P<uint32_t>(c->block_sums);
+  a.block_offsets = P<uint32_t>(c->block_offsets);
+  a.status = c->status_d;
+  uint64_t* total = P<uint64_t>(c->total);
+  {
+    LaunchScope ls(c, "iso_crossings");
+    launch_iso(a, false, c->stream);
+  }
+  {
+    LaunchScope ls(c, "scan_block_sums", 2);
+    launch_scan_block_sums(P<uint32_t>(c->block_sums), nb, 1, P<uint32_t>(c->block_offsets), total + 1,
+                           reinterpret_cast<uint32_t*>(total + 1 + kMaxViews), total, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  uint64_t m = 0;
+  GS_CUDA(c, cudaMemcpyAsync(&m, total, sizeof(m), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  *count = (int64_t)m;
+  if (!points) return GS_OK;
+  if ((int64_t)m > capacity) return fail(c, GS_ECAPACITY, "%llu crossings exceed the capacity", (unsigned long long)m);
+  a.points = points;
+  a.normals = normals;
+  a.capacity = capacity;
+  {
+    LaunchScope ls(c, "iso_crossings");
+    launch_iso(a, true, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  return GS_OK;
+}
+
+gs_status gs_init_gaussians(gs_ctx* c, const float* points, const float* normals, int64_t m, const int64_t* select,
+                            int64_t n, float flatten, float opacity_logit, gs_params* out) {
+  if (!c) return GS_EINVAL;
+  if (!points || !normals) return fail(c, GS_EINVAL, "points and normals must not be NULL");
+  GS_TRY(check_params(c, out, "out"));
+  if (out->n != n || n < 4 || m < n || (!select && m != n))
+    return fail(c, GS_EINVAL, "need n = out->n >= 4 and m >= n (m = n without select)");
+  if (!(flatten > 0.f) || n >= ((int64_t)1 << 31)) return fail(c, GS_EINVAL, "bad flatten or n");
+  set_device(c);
+  c->projected = c->sorted = c->rastered = c->cells_ready = false;
+  // the selected points, contiguous
+  const float* pts = points;
+  if (select) {
+    GS_TRY(ensure(c, c->init_pts, sizeof(float) * 3 * n));
+    launch_init_gather(points, select, n, P<float>(c->init_pts), c->stream);
+    GS_CHECK_LAUNCH(c);
+    pts = P<float>(c->init_pts);
+  }
+  // bounds -> grid of about one point per cell volume
+  const int nparts = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8));
+  GS_TRY(ensure(c, c->knn_part, sizeof(float) * 6 * (nparts + 1)));
+  float* bounds_d = P<float>(c->knn_part) + 6 * nparts;
+  launch_knn_bounds(pts, n, P<float>(c->knn_part), nparts, bounds_d, c->stream);
+  GS_CHECK_LAUNCH(c);
+  float bounds[6];
+  GS_CUDA(c, cudaMemcpyAsync(bounds, bounds_d, sizeof(bounds), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  KnnArgs k{};
+  k.pts = pts;
+  k.n = n;
+  k.k = 3;
+  double ext[3], vol = 1.0, emax = 0.0;
+  for (int d = 0; d < 3; d++) {
+    ext[d] = (double)bounds[3 + d] - (double)bounds[d];
+    emax = std::max(emax, ext[d]);
+  }
+  if (!(emax > 0.0) || !std::isfinite(emax)) return fail(c, GS_EINVAL, "points must span a finite, nonzero box");
+  for (int d = 0; d < 3; d++) vol *= std::max(ext[d], emax * 1e-3);
+  double cell = std::cbrt(vol / (double)n);
+  int64_t cells = 1;
+  for (int d = 0; d < 3; d++) {
+    int64_t dim = (int64_t)(ext[d] / cell) + 1;
+    while (dim > (1 << 20)) {  // keep every axis within 2^20 cells
+      cell *= 2.0;
+      dim = (int64_t)(ext[d] / cell) + 1;
+    }
+    k.dims[d] = (int)dim;
+  }
+  for (int d = 0; d < 3; d++) {
+    k.dims[d] = (int)((int64_t)(ext[d] / cell) + 1);
+    cells *= k.dims[d];
+    k.lo[d] = bounds[d];
+  }
+  k.cell = (float)cell;
+  k.inv_cell = (float)(1.0 / cell);
+  int bits = 1;
+  while (((int64_t)1 << bits) < cells) bits++;
+  int tbits = 10;
+  while (((int64_t)1 << tbits) < 2 * n) tbits++;
+  k.table_bits = tbits;
+  GS_TRY(ensure(c, c->keys0, sizeof(uint64_t) * n));
+  GS_TRY(ensure(c, c->keys1, sizeof(uint64_t) * n));
+  GS_TRY(ensure(c, c->vals0, sizeof(uint32_t) * n));
+  GS_TRY(ensure(c, c->vals1, sizeof(uint32_t) * n));
+  GS_TRY(ensure(c, c->knn_table, (sizeof(uint64_t) + sizeof(uint32_t)) << tbits));
+  GS_TRY(ensure(c, c->init_scales, sizeof(float) * n));
+  {
+    LaunchScope ls(c, "knn_cells");
+    launch_knn_keys(k, P<uint64_t>(c->keys0), P<uint32_t>(c->vals0), c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  int which = 0;
+  GS_TRY(sort_pairs(c, n, bits, &which));
+  k.skeys = which ? P<uint64_t>(c->keys1) : P<uint64_t>(c->keys0);
+  k.svals = which ? P<uint32_t>(c->vals1) : P<uint32_t>(c->vals0);
+  k.table_keys = P<uint64_t>(c->knn_table);
+  k.table_start = reinterpret_cast<uint32_t*>(P<uint64_t>(c->knn_table) + ((size_t)1 << tbits));
+  k.out = P<float>(c->init_scales);
+  GS_CUDA(c, cudaMemsetAsync(k.table_keys, 0xff, sizeof(uint64_t) << tbits, c->stream));
+  {
+    LaunchScope ls(c, "knn_query", 2);
+    launch_knn_query(k, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  InitArgs a{};
+  a.points = points;
+  a.normals = normals;
+  a.sel = select;
+  a.n = n;
+  a.log_scales = P<float>(c->init_scales);
+  a.log_flatten = std::log(flatten);
+  a.opacity_logit = opacity_logit;
+  a.params = out->data;
+  a.stride = out->stride;
+  a.planes = n_planes(out->sh_degree);
+  {
+    LaunchScope ls(c, "init_params");
+    launch_init_params(a, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
   return GS_OK;
 }
 

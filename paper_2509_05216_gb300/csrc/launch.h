@@ -159,6 +159,53 @@ void ssim_window(float* w);
 // backward, the gradient
 void launch_ssim(const SsimArgs& a, int blocks, bool backward, double* out_view, float* loss, cudaStream_t s);
 
+// Point-cloud initialisation (init.cu).
+struct IsoArgs {
+  const float* vol;  // [nz][ny][nx]
+  int nx, ny, nz;
+  int64_t nverts;
+  float iso;
+  float origin[3], h[3];
+  uint32_t* block_counts;         // count pass: crossings per block of 256 vertices
+  const uint32_t* block_offsets;  // emit pass: exclusive scan of block_counts
+  float* points;                  // [capacity][3]
+  float* normals;                 // [capacity][3]
+  int64_t capacity;
+  int* status;
+};
+void launch_iso(const IsoArgs& a, bool emit, cudaStream_t s);
+
+struct KnnArgs {
+  const float* pts;  // [n][3]
+  int64_t n;
+  int k;             // 1..8 neighbours
+  float lo[3], cell, inv_cell;
+  int dims[3];
+  const uint64_t* skeys;  // cell ids, sorted
+  const uint32_t* svals;  // point of each sorted position
+  uint64_t* table_keys;   // [2^table_bits] cell id (all ones: empty)
+  uint32_t* table_start;  // first sorted position of the cell
+  int table_bits;
+  float* out;        // [n] log-scales
+};
+void launch_knn_bounds(const float* pts, int64_t n, float* part, int nparts, float* out, cudaStream_t s);
+void launch_knn_keys(const KnnArgs& a, uint64_t* keys, uint32_t* vals, cudaStream_t s);
+void launch_knn_query(const KnnArgs& a, cudaStream_t s);
+
+struct InitArgs {
+  const float* points;   // [m][3]
+  const float* normals;  // [m][3]
+  const int64_t* sel;    // [n] indices into the points (NULL: the first n)
+  int64_t n;
+  const float* log_scales;  // [n]
+  float log_flatten, opacity_logit;
+  float* params;
+  int64_t stride;
+  int planes;
+};
+void launch_init_params(const InitArgs& a, cudaStream_t s);
+void launch_init_gather(const float* pts, const int64_t* sel, int64_t n, float* out, cudaStream_t s);
+
 struct AdamArgs {
   float* p;
   const float* g;

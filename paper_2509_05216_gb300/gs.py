@@ -86,7 +86,7 @@ EXPORTS = ["gs_raster_fwd_l1", "gs_train_graph_capture", "gs_train_graph_launch"
            "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
            "gs_get_counts", "gs_pair_stats", "gs_serve_timeline", "gs_ssim_loss",
-           "gs_image_metrics"]
+           "gs_image_metrics", "gs_iso_crossings", "gs_init_gaussians"]
 
 
 def load(path: str | None = None):
@@ -133,6 +133,9 @@ def load(path: str | None = None):
     L.gs_profile_reset.argtypes = [vp]
     L.gs_pair_stats.argtypes = [vp, P(i64), P(i64)]
     L.gs_ssim_loss.argtypes = [vp, vp, vp, ctypes.c_float, vp, vp]
+    L.gs_iso_crossings.argtypes = [vp, vp, i32, i32, i32, ctypes.c_float, P(ctypes.c_float), P(ctypes.c_float),
+                                   vp, vp, i64, P(i64)]
+    L.gs_init_gaussians.argtypes = [vp, vp, vp, i64, vp, i64, ctypes.c_float, ctypes.c_float, P(gs_params)]
     L.gs_image_metrics.argtypes = [vp, vp, vp, P(ctypes.c_double), P(ctypes.c_double)]
     L.gs_serve_timeline.argtypes = [vp, P(ctypes.c_double), i32, P(i32), P(i64)]
     for name in EXPORTS:
@@ -308,6 +311,41 @@ class Context:
         self._check(self.L.gs_image_metrics(self.h, ctypes.c_void_p(images.data_ptr()),
                                             ctypes.c_void_p(targets.data_ptr()), s, p), "gs_image_metrics")
         return list(s), list(p)
+
+    def gs_iso_crossings(self, volume: torch.Tensor, iso: float, origin, spacing):
+        """(points [m, 3], normals [m, 3]) device tensors of the level's edge
+        crossings of a [nz, ny, nx] float32 CUDA volume."""
+        self._bind_stream()
+        assert volume.is_cuda and volume.dtype == torch.float32 and volume.is_contiguous() and volume.dim() == 3
+        nz, ny, nx = volume.shape
+        o = (ctypes.c_float * 3)(*[float(x) for x in origin])
+        h = (ctypes.c_float * 3)(*[float(x) for x in spacing])
+        cnt = ctypes.c_int64()
+        self._check(self.L.gs_iso_crossings(self.h, ctypes.c_void_p(volume.data_ptr()), nx, ny, nz, float(iso), o, h,
+                                            None, None, 0, ctypes.byref(cnt)), "gs_iso_crossings")
+        m = cnt.value
+        pts = torch.empty((max(m, 1), 3), device=volume.device, dtype=torch.float32)
+        nrm = torch.empty_like(pts)
+        self._check(self.L.gs_iso_crossings(self.h, ctypes.c_void_p(volume.data_ptr()), nx, ny, nz, float(iso), o, h,
+                                            ctypes.c_void_p(pts.data_ptr()), ctypes.c_void_p(nrm.data_ptr()), m,
+                                            ctypes.byref(cnt)), "gs_iso_crossings")
+        return pts[:m], nrm[:m]
+
+    def gs_init_gaussians(self, points: torch.Tensor, normals: torch.Tensor, out: torch.Tensor, n: int, deg: int,
+                          select: torch.Tensor | None = None, flatten: float = 0.3, opacity_logit: float = 2.0):
+        """Write the initial Gaussians (plane layout) of the selected points into `out`."""
+        self._bind_stream()
+        for t in (points, normals):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.shape[1:] == (3,)
+        sp = None
+        if select is not None:
+            assert select.is_cuda and select.dtype == torch.int64 and select.is_contiguous()
+            sp = ctypes.c_void_p(select.data_ptr())
+        o = params_struct(out, n, deg)
+        self._check(self.L.gs_init_gaussians(self.h, ctypes.c_void_p(points.data_ptr()),
+                                             ctypes.c_void_p(normals.data_ptr()), points.shape[0], sp, n,
+                                             float(flatten), float(opacity_logit), ctypes.byref(o)),
+                    "gs_init_gaussians")
 
     def gs_sync(self):
         self._check(self.L.gs_sync(self.h), "gs_sync")
