@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -65,6 +66,7 @@ def parse():
     ap.add_argument("--bwd-direct", type=int, default=-1,
                     help="force the backward's direct-atomic lane limit (with forced variants)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-init-bench", action="store_true", help="skip the point-cloud initialisation timings")
     ap.add_argument("--cache", default=os.environ.get("GS_SCENE_CACHE", "/tmp/gs_scene_cache"))
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -510,6 +512,8 @@ def gpu_arm(args):
              "note": "D-SSIM loss and gradient over the B views (kernels ssim_fwd, finish, ssim_bwd); SSIM / PSNR "
                      "of the trained set's render against the targets after the timed steps"}
 
+    init = init_bench(ctx, scene, dev) if not args.no_init_bench else None
+
     # plain path: one view per launch, Adam after each view
     ctx2 = gs.Context(local)
     tr2 = Trainer(ctx2, trained, dev)
@@ -576,7 +580,7 @@ def gpu_arm(args):
                  "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
         "instances_per_step": int(inst), "pair_entries_per_step": int(pairs[0]),
         "contributing_pairs_per_step": int(pairs[1]), "sort_passes_executed": executed,
-        "kernels": per_kernel, "visible_only_adam": visible_only, "dssim": dssim,
+        "kernels": per_kernel, "visible_only_adam": visible_only, "dssim": dssim, "init": init,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
         "memory": memory,
     }
@@ -612,6 +616,61 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- initialisation
+
+def init_bench(ctx, scene, dev):
+    """Point-cloud initialisation on the GPU at the benchmark's scale: the
+    initial Gaussians of the workload's 4M isosurface points (normals from
+    the scene's rotations) against the scene builder's host k-d-tree scales,
+    and the edge crossings of a 512^3 gyroid volume."""
+    import torch
+    from scipy.spatial import cKDTree
+    p = scene["params"]
+    n = scene["n"]
+    pts = np.ascontiguousarray(p[0:3, :n].T)
+    w, x, y, z = (p[6 + i, :n].astype(np.float64) for i in range(4))
+    nrm = np.stack([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)], 1)  # R(q) e_z
+    nrm = (nrm / np.linalg.norm(nrm, axis=1, keepdims=True)).astype(np.float32)
+    tp, tn = torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev)
+    out = torch.zeros_like(torch.from_numpy(p)).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.gs_init_gaussians(tp, tn, out, n, scene["deg"])  # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0.record()
+    ctx.gs_init_gaussians(tp, tn, out, n, scene["deg"])
+    e1.record()
+    torch.cuda.synchronize(dev)
+    gpu_s = time.perf_counter() - t0
+    got = out[3, :n].cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    d, _ = cKDTree(pts.astype(np.float64)).query(pts.astype(np.float64), k=4, workers=-1)
+    host_s = time.perf_counter() - t0
+    ref = 0.5 * np.log(np.maximum(np.mean(d[:, 1:] ** 2, axis=1), 1e-14))
+    err = np.abs(got - ref)
+    # edge crossings of the gyroid sin x cos y + sin y cos z + sin z cos x = 0
+    res = 512
+    ax = torch.linspace(-2 * math.pi, 2 * math.pi, res, device=dev)
+    zz, yy, xx = torch.meshgrid(ax, ax, ax, indexing="ij")
+    vol = (torch.sin(xx) * torch.cos(yy) + torch.sin(yy) * torch.cos(zz) + torch.sin(zz) * torch.cos(xx)).contiguous()
+    del zz, yy, xx
+    h = float(ax[1] - ax[0])
+    ctx.gs_iso_crossings(vol, 0.0, (-2 * math.pi,) * 3, (h,) * 3)  # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    cp, _ = ctx.gs_iso_crossings(vol, 0.0, (-2 * math.pi,) * 3, (h,) * 3)
+    torch.cuda.synchronize(dev)
+    cross_s = time.perf_counter() - t0
+    return {"gaussians": int(n), "gpu_init_ms": round(e0.elapsed_time(e1), 2), "gpu_init_wall_s": round(gpu_s, 3),
+            "host_kdtree_knn_s": round(host_s, 2), "host_threads": os.cpu_count(),
+            "log_scale_vs_host": {"median_abs": float(np.median(err)), "p999_abs": float(np.quantile(err, 0.999)),
+                                  "max_abs": float(err.max())},
+            "crossings_512cube": {"count": int(cp.shape[0]), "wall_s": round(cross_s, 3)},
+            "note": "gs_init_gaussians: exact 3-NN scales on the GPU (grid + radix sort) and the parameter planes; "
+                    "host: scipy cKDTree query of the same FP32 points (all cores); crossings: two passes "
+                    "(count, emit) with a host read of the count in between"}
 
 
 # ---------------------------------------------------------------- serving
