@@ -582,6 +582,7 @@ def gpu_arm(args):
         "contributing_pairs_per_step": int(pairs[1]), "sort_passes_executed": executed,
         "kernels": per_kernel, "visible_only_adam": visible_only, "dssim": dssim, "init": init,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
+        "autotune_ms": autotune.report(key),
         "memory": memory,
     }
     if args.serve_sweep:

@@ -149,7 +149,7 @@ typedef enum {
                             (default), 20 or 24 (partitions of 256 x items
                             keys).  Same result.  Fixed once a training graph
                             is captured (GS_ESTATE). */
-  GS_OPT_SORT_WAIT = 4   /* look-back rounds a radix-sort partition waits for
+  GS_OPT_SORT_WAIT = 4,  /* look-back rounds a radix-sort partition waits for
                             the partitions before it: 1 .. 1048576 (default
                             1048576, about a second), after which the sort
                             gives up and the next gs_sync reports
@@ -157,6 +157,14 @@ typedef enum {
                             back gives up at once (exercises the timeout
                             path; the blocks return, nothing hangs).  Fixed
                             once a training graph is captured (GS_ESTATE). */
+  GS_OPT_TILE_ORDER = 5  /* order in which the compositing kernels take the
+                            batch's tiles: 0 (default) bin order; 1 longest
+                            lists first (tiles bucketed by floor(log2(list
+                            length + 1)), bin order within a bucket; one extra
+                            sort pass over the bins per batch).  Same result
+                            (the fused L1 loss sums its per-tile partials in
+                            bin order either way).  Fixed once a training graph
+                            is captured (GS_ESTATE). */
 } gs_option;
 
 /* Set / read an option.  Errors: GS_EINVAL (unknown option, bad value). */

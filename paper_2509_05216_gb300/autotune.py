@@ -16,7 +16,8 @@ import torch
 from . import gs
 
 CANDIDATES = {gs.GS_OPT_RASTER_FWD: [2, 8, 4, 1], gs.GS_OPT_RASTER_BWD: [2, 4, 8, 1],
-              gs.GS_OPT_BWD_DIRECT: [2, 0, 4, 8], gs.GS_OPT_SORT_ITEMS: [16, 12, 20, 24]}
+              gs.GS_OPT_BWD_DIRECT: [2, 0, 4, 8], gs.GS_OPT_SORT_ITEMS: [16, 12, 20, 24],
+              gs.GS_OPT_TILE_ORDER: [0, 1]}
 
 
 def workload_key(n, cams, batch):
@@ -64,6 +65,13 @@ def time_step(step, reps=3):
         torch.cuda.synchronize()
         best = min(best, ev0.elapsed_time(ev1))
     return best
+
+
+def report(key):
+    """The timings (ms per step, "option=value") of the cached search for
+    `key`, or None."""
+    entry = _load().get(key)
+    return entry.get("ms") if entry else None
 
 
 def tune(ctxs, step, key, candidates=None, reps=3, rounds=2, use_cache=True):

@@ -622,6 +622,48 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __r
   }
 }
 
+// ---------------------------------------------------------------- tile order
+
+// Keys of the longest-list-first order: tiles bucketed by floor(log2(length
+// + 1)), longest bucket first (a stable sort keeps bin order inside a bucket,
+// so the order is deterministic); block 0 also writes the sort's count and
+// segment bounds.
+__global__ void __launch_bounds__(256) tile_order_keys_kernel(const uint2* __restrict__ ranges, int64_t bins,
+                                                              uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                              uint64_t* count, uint32_t* seg) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) {
+    *count = (uint64_t)bins;
+    seg[0] = 0u;
+    seg[1] = (uint32_t)bins;
+  }
+  if (b >= bins) return;
+  const uint2 r = ranges[b];
+  const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+  keys[b] = (uint64_t)(31 - (31 - __clz(len + 1u)));
+  vals[b] = (uint32_t)b;
+}
+
+__global__ void __launch_bounds__(256) tile_order_finish_kernel(const uint32_t* __restrict__ ctrl, int npass,
+                                                                const uint32_t* __restrict__ v0,
+                                                                const uint32_t* __restrict__ v1, int64_t bins,
+                                                                uint32_t* __restrict__ order) {
+  const uint32_t* src = (ctrl[npass] & kCtrlParity) ? v1 : v0;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < bins; b += (int64_t)gridDim.x * blockDim.x)
+    order[b] = src[b];
+}
+
+void launch_tile_order_keys(const uint2* ranges, int64_t bins, uint64_t* keys, uint32_t* vals, uint64_t* count,
+                            uint32_t* seg, cudaStream_t s) {
+  tile_order_keys_kernel<<<(unsigned)((bins + 255) / 256), 256, 0, s>>>(ranges, bins, keys, vals, count, seg);
+}
+
+void launch_tile_order_finish(const uint32_t* ctrl, int npass, const uint32_t* v0, const uint32_t* v1, int64_t bins,
+                              uint32_t* order, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((bins + 255) / 256, (int64_t)sm_count() * 8);
+  tile_order_finish_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(ctrl, npass, v0, v1, bins, order);
+}
+
 void launch_tile_ranges(const SortArgs& a, int64_t grid_hint, uint2* ranges, cudaStream_t s) {
   int64_t blocks = (grid_hint + 255) / 256;
   const int64_t most = (int64_t)sm_count() * 32;

@@ -63,6 +63,8 @@ struct gs_ctx {
   int sort_passes = 0;  // LSD passes of the last sort
   int sort_items = 16;  // keys per thread of a sort partition
   int sort_wait = 1 << 20;  // look-back rounds before a sort gives up
+  int tile_order_mode = 0;  // 0: composite tiles in bin order; 1: longest lists first
+  bool tile_order_ready = false;
   int64_t batch_cap = 0;    // instance capacity of the next sorts (0: cfg.instance_capacity)
   bool forward_only = false;  // no contribution cells: gs_raster_bwd unavailable (render server)
   bool cells_ready = false;   // the last forward recorded contribution cells
@@ -76,7 +78,8 @@ struct gs_ctx {
   DevBuf views, rec, rec3, tiles, block_sums, block_offsets, total, keys0, keys1, vals0, vals1,
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
       target_slot, host_tgt0, host_tgt1, pair_stats, cells, vismask, ssim_table, ssim_partials, ssim_sums,
-      init_pts, init_scales, knn_part, knn_table;
+      init_pts, init_scales, knn_part, knn_table, ord_keys0, ord_keys1, ord_vals0, ord_vals1, ord_total, ord_hist,
+      ord_hist_scan, ord_lookback, ord_counters, ord_views, tile_order;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -373,7 +376,9 @@ void gs_destroy(gs_ctx* c) {
                     &c->lookback, &c->counters, &c->ranges, &c->tfinal, &c->nlast, &c->g2d, &c->l1_partial,
                     &c->sorted_slots, &c->adam_consts, &c->target_slot, &c->host_tgt0, &c->host_tgt1,
                     &c->pair_stats, &c->cells, &c->vismask, &c->ssim_table, &c->ssim_partials, &c->ssim_sums,
-                    &c->init_pts, &c->init_scales, &c->knn_part, &c->knn_table};
+                    &c->init_pts, &c->init_scales, &c->knn_part, &c->knn_table, &c->ord_keys0, &c->ord_keys1,
+                    &c->ord_vals0, &c->ord_vals1, &c->ord_total, &c->ord_hist, &c->ord_hist_scan, &c->ord_lookback,
+                    &c->ord_counters, &c->ord_views, &c->tile_order};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -472,6 +477,8 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   c->projected = true;
   return GS_OK;
 }
+
+static gs_status sort_tiles_longest_first(gs_ctx* c);
 
 gs_status gs_bin_sort(gs_ctx* c) {
   if (!c) return GS_EINVAL;
@@ -593,7 +600,70 @@ gs_status gs_bin_sort(gs_ctx* c) {
     launch_tile_ranges(sa, cap, P<uint2>(c->ranges), c->stream);
   }
   GS_CHECK_LAUNCH(c);
+  c->tile_order_ready = false;
+  if (c->tile_order_mode == 1) GS_TRY(sort_tiles_longest_first(c));
   c->sorted = true;
+  return GS_OK;
+}
+
+// Longest-list-first order of the batch's tiles (bins bucketed by
+// floor(log2(length + 1)), a one-pass stable sort, bin order inside a
+// bucket) into c->tile_order; every step on the device, so a captured step
+// replays it.
+static gs_status sort_tiles_longest_first(gs_ctx* c) {
+  const int64_t bins = c->bins;
+  const int items = 16;
+  const size_t lb = sort_lookback_bytes(bins, items, 1);
+  GS_TRY(ensure(c, c->ord_keys0, sizeof(uint64_t) * bins));
+  GS_TRY(ensure(c, c->ord_keys1, sizeof(uint64_t) * bins));
+  GS_TRY(ensure(c, c->ord_vals0, sizeof(uint32_t) * bins));
+  GS_TRY(ensure(c, c->ord_vals1, sizeof(uint32_t) * bins));
+  GS_TRY(ensure(c, c->ord_total, sizeof(uint64_t) + sizeof(uint32_t) * (2 + 2 + 16 + 8)));
+  GS_TRY(ensure(c, c->ord_hist, sizeof(uint32_t) * 256));
+  GS_TRY(ensure(c, c->ord_hist_scan, sizeof(uint32_t) * 256));
+  GS_TRY(ensure(c, c->ord_lookback, lb));
+  GS_TRY(ensure(c, c->ord_counters, sizeof(uint32_t) * 8));
+  GS_TRY(ensure(c, c->ord_views, sizeof(ViewRec)));
+  GS_TRY(ensure(c, c->tile_order, sizeof(uint32_t) * bins));
+  uint64_t* count = P<uint64_t>(c->ord_total);
+  uint32_t* seg = reinterpret_cast<uint32_t*>(count + 1);
+  uint32_t* part_off = seg + 2;
+  uint32_t* ctrl = part_off + 2;
+  SortArgs sa{};
+  sa.keys[0] = P<uint64_t>(c->ord_keys0);
+  sa.keys[1] = P<uint64_t>(c->ord_keys1);
+  sa.vals[0] = P<uint32_t>(c->ord_vals0);
+  sa.vals[1] = P<uint32_t>(c->ord_vals1);
+  sa.count = count;
+  sa.capacity = bins;
+  sa.bins = bins;
+  sa.B = 1;
+  sa.views = P<ViewRec>(c->ord_views);
+  sa.seg = seg;
+  sa.part_off = part_off;
+  sa.hist = P<uint32_t>(c->ord_hist);
+  sa.hist_scan = P<uint32_t>(c->ord_hist_scan);
+  sa.ctrl = ctrl;
+  sa.single = ctrl + 16;
+  sa.lookback = P<uint32_t>(c->ord_lookback);
+  sa.lookback_stride = lb / sizeof(uint32_t);
+  sa.counters = P<uint32_t>(c->ord_counters);
+  sa.npass = 1;
+  sa.wait_rounds = c->sort_wait;
+  sa.status = c->status_d;
+  GS_CUDA(c, cudaMemsetAsync(c->ord_views.p, 0, sizeof(ViewRec), c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->ord_hist.p, 0, sizeof(uint32_t) * 256, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->ord_counters.p, 0, sizeof(uint32_t) * 8, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->ord_lookback.p, 0, lb, c->stream));
+  {
+    LaunchScope ls(c, "tile_order", 6);
+    launch_tile_order_keys(P<uint2>(c->ranges), bins, sa.keys[0], sa.vals[0], count, seg, c->stream);
+    launch_digit_histogram(sa, bins, items, c->stream);
+    launch_onesweep_pass(sa, 0, items, c->stream);
+    launch_tile_order_finish(ctrl, 1, sa.vals[0], sa.vals[1], bins, P<uint32_t>(c->tile_order), c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  c->tile_order_ready = true;
   return GS_OK;
 }
 
@@ -611,6 +681,7 @@ static RasterArgs raster_args(gs_ctx* c) {
   r.tfinal = P<float>(c->tfinal);
   r.nlast = P<uint32_t>(c->nlast);
   r.cells = c->forward_only ? nullptr : P<uint32_t>(c->cells);
+  r.tile_order = c->tile_order_ready ? P<uint32_t>(c->tile_order) : nullptr;
   return r;
 }
 
@@ -1157,6 +1228,11 @@ gs_status gs_set_option(gs_ctx* c, int32_t option, int64_t value) {
       if (c->capturing || c->gexec) return fail(c, GS_ESTATE, "sort partition size is fixed once a graph is captured");
       c->sort_items = (int)value;
       return GS_OK;
+    case GS_OPT_TILE_ORDER:
+      if (value != 0 && value != 1) return fail(c, GS_EINVAL, "tile order must be 0 or 1");
+      if (c->capturing || c->gexec) return fail(c, GS_ESTATE, "tile order is fixed once a graph is captured");
+      c->tile_order_mode = (int)value;
+      return GS_OK;
     case GS_OPT_SORT_WAIT:
       if (value < 0 || value > (1 << 20)) return fail(c, GS_EINVAL, "sort wait rounds must be 0..1048576");
       if (c->capturing || c->gexec) return fail(c, GS_ESTATE, "sort wait is fixed once a graph is captured");
@@ -1175,6 +1251,7 @@ gs_status gs_get_option(gs_ctx* c, int32_t option, int64_t* value) {
     case GS_OPT_BWD_DIRECT: *value = c->bwd_direct; return GS_OK;
     case GS_OPT_SORT_ITEMS: *value = c->sort_items; return GS_OK;
     case GS_OPT_SORT_WAIT: *value = c->sort_wait; return GS_OK;
+    case GS_OPT_TILE_ORDER: *value = c->tile_order_mode; return GS_OK;
     default: return fail(c, GS_EINVAL, "unknown option %d", option);
   }
 }

@@ -64,6 +64,9 @@ struct RasterArgs {
   // (instances + 32 bins words; written by the forward, NULL: not recorded;
   // read by the backward, which walks only those entries)
   uint32_t* cells;
+  // tile order of the compositing kernels: block slot k composites bin
+  // tile_order[k] (NULL: bin order)
+  const uint32_t* tile_order;
   const float* dimage;  // backward only
   float* g2d;           // backward only: [B][stride] geometry records, then [B][stride] colour records
   int direct_max;       // backward only: at most this many contributing lanes -> per-lane atomics
@@ -116,6 +119,14 @@ struct SortArgs {
   const uint64_t** sorted_keys;  // device slots: where the sorted list ends up
   const uint32_t** sorted_vals;
 };
+
+// Longest-list-first tile order: key = 31 - floor(log2(list length + 1)),
+// value = bin, for a one-segment stable sort of the bins; the count and the
+// segment bounds of that sort; the sorted values copied into `order`.
+void launch_tile_order_keys(const uint2* ranges, int64_t bins, uint64_t* keys, uint32_t* vals, uint64_t* count,
+                            uint32_t* seg, cudaStream_t s);
+void launch_tile_order_finish(const uint32_t* ctrl, int npass, const uint32_t* v0, const uint32_t* v1, int64_t bins,
+                              uint32_t* order, cudaStream_t s);
 
 size_t sort_lookback_bytes(int64_t count, int items, int segments);
 int64_t sort_partitions(int64_t count, int items, int segments);

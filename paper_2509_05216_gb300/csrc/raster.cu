@@ -450,6 +450,7 @@ struct Geo {
     const int tile_in_block = warp / NW, sub = warp % NW;
     bin = (int64_t)blockIdx.x * TPB + tile_in_block;
     if (bin >= bins) return false;
+    if (a.tile_order) bin = a.tile_order[bin];
     v = view_of_bin(a.views, a.B, (int)bin);
     const ViewRec& V = a.views[v];
     const int tile = (int)bin - V.tile_offset;
@@ -491,9 +492,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   G geo;
   if (!geo.init(a, bins, w, lane)) {
-    // a warp past the last tile (one-warp-per-tile shape): no pixels, a zero L1 partial
-    if (lane == 0 && (a.target || a.target_slot)) a.l1_partial[(int64_t)blockIdx.x * NWB + w] = 0.f;
-    return;
+    return;  // a warp past the last tile (one-warp-per-tile shape): no pixels
   }
   const int v = geo.v, px = geo.px, py0 = geo.py0;
   const ViewRec& V = a.views[v];
@@ -673,7 +672,8 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     // one partial sum per warp (fixed order: deterministic)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) l1sum += __shfl_down_sync(0xffffffffu, l1sum, off);
-    if (lane == 0) a.l1_partial[(int64_t)blockIdx.x * NWB + w] = l1sum;
+    // indexed by tile, so the loss does not depend on the tile order
+    if (lane == 0) a.l1_partial[geo.bin * G::NW + (w % G::NW)] = l1sum;
   }
 }
 
@@ -822,12 +822,12 @@ void launch_shape(bool fwd, const RasterArgs& a, int64_t bins, cudaStream_t s) {
 }
 
 int64_t raster_fwd_warps(int64_t bins, int ppt) {
-  // L1 partial sums of a fused forward: one per warp of the launch
+  // L1 partial sums of a fused forward: one per warp of each tile
   switch (ppt) {
-    case 1: return bins * Geo<1>::NW * Geo<1>::TPB;
-    case 4: return bins * Geo<4>::NW * Geo<4>::TPB;
-    case 8: return (bins + Geo<8>::TPB - 1) / Geo<8>::TPB * Geo<8>::NW * Geo<8>::TPB;
-    default: return bins * Geo<2>::NW * Geo<2>::TPB;
+    case 1: return bins * Geo<1>::NW;
+    case 4: return bins * Geo<4>::NW;
+    case 8: return bins * Geo<8>::NW;
+    default: return bins * Geo<2>::NW;
   }
 }
 

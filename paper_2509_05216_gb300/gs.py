@@ -74,7 +74,8 @@ class gs_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
-GS_OPT_RASTER_FWD, GS_OPT_RASTER_BWD, GS_OPT_BWD_DIRECT, GS_OPT_SORT_ITEMS, GS_OPT_SORT_WAIT = 0, 1, 2, 3, 4
+GS_OPT_RASTER_FWD, GS_OPT_RASTER_BWD, GS_OPT_BWD_DIRECT, GS_OPT_SORT_ITEMS, GS_OPT_SORT_WAIT, GS_OPT_TILE_ORDER = \
+    0, 1, 2, 3, 4, 5
 
 class gs_serve_cfg(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch_views", ctypes.c_int32), ("max_queue", ctypes.c_int32),

@@ -39,7 +39,8 @@ class State:
         self.v = torch.zeros_like(self.p)
 
 
-def test_graph_step_matches_call_by_call():
+@pytest.mark.parametrize("tile_order", [0, 1])
+def test_graph_step_matches_call_by_call(tile_order):
     ref, cur, cams = setup()
     n, deg = cur["n"], cur["deg"]
     plain = gs.Context(0)
@@ -57,6 +58,7 @@ def test_graph_step_matches_call_by_call():
     d_b = torch.empty(total, device="cuda")
     loss_b = torch.zeros(1, device="cuda")
     gctx = gs.Context(0, instance_capacity=2 * inst + 1024)
+    gctx.gs_set_option(gs.GS_OPT_TILE_ORDER, tile_order)
     scratch = torch.empty(total, device="cuda")
     gctx.gs_train_graph_capture(b.p, b.g, b.m, b.v, n, deg, HP, cams, scratch, img_b, d_b, loss_b)
     for step in range(1, 4):

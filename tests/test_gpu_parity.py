@@ -355,6 +355,39 @@ def test_pair_stats_count_entries_and_contributions(ctx, oracle):
     assert abs(contrib - ref) <= 1e-3 * ref
 
 
+@pytest.mark.parametrize("variant", [2, 8])
+def test_longest_first_tile_order_gives_the_same_results(ctx, variant):
+    """GS_OPT_TILE_ORDER = 1 only reorders the tiles the compositing kernels
+    take: the image, T_final, n_last, the fused L1 loss and its gradient are
+    bit-identical, the backward's gradients equal up to FP32 summation
+    order."""
+    scene, cams = SCENES["random_deg3_mixed"]()
+    _, total = gs.image_offsets(cams)
+    rng = np.random.default_rng(23)
+    tgt = torch.from_numpy(rng.uniform(0, 1, total).astype(np.float32)).cuda()
+    p = torch.from_numpy(scene["params"]).cuda()
+    out = []
+    for order in (0, 1):
+        ctx.gs_set_option(gs.GS_OPT_TILE_ORDER, order)
+        ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, variant)
+        ctx.gs_set_option(gs.GS_OPT_RASTER_BWD, variant)
+        ctx.gs_project(p, scene["n"], scene["deg"], cams)
+        ctx.gs_bin_sort()
+        img, loss, dimg = torch.empty(total, device="cuda"), torch.zeros(1, device="cuda"), torch.empty(total, device="cuda")
+        ctx.gs_raster_fwd_l1(img, tgt, loss, dimg)
+        grads = torch.zeros_like(p)
+        ctx.gs_raster_bwd(p, scene["n"], scene["deg"], dimg, grads)
+        ctx.gs_sync()
+        out.append((img, loss, dimg, grads, ctx.gs_get_buffer(gs.GS_BUF_TFINAL), ctx.gs_get_buffer(gs.GS_BUF_NLAST)))
+    ctx.gs_set_option(gs.GS_OPT_TILE_ORDER, 0)
+    ctx.gs_set_option(gs.GS_OPT_RASTER_FWD, 2)
+    ctx.gs_set_option(gs.GS_OPT_RASTER_BWD, 2)
+    a, b = out
+    for k in (0, 1, 2, 4, 5):
+        assert torch.equal(a[k], b[k]), k
+    assert (torch.linalg.norm(a[3] - b[3]) / torch.linalg.norm(a[3])).item() <= 1e-5
+
+
 def test_raster_variants_agree(ctx, oracle):
     scene, cams = SCENES["random_deg3_mixed"]()
     out = {}
@@ -384,6 +417,9 @@ def test_options_reject_bad_values(ctx):
     assert 0 <= ctx.gs_get_option(gs.GS_OPT_BWD_DIRECT) <= 32
     with pytest.raises(gs.GsError):
         ctx.gs_set_option(gs.GS_OPT_SORT_ITEMS, 8)
+    with pytest.raises(gs.GsError):
+        ctx.gs_set_option(gs.GS_OPT_TILE_ORDER, 2)
+    assert ctx.gs_get_option(gs.GS_OPT_TILE_ORDER) in (0, 1)
     assert ctx.gs_get_option(gs.GS_OPT_SORT_ITEMS) in (12, 16, 20, 24)
 
 
