@@ -317,6 +317,44 @@ gs_status gs_iso_crossings(gs_ctx* ctx, const float* volume, int32_t nx, int32_t
 gs_status gs_init_gaussians(gs_ctx* ctx, const float* points, const float* normals, int64_t m, const int64_t* select,
                             int64_t n, float flatten, float opacity_logit, gs_params* out);
 
+/* Adaptive density control of 3D-GS (the paper is silent on it; N is set
+ * by the point cloud unless the caller densifies).  gs_set_densify_stats:
+ * every following gs_raster_bwd adds, per Gaussian i, to grad_accum[i] the
+ * norms of its screen-space mean gradient in normalised device coordinates,
+ * ||(dL/dmu2D_x W/2, dL/dmu2D_y H/2)||, over the views of the batch where it
+ * touches a tile, and to count[i] the number of those views (device arrays of
+ * at least n floats owned by the caller, who zeroes them; both NULL
+ * disables; fixed once a training graph is captured).
+ * gs_densify writes the new set of one densification step into p_out,
+ * m_out, v_out (device, the layout of p, capacity = their common stride; their
+ * n is ignored) and *n_out (host) = its size.  For Gaussian i, avg =
+ * grad_accum[i] / count[i] (0 when count is 0), smax = largest exp(log-scale):
+ *   opacity sigma(o_i) < min_opacity   -> removed;
+ *   avg >= grad_threshold and smax <= percent_dense * scene_extent -> kept,
+ *     then a copy with zero moments (clone);
+ *   avg >= grad_threshold, larger -> replaced by split_n Gaussians with means
+ *     mu + R(q/|q|) (exp(s) * z_k), z_k = noise[i][k][0..3) (device, standard
+ *     normals the caller draws, [n][split_n][3]), log-scales s - log(0.8
+ *     split_n), the other parameters copied, zero moments (split);
+ *   otherwise kept with its moments.
+ * The outputs keep the input order, a Gaussian's outputs together.
+ * Synchronises the stream (reads the new size); ends the context's current
+ * batch.  Errors: GS_EINVAL, GS_ECAPACITY (the new set exceeds the output
+ * stride; *n_out is set, nothing written), GS_ENOMEM, GS_ECUDA. */
+typedef struct {
+  float grad_threshold; /* 3D-GS: 0.0002 */
+  float percent_dense;  /* 0.01 */
+  float scene_extent;   /* world units */
+  float min_opacity;    /* 0.005 */
+  int32_t split_n;      /* 2 (1..4) */
+  int32_t reserved;
+} gs_densify_hp;
+
+gs_status gs_set_densify_stats(gs_ctx* ctx, float* grad_accum, float* count);
+gs_status gs_densify(gs_ctx* ctx, const gs_params* p, const gs_params* m, const gs_params* v, const float* grad_accum,
+                     const float* count, const float* noise, const gs_densify_hp* hp, gs_params* p_out,
+                     gs_params* m_out, gs_params* v_out, int64_t* n_out);
+
 /* Step 5, Adam with bias correction (torch.optim.Adam semantics), dense over
  * all planes (or visible-only, see gs_adam_hp), per-group learning rate;
  * step counts from 1.  p, m, v are updated in place; g is read.  All four

@@ -64,6 +64,8 @@ struct gs_ctx {
   int sort_items = 16;  // keys per thread of a sort partition
   int sort_wait = 1 << 20;  // look-back rounds before a sort gives up
   int tile_order_mode = 0;  // 0: composite tiles in bin order; 1: longest lists first
+  float* dens_grad = nullptr;   // densification statistic accumulated by gs_raster_bwd (caller-owned)
+  float* dens_count = nullptr;
   bool tile_order_ready = false;
   int64_t batch_cap = 0;    // instance capacity of the next sorts (0: cfg.instance_capacity)
   bool forward_only = false;  // no contribution cells: gs_raster_bwd unavailable (render server)
@@ -773,6 +775,8 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   b.g2d = P<float>(c->g2d);
   b.grads = grads->data;
   b.vismask = P<uint64_t>(c->vismask);
+  b.dens_grad = c->dens_grad;
+  b.dens_count = c->dens_count;
   if (grads->stride > grads->n) {
     // padding columns are not written by the kernel; keep them zero
     GS_CUDA(c, cudaMemsetAsync(grads->data, 0, sizeof(float) * n_planes(c->deg) * grads->stride, c->stream));
@@ -1187,6 +1191,96 @@ gs_status gs_init_gaussians(gs_ctx* c, const float* points, const float* normals
     launch_init_params(a, c->stream);
   }
   GS_CHECK_LAUNCH(c);
+  return GS_OK;
+}
+
+// ---------------------------------------------------------------- densification
+
+gs_status gs_set_densify_stats(gs_ctx* c, float* grad_accum, float* count) {
+  if (!c) return GS_EINVAL;
+  if ((grad_accum == nullptr) != (count == nullptr)) return fail(c, GS_EINVAL, "both arrays or neither");
+  if (c->capturing || c->gexec) return fail(c, GS_ESTATE, "the statistic arrays are fixed once a graph is captured");
+  c->dens_grad = grad_accum;
+  c->dens_count = count;
+  return GS_OK;
+}
+
+static gs_status check_out_set(gs_ctx* c, const gs_params* o, int deg, const char* what) {
+  if (!o || !o->data) return fail(c, GS_EINVAL, "%s is NULL", what);
+  if (o->stride < 4 || o->stride % 4 != 0 || reinterpret_cast<uintptr_t>(o->data) % 16 != 0)
+    return fail(c, GS_EINVAL, "%s: stride must be a positive multiple of 4, data 16-byte aligned", what);
+  if (o->sh_degree != deg) return fail(c, GS_EINVAL, "%s: SH degree differs from the input set", what);
+  return GS_OK;
+}
+
+gs_status gs_densify(gs_ctx* c, const gs_params* p, const gs_params* m, const gs_params* v, const float* grad_accum,
+                     const float* count, const float* noise, const gs_densify_hp* hp, gs_params* p_out,
+                     gs_params* m_out, gs_params* v_out, int64_t* n_out) {
+  if (!c) return GS_EINVAL;
+  GS_TRY(check_params(c, p, "p"));
+  GS_TRY(check_params(c, m, "m"));
+  GS_TRY(check_params(c, v, "v"));
+  if (m->n != p->n || v->n != p->n || m->stride != p->stride || v->stride != p->stride ||
+      m->sh_degree != p->sh_degree || v->sh_degree != p->sh_degree)
+    return fail(c, GS_EINVAL, "p, m, v must share n, stride and sh_degree");
+  if (!grad_accum || !count || !noise || !hp || !n_out) return fail(c, GS_EINVAL, "NULL argument");
+  if (hp->split_n < 1 || hp->split_n > 4) return fail(c, GS_EINVAL, "split_n must be 1..4");
+  GS_TRY(check_out_set(c, p_out, p->sh_degree, "p_out"));
+  GS_TRY(check_out_set(c, m_out, p->sh_degree, "m_out"));
+  GS_TRY(check_out_set(c, v_out, p->sh_degree, "v_out"));
+  if (m_out->stride != p_out->stride || v_out->stride != p_out->stride)
+    return fail(c, GS_EINVAL, "p_out, m_out, v_out must share the stride");
+  set_device(c);
+  const int64_t nb = (p->n + 255) / 256;
+  GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * nb));
+  GS_TRY(ensure(c, c->block_offsets, sizeof(uint32_t) * nb));
+  GS_TRY(ensure(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
+                                 sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
+  DensifyArgs a{};
+  a.p = p->data;
+  a.m = m->data;
+  a.v = v->data;
+  a.n = p->n;
+  a.stride = p->stride;
+  a.planes = n_planes(p->sh_degree);
+  a.grad = grad_accum;
+  a.count = count;
+  a.noise = noise;
+  a.tau = hp->grad_threshold;
+  a.dense_extent = hp->percent_dense * hp->scene_extent;
+  a.min_opacity = hp->min_opacity;
+  a.split_n = hp->split_n;
+  a.log_shrink = (float)std::log(0.8 * hp->split_n);
+  a.block_counts = P<uint32_t>(c->block_sums);
+  a.block_offsets = P<uint32_t>(c->block_offsets);
+  uint64_t* total = P<uint64_t>(c->total);
+  {
+    LaunchScope ls(c, "densify");
+    launch_densify(a, false, c->stream);
+  }
+  {
+    LaunchScope ls(c, "scan_block_sums", 2);
+    launch_scan_block_sums(P<uint32_t>(c->block_sums), nb, 1, P<uint32_t>(c->block_offsets), total + 1,
+                           reinterpret_cast<uint32_t*>(total + 1 + kMaxViews), total, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  uint64_t cnt = 0;
+  GS_CUDA(c, cudaMemcpyAsync(&cnt, total, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  GS_CUDA(c, cudaStreamSynchronize(c->stream));
+  *n_out = (int64_t)cnt;
+  if ((int64_t)cnt > p_out->stride)
+    return fail(c, GS_ECAPACITY, "%llu Gaussians after densification exceed the output stride",
+                (unsigned long long)cnt);
+  a.po = p_out->data;
+  a.mo = m_out->data;
+  a.vo = v_out->data;
+  a.out_stride = p_out->stride;
+  {
+    LaunchScope ls(c, "densify");
+    launch_densify(a, true, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  c->projected = c->sorted = c->rastered = c->cells_ready = false;
   return GS_OK;
 }
 

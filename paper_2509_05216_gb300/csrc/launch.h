@@ -30,6 +30,8 @@ struct ProjectBwdArgs {
   const float* g2d;   // [B][stride] geometry records (kG2dGeo floats), then [B][stride] colour records (kG2dCol)
   float* grads;       // [P][stride]
   const uint64_t* vismask;  // [stride] views where the Gaussian touches a tile (others: zero 2D gradient)
+  float* dens_grad;   // densification statistic (NULL: not accumulated): += sum of NDC mean-gradient norms
+  float* dens_count;  //   and += the number of views where the Gaussian touches a tile
 };
 
 struct DuplicateArgs {
@@ -216,6 +218,27 @@ struct InitArgs {
 };
 void launch_init_params(const InitArgs& a, cudaStream_t s);
 void launch_init_gather(const float* pts, const int64_t* sel, int64_t n, float* out, cudaStream_t s);
+
+// Adaptive density control (densify.cu).
+struct DensifyArgs {
+  const float* p;
+  const float* m;
+  const float* v;
+  int64_t n, stride;
+  int planes;
+  const float* grad;   // [n] summed statistic
+  const float* count;  // [n] views counted
+  const float* noise;  // [n][split_n][3] standard normals
+  float tau, dense_extent, min_opacity, log_shrink;
+  int split_n;
+  uint32_t* block_counts;
+  const uint32_t* block_offsets;
+  float* po;
+  float* mo;
+  float* vo;
+  int64_t out_stride;
+};
+void launch_densify(const DensifyArgs& a, bool emit, cudaStream_t s);
 
 struct AdamArgs {
   float* p;

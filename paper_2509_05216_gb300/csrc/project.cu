@@ -393,6 +393,10 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
   float cur[6], nxt[6];
   int vn = __ffsll((long long)vm) - 1;
   load6(vn, cur);
+  // densification statistic: the screen-space mean gradient in normalised
+  // device coordinates, summed over the views where the Gaussian touches a
+  // tile, and the number of those views
+  float dens_g = 0.f, dens_c = 0.f;
   while (vn >= 0) {  // the views where the Gaussian touches a tile
     const int v = vn;
     vm &= vm - 1;
@@ -401,6 +405,12 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
     const float gmx = cur[0], gmy = cur[1], gA = cur[2], gB = cur[3], gC = cur[4], gsig = cur[5];
 #pragma unroll
     for (int q = 0; q < 6; q++) cur[q] = nxt[q];
+    if (a.dens_grad) {
+      const ViewRec& Vd = a.views[v];
+      const float nx = gmx * 0.5f * (float)Vd.W, ny = gmy * 0.5f * (float)Vd.H;
+      dens_g += sqrtf(fmaf(nx, nx, ny * ny));
+      dens_c += 1.f;
+    }
     if (gmx == 0.f && gmy == 0.f && gA == 0.f && gB == 0.f && gC == 0.f && gsig == 0.f) continue;
     const ViewRec& V = a.views[v];
     const float depth = depth_key(V, mean[0], mean[1], mean[2]);
@@ -490,6 +500,10 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
   const float dq = gqn[0] * gc.qn[0] + gqn[1] * gc.qn[1] + gqn[2] * gc.qn[2] + gqn[3] * gc.qn[3];
 #pragma unroll
   for (int i = 0; i < 3; i++) G[i * S + g] += gm[i];
+  if (a.dens_grad) {
+    a.dens_grad[g] += dens_g;
+    a.dens_count[g] += dens_c;
+  }
 #pragma unroll
   for (int i = 0; i < 3; i++) G[(3 + i) * S + g] = gls[i];
 #pragma unroll

@@ -70,6 +70,12 @@ def adam_hp_struct(hp: dict) -> gs_adam_hp:
                       flags)
 
 
+class gs_densify_hp(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("percent_dense", ctypes.c_float),
+                ("scene_extent", ctypes.c_float), ("min_opacity", ctypes.c_float), ("split_n", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class gs_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -87,7 +93,8 @@ EXPORTS = ["gs_raster_fwd_l1", "gs_train_graph_capture", "gs_train_graph_launch"
            "gs_serve_stats", "gs_set_option", "gs_get_option", "gs_l1_loss_noalloc", "gs_profile_enable", "gs_profile_read", "gs_profile_reset", "gs_create", "gs_destroy", "gs_last_error", "gs_set_stream", "gs_sync", "gs_project",
            "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_l1_loss", "gs_adam", "gs_get_buffer",
            "gs_get_counts", "gs_pair_stats", "gs_serve_timeline", "gs_ssim_loss",
-           "gs_image_metrics", "gs_iso_crossings", "gs_init_gaussians"]
+           "gs_image_metrics", "gs_iso_crossings", "gs_init_gaussians",
+           "gs_set_densify_stats", "gs_densify"]
 
 
 def load(path: str | None = None):
@@ -134,6 +141,9 @@ def load(path: str | None = None):
     L.gs_profile_reset.argtypes = [vp]
     L.gs_pair_stats.argtypes = [vp, P(i64), P(i64)]
     L.gs_ssim_loss.argtypes = [vp, vp, vp, ctypes.c_float, vp, vp]
+    L.gs_set_densify_stats.argtypes = [vp, vp, vp]
+    L.gs_densify.argtypes = [vp, P(gs_params), P(gs_params), P(gs_params), vp, vp, vp, P(gs_densify_hp),
+                             P(gs_params), P(gs_params), P(gs_params), P(i64)]
     L.gs_iso_crossings.argtypes = [vp, vp, i32, i32, i32, ctypes.c_float, P(ctypes.c_float), P(ctypes.c_float),
                                    vp, vp, i64, P(i64)]
     L.gs_init_gaussians.argtypes = [vp, vp, vp, i64, vp, i64, ctypes.c_float, ctypes.c_float, P(gs_params)]
@@ -347,6 +357,32 @@ class Context:
                                              ctypes.c_void_p(normals.data_ptr()), points.shape[0], sp, n,
                                              float(flatten), float(opacity_logit), ctypes.byref(o)),
                     "gs_init_gaussians")
+
+    def gs_set_densify_stats(self, grad_accum, count):
+        """Accumulate the densification statistic into these float32 CUDA
+        tensors in every following gs_raster_bwd (None, None: stop)."""
+        ga = ctypes.c_void_p(grad_accum.data_ptr()) if grad_accum is not None else None
+        ct = ctypes.c_void_p(count.data_ptr()) if count is not None else None
+        self._keep_stats = (grad_accum, count)
+        self._check(self.L.gs_set_densify_stats(self.h, ga, ct), "gs_set_densify_stats")
+
+    def gs_densify(self, p, m, v, n, deg, grad_accum, count, noise, hp: dict, p_out, m_out, v_out) -> int:
+        """One densification step into the output tensors; returns the new size."""
+        self._bind_stream()
+        sp, sm, sv = (params_struct(t, n, deg) for t in (p, m, v))
+        so, smo, svo = (gs_params(t.data_ptr(), 1, t.shape[1], deg, 0) for t in (p_out, m_out, v_out))
+        h = gs_densify_hp(hp.get("grad_threshold", 2e-4), hp.get("percent_dense", 0.01), hp["scene_extent"],
+                          hp.get("min_opacity", 0.005), hp.get("split_n", 2), 0)
+        nout = ctypes.c_int64()
+        st = self.L.gs_densify(self.h, ctypes.byref(sp), ctypes.byref(sm), ctypes.byref(sv),
+                               ctypes.c_void_p(grad_accum.data_ptr()), ctypes.c_void_p(count.data_ptr()),
+                               ctypes.c_void_p(noise.data_ptr()), ctypes.byref(h), ctypes.byref(so),
+                               ctypes.byref(smo), ctypes.byref(svo), ctypes.byref(nout))
+        if st != GS_OK:
+            e = GsError(st, "gs_densify: %s" % self.L.gs_last_error(self.h).decode())
+            e.n_out = nout.value
+            raise e
+        return nout.value
 
     def gs_sync(self):
         self._check(self.L.gs_sync(self.h), "gs_sync")
