@@ -514,6 +514,28 @@ def gpu_arm(args):
 
     init = init_bench(ctx, scene, dev) if not args.no_init_bench else None
 
+    # one adaptive-density-control step after a batch's statistic
+    ga = torch.zeros(tr.n, device=dev)
+    gc = torch.zeros(tr.n, device=dev)
+    ctx.gs_set_densify_stats(ga, gc)
+    tr.step(*batch(args.warmup), img, dimg)
+    ctx.gs_set_densify_stats(None, None)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    noise = torch.randn((tr.n, 2, 3), device=dev, generator=gen)
+    cap = 3 * tr.p.shape[1]
+    outs = [torch.empty((tr.p.shape[0], cap), device=dev) for _ in range(3)]
+    dhp = dict(grad_threshold=2e-4, percent_dense=0.01, scene_extent=1.1 * 2.0, min_opacity=0.005, split_n=2)
+    ctx.gs_densify(tr.p, tr.m, tr.v, tr.n, tr.deg, ga, gc, noise, dhp, *outs)  # warm-up
+    torch.cuda.synchronize(dev)
+    t_d = time.perf_counter()
+    n_new = ctx.gs_densify(tr.p, tr.m, tr.v, tr.n, tr.deg, ga, gc, noise, dhp, *outs)
+    torch.cuda.synchronize(dev)
+    densify = {"gaussians_in": int(tr.n), "gaussians_out": int(n_new), "wall_ms": round(1e3 * (time.perf_counter() - t_d), 3),
+               "hp": dhp, "note": "statistic from one B-view step; counting pass, scan, host read of the new size, "
+                                  "emitting pass into a second set of parameters and moments"}
+    del outs
+
     # plain path: one view per launch, Adam after each view
     ctx2 = gs.Context(local)
     tr2 = Trainer(ctx2, trained, dev)
@@ -580,7 +602,7 @@ def gpu_arm(args):
                  "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
         "instances_per_step": int(inst), "pair_entries_per_step": int(pairs[0]),
         "contributing_pairs_per_step": int(pairs[1]), "sort_passes_executed": executed,
-        "kernels": per_kernel, "visible_only_adam": visible_only, "dssim": dssim, "init": init,
+        "kernels": per_kernel, "visible_only_adam": visible_only, "dssim": dssim, "init": init, "densify": densify,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},
         "autotune_ms": autotune.report(key),
         "memory": memory,
