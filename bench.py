@@ -5,9 +5,10 @@ Workload (Kingsnake-scale stand-in): 4,000,000 Gaussians on the 0.5 level of
 a seeded 200-blob field, SH degree 3, FP32 parameters and Adam state; 256
 orbit cameras (16 azimuths x 16 elevations, radius 4, 60 degree FOV) at
 2048x2048; targets are renders of the reference set, the trained set starts
-from a seeded +-5% perturbation of it.  One step = projection, binning (scan,
-duplication, onesweep sort, ranges), forward compositing, L1 loss, backward
-compositing, projection backward and Adam, over a batch of B=16 views.
+from a seeded +-5% perturbation of it.  One step = projection, binning (scans,
+depth sort of the visible Gaussians, emission of the tile instances, tile
+sort, ranges), forward compositing, L1 loss, backward compositing,
+projection backward and Adam, over a batch of B=16 views.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
                     [--workload blobs4M|gyroid500k|noise18M] [--serve-sweep]
@@ -276,10 +277,11 @@ def raster_work(kind, entries, contributing):
     return full * contributing + RASTER_OPS_TEST * (entries - contributing)
 
 
-def algorithmic_work(name, n, P, B, I, pairs, pixels):
+def algorithmic_work(name, n, P, B, I, pairs, pixels, V=0):
     """(bound, work per launch scope): bytes for the HBM-bound kernels, FP32
-    operations for the compositing kernels.  I = tile instances; pairs =
-    (entries up to each pixel's last contributor, contributing pairs)."""
+    operations for the compositing kernels.  I = tile instances; V = visible
+    (view, Gaussian) pairs; pairs = (entries up to each pixel's last
+    contributor, contributing pairs)."""
     if name == "project_fwd":
         # parameters once; per (view, Gaussian) the 48-byte record, the
         # 16-byte (radius, tiles, rect) entry and the (tiles, depth) pair
@@ -288,16 +290,23 @@ def algorithmic_work(name, n, P, B, I, pairs, pixels):
         return "hbm", n * (8 * P + B * 36.0)
     if name == "adam":
         return "hbm", 28.0 * P * n
-    if name == "duplicate":
-        # tile count, depth bits and packed tile rect per (view, Gaussian);
-        # key and value per instance written
-        return "hbm", n * B * 16.0 + 12.0 * I
-    if name == "digit_histogram":
-        return "hbm", 8.0 * I
-    if name == "onesweep_pass":
-        return "hbm", 24.0 * I
+    if name == "compact":
+        # (tile count, depth bits) per (view, Gaussian) read; (depth bits,
+        # Gaussian) per visible pair written
+        return "hbm", n * B * 8.0 + 8.0 * V
+    if name == "depth_histogram":
+        return "hbm", 4.0 * V
+    if name == "depth_pass":
+        # 32-bit key and value read and written per visible pair
+        return "hbm", 16.0 * V
+    if name == "emit":
+        # sorted Gaussian and its 16-byte (radius, tiles, rect) entry per
+        # visible pair; 32-bit bin and Gaussian per instance written
+        return "hbm", 20.0 * V + 8.0 * I
+    if name == "tile_pass":
+        return "hbm", 16.0 * I
     if name == "tile_ranges":
-        return "hbm", 8.0 * I
+        return "hbm", 4.0 * I
     if name == "raster_fwd":
         return "alu", raster_work("fwd", *pairs)
     if name == "raster_bwd":
@@ -431,11 +440,15 @@ def gpu_arm(args):
                               "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in kstats), 1e-9), 4)}
                   for k in kstats}
     ctrl = ctx.gs_get_buffer(gs.GS_BUF_SORT_CTRL).cpu().numpy()
-    executed = {"onesweep_pass": int(sum((ctrl[p] & 2) == 0 for p in range(ctrl.size - 1)))}
+    dctrl = ctx.gs_get_buffer(gs.GS_BUF_DEPTH_CTRL).cpu().numpy()
+    executed = {"tile_pass": int(sum((ctrl[p] & 2) == 0 for p in range(ctrl.size - 1))),
+                "depth_pass": int(sum((dctrl[p] & 2) == 0 for p in range(dctrl.size - 1)))}
+    vm = ctx.gs_get_buffer(gs.GS_BUF_VISMASK).cpu().numpy().view(np.uint64)
+    vis_pairs = int(sum(int(((vm >> np.uint64(v)) & np.uint64(1)).sum()) for v in range(B)))
     peak_hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
     for k in kstats:
-        kk, w = algorithmic_work(k["name"], tr.n, P, B, inst, pairs, pixels)
+        kk, w = algorithmic_work(k["name"], tr.n, P, B, inst, pairs, pixels, vis_pairs)
         if kk is None or k["total_ms"] <= 0:
             continue
         runs = executed.get(k["name"], 1) * args.steps  # one launch scope per step, sort passes as executed
@@ -446,7 +459,7 @@ def gpu_arm(args):
             e["frac_hbm"] = round(rate / 1e9 / peak_hbm, 3)
         else:
             e["TFLOP_s"] = round(rate / 1e12, 2)
-    kind, work = algorithmic_work(dom["name"], tr.n, P, B, inst, pairs, pixels)
+    kind, work = algorithmic_work(dom["name"], tr.n, P, B, inst, pairs, pixels, vis_pairs)
     avg_ms = dom["total_ms"] / max(dom["launches"], 1)
     peaks = {}
     try:
@@ -600,7 +613,8 @@ def gpu_arm(args):
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
         "graph": "each timed step is one CUDA-graph launch of the whole step; per-kernel times and the roofline "
                  "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
-        "instances_per_step": int(inst), "pair_entries_per_step": int(pairs[0]),
+        "instances_per_step": int(inst), "visible_pairs_per_step": vis_pairs,
+        "pair_entries_per_step": int(pairs[0]),
         "contributing_pairs_per_step": int(pairs[1]), "sort_passes_executed": executed,
         "kernels": per_kernel, "visible_only_adam": visible_only, "dssim": dssim, "init": init, "densify": densify,
         "setup_s": round(time.time() - t0, 1), "tuned_options": {str(k): v for k, v in tuned.items()},

@@ -185,14 +185,19 @@ gs_status gs_get_option(gs_ctx* ctx, int32_t option, int64_t* value);
  * stride/alignment, width/height <= 0), GS_ENOMEM, GS_ECUDA. */
 gs_status gs_project(gs_ctx* ctx, const gs_params* params, const gs_camera* cams, int32_t B);
 
-/* Step 2, binning: exclusive scan of per-(view, Gaussian) tile counts,
- * duplication into one instance per touched tile with the 64-bit key
- * (bin << 32) | FP32 depth bits (bin = the view's first tile + ty * gw + tx)
- * and value = Gaussian index, an LSD onesweep radix sort on the key bits
- * that vary, and per-bin [start, end) ranges of the sorted list.  With a
- * grow-on-demand context this call reads the instance count on the host
- * (one stream synchronisation).  Errors: GS_ESTATE (no gs_project),
- * GS_ENOMEM, GS_ECUDA; device-side GS_ECAPACITY via gs_sync. */
+/* Step 2, binning (Section I: per-tile lists ordered by depth): each
+ * tile's list holds the Gaussians whose tile rect covers it, ordered by
+ * (FP32 depth, Gaussian index) -- the order of a stable sort of the 64-bit
+ * keys (bin << 32) | depth bits (bin = the view's first tile + ty * gw + tx)
+ * of one instance per touched tile.  Computed as: exclusive scans of the
+ * per-(view, Gaussian) tile counts and visible flags, a stable LSD onesweep
+ * radix sort of each view's visible Gaussians by depth bits, emission of
+ * one (bin, Gaussian) instance per touched tile in that order, a stable
+ * onesweep sort of the instances by bin, and per-bin [start, end) ranges of
+ * the sorted list.  With a grow-on-demand context this call reads the
+ * instance count on the host (one stream synchronisation).  Errors:
+ * GS_ESTATE (no gs_project), GS_ENOMEM, GS_ECUDA; device-side GS_ECAPACITY
+ * and GS_ETIMEOUT via gs_sync. */
 gs_status gs_bin_sort(gs_ctx* ctx);
 
 /* Step 3, forward compositing.  Per pixel, over its tile's sorted list:
@@ -493,7 +498,7 @@ typedef enum {
   GS_BUF_REC1 = 1,   /* float4 [B][N]: cC = -C log2(e) / 2, opacity, red, green */
   GS_BUF_REC2 = 2,   /* float4 [B][N]: blue, hx, hy (half-extents of the box around
                         the alpha >= 1/255 ellipse), depth */
-  GS_BUF_KEYS = 3,   /* uint64 [I]: sorted keys */
+  GS_BUF_KEYS = 3,   /* uint32 [I]: bin of each sorted instance */
   GS_BUF_VALS = 4,   /* uint32 [I]: sorted Gaussian indices */
   GS_BUF_RANGES = 5, /* uint32 [bins][2]: [start, end) per bin */
   GS_BUF_TFINAL = 6, /* float [pixels]: transmittance after the last contributor */
@@ -502,11 +507,14 @@ typedef enum {
                         then [B][N][4] records dL/d(r, g, b), 0 */
   GS_BUF_REC3 = 9,   /* int4 [B][N]: radius, tiles touched (0: culled), tile rect
                         x0 | x1 << 16 and y0 | y1 << 16 (half-open) */
-  GS_BUF_SORT_CTRL = 10, /* uint32 [npass + 1]: control word of each sort pass; bit 1
-                        set = pass skipped (its digit is the same for every key),
-                        bit 0 = source buffer */
-  GS_BUF_VISMASK = 11 /* uint64 [N]: bit v = the Gaussian touches a tile of view v
+  GS_BUF_SORT_CTRL = 10, /* uint32 [npass + 1]: control word of each pass of the
+                        instances' sort by bin; bit 1 set = pass skipped (its
+                        digit is the same for every key of each view), bit 0 =
+                        source buffer */
+  GS_BUF_VISMASK = 11, /* uint64 [N]: bit v = the Gaussian touches a tile of view v
                         of the last projected batch */
+  GS_BUF_DEPTH_CTRL = 12 /* uint32 [5]: control words of the 4 passes of the visible
+                        Gaussians' sort by depth bits, as GS_BUF_SORT_CTRL */
 } gs_buffer;
 
 /* *ptr = device pointer of the buffer, *count = number of elements (of the

@@ -1,17 +1,22 @@
-// Binning: scan of tile counts, duplication into (tile, depth) keyed
-// instances, an LSD onesweep radix sort and per-tile ranges.
+// Binning: scan of tile counts, a per-view depth sort of the visible
+// Gaussians, emission of one instance per touched tile in depth order, a
+// stable LSD onesweep radix sort of the instances by tile and per-tile
+// ranges.
 //
-// 3D-GS renders tile by tile from a list sorted by (tile, depth) (Section I);
-// each Gaussian is emitted once per 16x16 tile its rect touches with the key
-// (bin << 32) | bits(depth).  Depths are positive FP32 values, so their bit
-// patterns order like the values.  The sort is stable, so equal keys keep the
-// emission order, which is increasing Gaussian index within a bin.
+// 3D-GS renders tile by tile from a list sorted by (tile, depth) (Section I).
+// Sorting (bin << 32 | depth bits) keys of every instance takes the 32 depth
+// bits through every instance, although they are the same for all instances
+// of one (view, Gaussian) pair.  Here the depth order is settled once per
+// visible pair instead: each view's visible Gaussians (in Gaussian order)
+// are sorted by depth bits, the instances are emitted in that order, and a
+// stable sort by tile only (2 passes of 8 bits for up to 65,536 tiles per
+// view) leaves each tile's list in (depth, Gaussian index) order -- the
+// same list as the stable sort of the 64-bit keys.  Depths of visible
+// Gaussians are positive FP32 values, so their bit patterns order like the
+// values.
 //
-// Instances are emitted view by view (view v's instances form one segment),
-// and the sort orders each segment on its own by (bin - view's first bin,
-// depth): the bins of different views never interleave, so the view part of
-// the bin needs no radix pass (5 executed passes instead of 6 for 16 views
-// of 2048^2).
+// Both sorts order each view's segment on its own (the tile sort on bin -
+// view's first bin), so the view part of a bin needs no radix pass.
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -85,99 +90,43 @@ void launch_scan_block_sums(const uint32_t* sums, int64_t nb, int B, uint32_t* o
   segment_offsets_kernel<<<1, 32, 0, s>>>(view_total, B, seg, total);
 }
 
-// ---------------------------------------------------------------- duplicate
+// ---------------------------------------------------------------- compaction
 
 // Same block partition as the projection (256 Gaussians per block).  Each
-// warp emits the instances of its 32 Gaussians view by view into view v's
-// segment (offset: the view's first instance + the block's scanned count +
-// the earlier warps of the block): the warp's (Gaussian, view) items are
-// expanded cooperatively, lane j writing output position base + 32 i + j of
-// the chunk i, so every store of keys and values is coalesced.  Within a
-// view the order is (Gaussian, ty, tx), so in every bin the instances appear
-// in increasing Gaussian index, which the stable sort preserves for equal
-// keys.
-__global__ void __launch_bounds__(256) duplicate_kernel(DuplicateArgs a) {
-  __shared__ uint32_t wtot[kMaxViews][8];
+// view's visible (view, Gaussian) pairs -- tiles touched > 0 -- are written
+// in Gaussian order as (depth bits, Gaussian) into the view's segment of the
+// depth sort's input: offset = the view's first pair + the block's scanned
+// count + the earlier warps of the block + the lane's rank in the warp.
+// Phase 1 takes each warp's ballot per view, phase 2 re-reads the depth bits
+// of the visible lanes (the block's own lines, still in cache) and writes.
+__global__ void __launch_bounds__(256) compact_kernel(CompactArgs a) {
+  __shared__ uint32_t s_mask[kMaxViews][8];
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = g < a.n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nb = gridDim.x;
   for (int v = 0; v < a.B; v++) {
     const uint32_t c = live ? a.tiles[(int64_t)v * a.stride + g].x : 0u;
-    const uint32_t t = __reduce_add_sync(0xffffffffu, c);
-    if (lane == 0) wtot[v][wid] = t;
+    const unsigned m = __ballot_sync(0xffffffffu, c != 0u);
+    if (lane == 0) s_mask[v][wid] = m;
   }
   __syncthreads();
-  // the next view's count, rect and depth are loaded while this view's
-  // instances are written
-  uint32_t n_cnt = 0, n_dbits = 0;
-  int4 n_r3 = make_int4(0, 0, 0, 0);
-  auto load_view = [&](int v) {
-    const int64_t o = (int64_t)v * a.stride + g;
-    const uint2 td = live ? a.tiles[o] : make_uint2(0u, 0u);
-    n_cnt = td.x;
-    n_dbits = td.y;
-    if (n_cnt) n_r3 = a.rec3[o];
-  };
-  load_view(0);
+  const unsigned lt = (1u << lane) - 1u;
   for (int v = 0; v < a.B; v++) {
-    const uint32_t cnt = n_cnt, dbits = n_dbits;
-    const int4 r3 = n_r3;
-    if (v + 1 < a.B) load_view(v + 1);
-    const uint32_t vtot = wtot[v][wid];
-    if (vtot == 0) continue;
+    const unsigned m = s_mask[v][wid];
+    if (!((m >> lane) & 1u)) continue;
     uint32_t wpre = 0;
-    for (int w = 0; w < wid; w++) wpre += wtot[v][w];
-    const int64_t base = (int64_t)a.seg[v] + a.block_offsets[(int64_t)v * nb + blockIdx.x] + wpre;
-    if (base + vtot > a.capacity) {
-      if (lane == 0) atomicOr(a.status, kStatusCapacity);
-      continue;
-    }
-    // exclusive offsets of the warp's items in this view
-    uint32_t inc = cnt;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
-      if (lane >= off) inc += y;
-    }
-    const uint32_t excl = inc - cnt;
-    const ViewRec& V = a.views[v];
-    // the projection's tile rect
-    const int x0 = cnt ? (r3.z & 0xffff) : 0;
-    const int rw = cnt ? (int)((uint32_t)r3.z >> 16) - x0 : 0;
-    const int y0 = cnt ? (r3.w & 0xffff) : 0;
-    for (uint32_t q0 = 0; q0 < vtot; q0 += 32) {
-      const uint32_t q = q0 + lane;
-      // owner: the last lane whose exclusive offset is <= q
-      int own = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = own + step;
-        const uint32_t ec = __shfl_sync(0xffffffffu, excl, cand & 31);
-        if (cand < 32 && ec <= q) own = cand;
-      }
-      const uint32_t e_own = __shfl_sync(0xffffffffu, excl, own);
-      const int ox0 = __shfl_sync(0xffffffffu, x0, own);
-      const int oy0 = __shfl_sync(0xffffffffu, y0, own);
-      const int orw = __shfl_sync(0xffffffffu, rw, own);
-      const uint32_t od = __shfl_sync(0xffffffffu, dbits, own);
-      const uint32_t oc = __shfl_sync(0xffffffffu, cnt, own);
-      if (q < vtot && q - e_own < oc && orw > 0) {
-        const uint32_t local = q - e_own;
-        const int tx = ox0 + (int)(local % (uint32_t)orw);
-        const int ty = oy0 + (int)(local / (uint32_t)orw);
-        const uint64_t bin = (uint64_t)(V.tile_offset + ty * V.gw + tx);
-        a.keys[base + q] = (bin << 32) | (uint64_t)od;
-        a.vals[base + q] = (uint32_t)(g - lane + own);
-      }
-    }
+    for (int w = 0; w < wid; w++) wpre += __popc(s_mask[v][w]);
+    const int64_t pos = (int64_t)a.vseg[v] + a.vis_offsets[(int64_t)v * nb + blockIdx.x] + wpre + __popc(m & lt);
+    a.dkeys[pos] = a.tiles[(int64_t)v * a.stride + g].y;
+    a.dvals[pos] = (uint32_t)g;
   }
 }
 
-void launch_duplicate(const DuplicateArgs& a, cudaStream_t s) {
+void launch_compact(const CompactArgs& a, cudaStream_t s) {
   const int threads = project_fwd_block();
   const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
-  duplicate_kernel<<<blocks, threads, 0, s>>>(a);
+  compact_kernel<<<blocks, threads, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------- onesweep radix sort
@@ -220,12 +169,19 @@ __device__ __forceinline__ int segment_of(const uint32_t* off, int B, uint64_t i
   return lo;
 }
 
+// The key base of segment v: its keys' digits are taken from key - base.
+__device__ __forceinline__ uint64_t segment_key_base(const SortArgs& a, int v) {
+  return a.views ? (uint64_t)(uint32_t)a.views[v].tile_offset << a.view_shift : 0ull;
+}
+
 // Digit counts of every pass of every view in one read of the keys.  hist:
-// [B][npass][256], digits of key - (view's first bin << 32).  Block (x, v)
-// counts view v's segment with a grid stride over the x blocks of the view,
-// in shared memory; the tile digits stay constant over long runs of keys
-// (emission order), so their counts are first aggregated over the lanes
-// holding the same digit.
+// [B][npass][256], digits of key - segment base.  Block (x, v) counts view
+// v's segment with a grid stride over the x blocks of the view, in shared
+// memory.  The two top digits vary slowly along the keys (the tile digits
+// of instances in emission order, the exponent byte of depths), so their
+// counts are first aggregated over the lanes holding the same digit; the
+// others are added lane by lane.
+template <typename KeyT>
 __global__ void __launch_bounds__(256) digit_histogram_kernel(SortArgs a) {
   __shared__ uint32_t sh[8][kRadix];
   for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
@@ -233,17 +189,17 @@ __global__ void __launch_bounds__(256) digit_histogram_kernel(SortArgs a) {
   const int v = blockIdx.y;
   const int64_t count = min((int64_t)*a.count, a.capacity);
   const int64_t lo = min((int64_t)a.seg[v], count), hi = min((int64_t)a.seg[v + 1], count);
-  const uint64_t kb = (uint64_t)a.views[v].tile_offset << 32;
-  const uint64_t* __restrict__ keys = a.keys[0];
+  const KeyT kb = (KeyT)segment_key_base(a, v);
+  const KeyT* __restrict__ keys = static_cast<const KeyT*>(a.keys[0]);
   const int npass = a.npass, lane = threadIdx.x & 31;
   for (int64_t i0 = lo + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < hi;
        i0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = i0 + lane;
     const bool ok = i < hi;
-    const uint64_t k = ok ? keys[i] - kb : 0ull;
+    const KeyT k = ok ? (KeyT)(keys[i] - kb) : (KeyT)0;
     for (int p = 0; p < npass; p++) {
       const uint32_t dg = (uint32_t)(k >> (kRadixBits * p)) & (kRadix - 1);
-      if (p < 4) {
+      if (p < npass - 2) {
         if (ok) atomicAdd(&sh[p][dg], 1u);
       } else {
         const unsigned peers = __match_any_sync(0xffffffffu, ok ? dg : (uint32_t)kRadix);
@@ -266,15 +222,15 @@ __global__ void __launch_bounds__(256) digit_histogram_kernel(SortArgs a) {
 constexpr uint32_t kCtrlParity = 1u, kCtrlTrivial = 2u;
 
 // One LSD pass, each view's segment sorted on its own: a partition lies in
-// one segment; rank its keys by digit of key - (view's first bin << 32)
-// (stable), find its offset for each digit by decoupled look-back over the
-// earlier partitions of its segment (bounded waits), then scatter through
-// shared memory so that the global writes are coalesced.  The 32-bit halves
-// of the keys that hold the pass's digit are loaded up front (all loads in
-// flight before ranking; half the registers of whole keys, which spilled);
-// keys and then values go through one shared buffer (42 KB for 16 keys per
-// thread), and the scatter takes each staged key's digit from the key.
-template <int ITEMS>
+// one segment; rank its keys by digit of key - segment base (stable), find
+// its offset for each digit by decoupled look-back over the earlier
+// partitions of its segment (bounded waits), then scatter through shared
+// memory so that the global writes are coalesced.  Only the 32-bit word of
+// a key that holds the pass's digit is loaded up front (all loads in flight
+// before ranking; for 64-bit keys, half the registers of whole keys, which
+// spilled); keys and then values go through one shared buffer, and the
+// scatter takes each staged key's digit from the key.
+template <typename KeyT, int ITEMS>
 struct SortSmem {
   static constexpr int kTile = kSortThreads * ITEMS;
   uint32_t warp_hist[kSortWarps][kRadix];  // per-warp digit counts -> offsets
@@ -284,24 +240,24 @@ struct SortSmem {
   uint32_t part, seg, seg_lo, seg_hi, first_part;
   uint64_t key_base;
   int timed_out;
-  uint64_t buf[kTile];                     // keys, then values, in tile-sorted order
+  KeyT buf[kTile];                         // keys, then values, in tile-sorted order
 };
 
-template <int ITEMS, int MIN_BLOCKS>
+template <typename KeyT, int ITEMS, int MIN_BLOCKS>
 __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel(SortArgs a, int pass) {
   constexpr int kSortItems = ITEMS;
   constexpr int kSortTile = kSortThreads * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SortSmem<ITEMS>& sm = *reinterpret_cast<SortSmem<ITEMS>*>(smem_raw);
+  SortSmem<KeyT, ITEMS>& sm = *reinterpret_cast<SortSmem<KeyT, ITEMS>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t ctrl = a.ctrl[pass];
   if (ctrl & kCtrlTrivial) return;  // whole block: every view has one digit here
   const int par = (int)(ctrl & kCtrlParity);
   // selects, not a dynamically indexed parameter array (which would be
   // copied to local memory)
-  const uint64_t* __restrict__ kin = par ? a.keys[1] : a.keys[0];
+  const KeyT* __restrict__ kin = static_cast<const KeyT*>(par ? a.keys[1] : a.keys[0]);
   const uint32_t* __restrict__ vin = par ? a.vals[1] : a.vals[0];
-  uint64_t* __restrict__ kout = par ? a.keys[0] : a.keys[1];
+  KeyT* __restrict__ kout = static_cast<KeyT*>(par ? a.keys[0] : a.keys[1]);
   uint32_t* __restrict__ vout = par ? a.vals[0] : a.vals[1];
   const int shift = kRadixBits * pass;
   const uint32_t nparts = a.part_off[a.B];
@@ -316,7 +272,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
       sm.first_part = a.part_off[u];
       sm.seg_lo = min(a.seg[u], cap);
       sm.seg_hi = min(a.seg[u + 1], cap);
-      sm.key_base = (uint64_t)a.views[u].tile_offset << 32;
+      sm.key_base = segment_key_base(a, u);
     }
   }
   for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&sm.warp_hist[0][0])[i] = 0;
@@ -327,23 +283,23 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   const uint32_t lp0 = part - sm.first_part;  // partition index inside the segment
   const int64_t base = (int64_t)sm.seg_lo + (int64_t)lp0 * kSortTile;
   const int n_here = (int)min((int64_t)kSortTile, (int64_t)sm.seg_hi - base);
-  const uint64_t kb = sm.key_base;
+  const KeyT kb = (KeyT)sm.key_base;
   const uint32_t* __restrict__ hist_pass = a.hist_scan + ((int64_t)v * a.npass + pass) * kRadix;
   uint32_t* lookback = a.lookback + (size_t)pass * a.lookback_stride;
   const int wl = wid * kSortItems * 32 + lane;  // item i at base + wl + 32 i
 
-  // the pass's digit lies in one 32-bit half of the key (8-bit digits):
-  // only that half is held in registers for the ranking; the whole key is
-  // read again (from L2) when it is staged in sorted order
-  const int hw = shift >= 32 ? 1 : 0;
+  // the 32-bit word of the key that holds the pass's digit (8-bit digits
+  // never straddle the halves of a 64-bit key)
+  constexpr int kWords = (int)(sizeof(KeyT) / 4);
+  const int hw = kWords == 2 && shift >= 32 ? 1 : 0;
   const int wsh = shift & 31;
-  const uint32_t wsub = hw ? (uint32_t)(kb >> 32) : 0u;
+  const uint32_t wsub = (uint32_t)((uint64_t)kb >> (32 * hw));
   const uint32_t* __restrict__ kin32 = reinterpret_cast<const uint32_t*>(kin) + hw;
   uint32_t word[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; i++) {
     const int p = wl + 32 * i;
-    word[i] = p < n_here ? kin32[2 * (base + p)] - wsub : 0u;
+    word[i] = p < n_here ? kin32[kWords * (base + p)] - wsub : 0u;
   }
   // stable rank inside the warp (warp-striped order), 16-bit per item
   uint32_t rk[kSortItems / 2];
@@ -401,7 +357,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     if (ok) {
       const uint32_t dd = (word[i] >> wsh) & (kRadix - 1);
       lpos = sm.digit_start[dd] + sm.warp_hist[wid][dd] + r;
-      sm.buf[lpos] = kin[base + wl + 32 * i];
+      sm.buf[lpos] = kWords == 1 ? (KeyT)(word[i] + wsub) : kin[base + wl + 32 * i];
     }
     if (i & 1) rk[i >> 1] = (rk[i >> 1] & 0xffffu) | (lpos << 16); else rk[i >> 1] = (rk[i >> 1] & 0xffff0000u) | lpos;
   }
@@ -464,8 +420,8 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     const int q = tid + t * kSortThreads;
     dst[t] = 0xffffffffu;
     if (q < n_here) {
-      const uint64_t k = sm.buf[q];
-      const uint32_t dd = (uint32_t)((k - kb) >> shift) & (kRadix - 1);
+      const KeyT k = sm.buf[q];
+      const uint32_t dd = (uint32_t)((KeyT)(k - kb) >> shift) & (kRadix - 1);
       dst[t] = sm.global_base[dd] + ((uint32_t)q - sm.digit_start[dd]);
       if (dst[t] < hi) kout[dst[t]] = k;
     }
@@ -487,30 +443,36 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   }
 }
 
-template <int ITEMS, int MIN_BLOCKS>
+template <typename KeyT, int ITEMS, int MIN_BLOCKS>
 static void launch_pass(const SortArgs& a, int pass, int64_t grid, cudaStream_t s) {
-  const size_t smem = sizeof(SortSmem<ITEMS>);
+  const size_t smem = sizeof(SortSmem<KeyT, ITEMS>);
   // once per device (the attribute is per device; not repeated inside a graph capture)
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    cudaFuncSetAttribute(onesweep_pass_kernel<ITEMS, MIN_BLOCKS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    cudaFuncSetAttribute(onesweep_pass_kernel<KeyT, ITEMS, MIN_BLOCKS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  onesweep_pass_kernel<ITEMS, MIN_BLOCKS><<<(unsigned)grid, kSortThreads, smem, s>>>(a, pass);
+  onesweep_pass_kernel<KeyT, ITEMS, MIN_BLOCKS><<<(unsigned)grid, kSortThreads, smem, s>>>(a, pass);
+}
+
+template <typename KeyT>
+static void launch_pass_items(const SortArgs& a, int pass, int items, int64_t grid, cudaStream_t s) {
+  switch (items) {
+    case 12: launch_pass<KeyT, 12, 4>(a, pass, grid, s); break;
+    case 20: launch_pass<KeyT, 20, 3>(a, pass, grid, s); break;
+    case 24: launch_pass<KeyT, 24, 2>(a, pass, grid, s); break;
+    default: launch_pass<KeyT, 16, 4>(a, pass, grid, s); break;
+  }
 }
 
 void launch_onesweep_pass(const SortArgs& a, int pass, int items, cudaStream_t s) {
   const int64_t grid = sort_partitions(a.capacity, items, a.B);
   if (grid <= 0) return;
-  switch (items) {
-    case 12: launch_pass<12, 4>(a, pass, grid, s); break;
-    case 20: launch_pass<20, 3>(a, pass, grid, s); break;
-    case 24: launch_pass<24, 2>(a, pass, grid, s); break;
-    default: launch_pass<16, 4>(a, pass, grid, s); break;
-  }
+  if (a.key_bytes == 4) launch_pass_items<uint32_t>(a, pass, items, grid, s);
+  else launch_pass_items<uint64_t>(a, pass, items, grid, s);
 }
 
 // Exclusive scan of each (view, pass)'s 256 digit counts (block v of the
@@ -564,27 +526,261 @@ __global__ void sort_control_kernel(SortArgs a, int items) {
   a.part_off[a.B] = run;
 }
 
+void launch_digit_scan(const SortArgs& a, int items, cudaStream_t s) {
+  digit_scan_kernel<<<a.B, kRadix, 0, s>>>(a);
+  sort_control_kernel<<<1, 32, 0, s>>>(a, items);
+}
+
 void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, int items, cudaStream_t s) {
   const int sms = sm_count();
   // about 8 blocks per SM over all views, at least one per view
   int64_t want = (grid_hint + 4095) / 4096;
   want = want < 1 ? 1 : (want > (int64_t)sms * 8 ? (int64_t)sms * 8 : want);
   const unsigned per_view = (unsigned)std::max<int64_t>(1, want / a.B);
-  digit_histogram_kernel<<<dim3(per_view, a.B), 256, 0, s>>>(a);
-  digit_scan_kernel<<<a.B, kRadix, 0, s>>>(a);
-  sort_control_kernel<<<1, 32, 0, s>>>(a, items);
+  if (a.key_bytes == 4) digit_histogram_kernel<uint32_t><<<dim3(per_view, a.B), 256, 0, s>>>(a);
+  else digit_histogram_kernel<uint64_t><<<dim3(per_view, a.B), 256, 0, s>>>(a);
+  launch_digit_scan(a, items, s);
+}
+
+// ---------------------------------------------------------------- emission
+
+// Emission status words (one per partition): flag in the two top bits, the
+// partition's instance count (aggregate) or the instances of the segment up
+// to and including it (prefix) below.
+constexpr uint64_t kEmitAggregate = 1ull << 62;
+constexpr uint64_t kEmitPrefix = 2ull << 62;
+constexpr uint64_t kEmitFailed = 3ull << 62;
+constexpr uint64_t kEmitValue = (1ull << 62) - 1;
+constexpr int kEmitThreads = 256;
+constexpr int kEmitItems = 8;  // visible pairs per thread
+constexpr int kEmitWarps = kEmitThreads / 32;
+constexpr int kEmitTile = kEmitThreads * kEmitItems;
+static_assert(kEmitWarps * kEmitItems == 64, "the chunk scan takes two chunks per lane");
+
+int64_t emit_partitions(int64_t pairs, int segments) { return (pairs + kEmitTile - 1) / kEmitTile + segments; }
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
+
+// One partition of kEmitTile depth-sorted visible pairs of one view per
+// block (partitions taken by ticket, so every earlier partition is running
+// or done).  Warp w holds chunks of 32 consecutive pairs; each pair's tile
+// rect comes from its (view, Gaussian) entry.  The block scans the chunks'
+// instance counts, warp 0 finds the instances of the view's earlier
+// partitions by decoupled look-back (32 statuses per round, bounded waits),
+// and every warp expands its chunks cooperatively: lane j writes output
+// position base + 32 i + j of round i, (tile, Gaussian) of the pair that
+// owns it, tiles of a rect in row-major order.  The tile digits of the
+// following sort are counted on the way (shared memory, one flush per
+// block).
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
+  __shared__ uint32_t s_part[kMaxViews + 1];
+  __shared__ uint32_t s_chunk[kEmitWarps * kEmitItems];
+  __shared__ uint32_t s_hist[4][kRadix];
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_ticket, s_total;
+  __shared__ int s_failed;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < 4 * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+  if (wid == 0) {
+    // partitions per view (B <= 64: lanes take views lane and lane + 32)
+    uint32_t c[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int v = lane + 32 * h;
+      c[h] = v < a.B ? (a.vseg[v + 1] - a.vseg[v] + kEmitTile - 1) / kEmitTile : 0u;
+    }
+    uint32_t carry = 0;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      uint32_t inc = c[h];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+      }
+      const int v = lane + 32 * h;
+      if (v <= a.B) s_part[v] = carry + inc - c[h];
+      if (v + 1 == a.B) s_part[a.B] = carry + inc;
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) s_ticket = atomicAdd(a.counter, 1u);
+  }
+  __syncthreads();
+  const uint32_t part = s_ticket;
+  if (part >= s_part[a.B]) return;
+  const int v = segment_of(s_part, a.B, part);
+  const uint32_t lp = part - s_part[v];
+  const int64_t lo = (int64_t)a.vseg[v] + (int64_t)lp * kEmitTile;
+  const int n_here = (int)min((int64_t)kEmitTile, (int64_t)a.vseg[v + 1] - lo);
+  const uint32_t* __restrict__ src = (a.dctrl[a.dpass] & kCtrlParity) ? a.dvals[1] : a.dvals[0];
+  const int4* __restrict__ rec3 = a.rec3 + (int64_t)v * a.stride;
+
+  uint32_t gi[kEmitItems], rx[kEmitItems], ry[kEmitItems], cnt[kEmitItems];
+#pragma unroll
+  for (int r = 0; r < kEmitItems; r++) {
+    const int p = (wid * kEmitItems + r) * 32 + lane;
+    gi[r] = 0u;
+    rx[r] = ry[r] = cnt[r] = 0u;
+    if (p < n_here) gi[r] = src[lo + p];
+  }
+#pragma unroll
+  for (int r = 0; r < kEmitItems; r++) {
+    const int p = (wid * kEmitItems + r) * 32 + lane;
+    // (an index at or above n only comes from a depth sort that gave up)
+    if (p < n_here && (int64_t)gi[r] < a.n) {
+      const int4 e = rec3[gi[r]];
+      cnt[r] = (uint32_t)e.y;
+      rx[r] = (uint32_t)e.z;
+      ry[r] = (uint32_t)e.w;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kEmitItems; r++) {
+    const uint32_t t = __reduce_add_sync(0xffffffffu, cnt[r]);
+    if (lane == 0) s_chunk[wid * kEmitItems + r] = t;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    // exclusive scan of the block's chunk counts (kEmitWarps x kEmitItems = 64: two per lane)
+    const uint32_t c0 = s_chunk[2 * lane], c1 = s_chunk[2 * lane + 1];
+    const uint32_t t = c0 + c1;
+    uint32_t inc = t;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    s_chunk[2 * lane] = inc - t;
+    s_chunk[2 * lane + 1] = inc - t + c0;
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    volatile uint64_t* lb = a.lookback;
+    if (lane == 0) lb[part] = (lp == 0 ? kEmitPrefix : kEmitAggregate) | (uint64_t)total;
+    uint64_t excl = 0;
+    bool failed = false;
+    if (lp > 0 && a.wait_rounds <= 0) {
+      failed = true;  // give up without looking (exercises the timeout path)
+    } else if (lp > 0) {
+      const int64_t first = (int64_t)s_part[v];
+      int64_t j = (int64_t)part - 1;
+      int rounds = 0;
+      while (true) {
+        const int64_t q = j - lane;
+        const uint64_t w = q >= first ? (uint64_t)lb[q] : (uint64_t)kEmitPrefix;
+        const uint32_t flag = (uint32_t)(w >> 62);
+        const unsigned waiting = __ballot_sync(0xffffffffu, flag == 0u);
+        const unsigned stops = __ballot_sync(0xffffffffu, flag >= 2u);
+        const int first_wait = waiting ? __ffs(waiting) - 1 : 32;
+        const int first_stop = stops ? __ffs(stops) - 1 : 32;
+        if (first_stop < first_wait) {
+          const bool take = lane <= first_stop;
+          failed = __any_sync(0xffffffffu, take && flag == 3u) != 0;
+          excl += warp_sum_u64(take ? (w & kEmitValue) : 0ull);
+          break;
+        }
+        excl += warp_sum_u64(lane < first_wait ? (w & kEmitValue) : 0ull);
+        j -= first_wait;
+        if (++rounds > a.wait_rounds) {
+          failed = true;
+          break;
+        }
+      }
+    }
+    if (lane == 0) {
+      if (lp > 0) lb[part] = failed ? kEmitFailed : (kEmitPrefix | ((excl + total) & kEmitValue));
+      s_base = excl;
+      s_total = total;
+      s_failed = failed ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  if (s_failed) {
+    if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    return;
+  }
+  const int64_t gbase = (int64_t)a.seg[v] + (int64_t)s_base;
+  if (gbase + (int64_t)s_total > a.capacity) {
+    if (tid == 0) atomicOr(a.status, kStatusCapacity);
+    return;
+  }
+  const ViewRec& V = a.views[v];
+  const uint32_t gw = (uint32_t)V.gw, toff = (uint32_t)V.tile_offset;
+  const int tpass = a.tpass;
+#pragma unroll
+  for (int r = 0; r < kEmitItems; r++) {
+    const uint32_t c = cnt[r];
+    uint32_t inc = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    const uint32_t excl = inc - c;
+    const uint32_t ctot = __shfl_sync(0xffffffffu, inc, 31);
+    const int64_t cb = gbase + s_chunk[wid * kEmitItems + r];
+    const uint32_t x0 = rx[r] & 0xffffu, rw = (rx[r] >> 16) - x0, y0 = ry[r] & 0xffffu;
+    for (uint32_t q0 = 0; q0 < ctot; q0 += 32) {
+      const uint32_t q = q0 + lane;
+      // owner: the last lane whose exclusive offset is <= q
+      int own = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cand = own + step;
+        const uint32_t ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+        if (cand < 32 && ec <= q) own = cand;
+      }
+      const uint32_t e_own = __shfl_sync(0xffffffffu, excl, own);
+      const uint32_t ox0 = __shfl_sync(0xffffffffu, x0, own);
+      const uint32_t oy0 = __shfl_sync(0xffffffffu, y0, own);
+      const uint32_t orw = __shfl_sync(0xffffffffu, rw, own);
+      const uint32_t og = __shfl_sync(0xffffffffu, gi[r], own);
+      const bool ok = q < ctot;
+      uint32_t t = 0;
+      if (ok) {
+        const uint32_t local = q - e_own;
+        t = (oy0 + local / orw) * gw + ox0 + local % orw;
+        a.keys[cb + q] = toff + t;
+        a.vals[cb + q] = og;
+        atomicAdd(&s_hist[0][t & (kRadix - 1)], 1u);
+      }
+      for (int p = 1; p < tpass; p++) {
+        const uint32_t dg = (t >> (kRadixBits * p)) & (kRadix - 1);
+        const unsigned peers = __match_any_sync(0xffffffffu, ok ? dg : (uint32_t)kRadix);
+        if (ok && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_hist[p][dg], (uint32_t)__popc(peers));
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t* h = a.hist + (int64_t)v * tpass * kRadix;
+  for (int i = tid; i < tpass * kRadix; i += kEmitThreads) {
+    const uint32_t c = (&s_hist[0][0])[i];
+    if (c) atomicAdd(&h[i], c);
+  }
+}
+
+void launch_emit(const EmitArgs& a, int64_t pair_capacity, cudaStream_t s) {
+  const int64_t grid = emit_partitions(pair_capacity, a.B);
+  if (grid <= 0) return;
+  emit_kernel<<<(unsigned)grid, kEmitThreads, 0, s>>>(a);
+}
+
+size_t emit_lookback_bytes(int64_t pair_capacity, int segments) {
+  return (size_t)emit_partitions(pair_capacity, segments) * sizeof(uint64_t);
 }
 
 // ---------------------------------------------------------------- tile ranges
 
-// ranges[bin] = [first, last + 1) of the bin in the sorted keys; block 0
-// also records which buffers hold the sorted list.  Each key is loaded once:
-// a lane compares its bin with its neighbours' through shuffles (the warp's
-// edge lanes load one neighbour each).
+// ranges[bin] = [first, last + 1) of the bin in the sorted instance keys
+// (32-bit bins); block 0 also records which buffers hold the sorted list.
+// Each key is loaded once: a lane compares its bin with its neighbours'
+// through shuffles (the warp's edge lanes load one neighbour each).
 __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __restrict__ ranges) {
   const int64_t count = min((int64_t)*a.count, a.capacity);
   const int par = (int)(a.ctrl[a.npass] & kCtrlParity);
-  const uint64_t* __restrict__ keys = par ? a.keys[1] : a.keys[0];
+  const uint32_t* __restrict__ keys = static_cast<const uint32_t*>(par ? a.keys[1] : a.keys[0]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.sorted_keys = keys;
     *a.sorted_vals = par ? a.vals[1] : a.vals[0];
@@ -596,16 +792,15 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(SortArgs a, uint2* __r
   constexpr int U = 4;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const uint32_t* __restrict__ hi32 = reinterpret_cast<const uint32_t*>(keys) + 1;  // bin = upper half
   for (int64_t w0 = warp * 32 * U; w0 < count; w0 += nwarps * 32 * U) {
     uint32_t bin[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t i = w0 + 32 * u + lane;
-      bin[u] = i < count ? hi32[2 * i] : none;
+      bin[u] = i < count ? keys[i] : none;
     }
-    const uint32_t before = (lane == 0 && w0 > 0) ? hi32[2 * (w0 - 1)] : none;
-    const uint32_t after = (lane == 31 && w0 + 32 * U < count) ? hi32[2 * (w0 + 32 * U)] : none;
+    const uint32_t before = (lane == 0 && w0 > 0) ? keys[w0 - 1] : none;
+    const uint32_t after = (lane == 31 && w0 + 32 * U < count) ? keys[w0 + 32 * U] : none;
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t i = w0 + 32 * u + lane;

@@ -60,7 +60,7 @@ struct gs_ctx {
   int raster_fwd = 2;  // compositing variants (pixels per thread; 8 = one warp per tile)
   int raster_bwd = 2;
   int bwd_direct = 2;  // per-lane gradient atomics when at most this many lanes contribute
-  int sort_passes = 0;  // LSD passes of the last sort
+  int sort_passes = 0;  // LSD passes of the last tile sort
   int sort_items = 16;  // keys per thread of a sort partition
   int sort_wait = 1 << 20;  // look-back rounds before a sort gives up
   int tile_order_mode = 0;  // 0: composite tiles in bin order; 1: longest lists first
@@ -81,7 +81,8 @@ struct gs_ctx {
       hist, hist_scan, lookback, counters, ranges, tfinal, nlast, g2d, l1_partial, sorted_slots, adam_consts,
       target_slot, host_tgt0, host_tgt1, pair_stats, cells, vismask, ssim_table, ssim_partials, ssim_sums,
       init_pts, init_scales, knn_part, knn_table, ord_keys0, ord_keys1, ord_vals0, ord_vals1, ord_total, ord_hist,
-      ord_hist_scan, ord_lookback, ord_counters, ord_views, tile_order;
+      ord_hist_scan, ord_lookback, ord_counters, ord_views, tile_order, vis_sums, vis_offsets, dtotal, dkeys0,
+      dkeys1, dvals0, dvals1, dhist, dhist_scan, dlookback, elookback;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -278,6 +279,42 @@ void adam_constants(const gs_adam_hp* hp, int planes, int64_t step, int B, float
 
 }  // namespace
 
+// Device words of one sort: total (u64) | view totals (u64 x 64) | seg (u32 x 65)
+// | part_off (u32 x 65) | ctrl (u32 x 16) | single-digit flags (u32 x 64 x 8).
+struct SortWords {
+  uint64_t* total;
+  uint64_t* view_total;
+  uint32_t* seg;
+  uint32_t* part_off;
+  uint32_t* ctrl;
+  uint32_t* single;
+};
+
+static size_t sort_words_bytes() {
+  return sizeof(uint64_t) * (1 + kMaxViews) + sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews);
+}
+
+static SortWords sort_words(DevBuf& b) {
+  SortWords w;
+  w.total = P<uint64_t>(b);
+  w.view_total = w.total + 1;
+  w.seg = reinterpret_cast<uint32_t*>(w.view_total + kMaxViews);
+  w.part_off = w.seg + kMaxViews + 1;
+  w.ctrl = w.part_off + kMaxViews + 1;
+  w.single = w.ctrl + 16;
+  return w;
+}
+
+constexpr int kDepthPasses = 4;  // 32 depth bits
+constexpr int kSortCounters = 24;  // tickets: [0, 8) tile sort, [8, 16) depth sort, [16] emission
+
+// LSD passes of the tile sort: the bits of the largest tile index inside a view.
+static int tile_passes(int64_t view_tiles) {
+  int bits = 0;
+  while (((int64_t)1 << bits) < view_tiles) bits++;
+  return std::max(1, (bits + 7) / 8);
+}
+
 namespace gs {
 
 gs_status ctx_reserve(gs_ctx* c, int64_t stride, int B, int64_t bins, int64_t pixels, int64_t view_tiles) {
@@ -288,27 +325,36 @@ gs_status ctx_reserve(gs_ctx* c, int64_t stride, int B, int64_t bins, int64_t pi
   auto ensure_exact = [](gs_ctx* cc, DevBuf& b, size_t bytes) { return ensure(cc, b, bytes, true); };
   const int64_t cap = c->cfg.instance_capacity;
   const int64_t nb = (stride + project_fwd_block() - 1) / project_fwd_block();
-  int tile_bits = 0;
-  while (((int64_t)1 << tile_bits) < view_tiles) tile_bits++;
-  const int npass = (32 + tile_bits + 7) / 8;
+  const int tpass = tile_passes(view_tiles);
+  const int64_t pc = (int64_t)B * stride;  // visible pairs at most
   GS_TRY(ensure_exact(c, c->views, sizeof(ViewRec) * B));
   GS_TRY(ensure_exact(c, c->rec, sizeof(float4) * kRecStride * B * stride));
   GS_TRY(ensure_exact(c, c->rec3, sizeof(int4) * B * stride));
   GS_TRY(ensure_exact(c, c->tiles, sizeof(uint2) * B * stride));
   GS_TRY(ensure_exact(c, c->block_sums, sizeof(uint32_t) * B * nb));
+  GS_TRY(ensure_exact(c, c->vis_sums, sizeof(uint32_t) * B * nb));
   GS_TRY(ensure_exact(c, c->vismask, sizeof(uint64_t) * stride));
   GS_TRY(ensure_exact(c, c->block_offsets, sizeof(uint32_t) * B * nb));
-  GS_TRY(ensure_exact(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
-                                 sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
-  GS_TRY(ensure_exact(c, c->keys0, sizeof(uint64_t) * cap));
-  GS_TRY(ensure_exact(c, c->keys1, sizeof(uint64_t) * cap));
+  GS_TRY(ensure_exact(c, c->vis_offsets, sizeof(uint32_t) * B * nb));
+  GS_TRY(ensure_exact(c, c->total, sort_words_bytes()));
+  GS_TRY(ensure_exact(c, c->dtotal, sort_words_bytes()));
+  GS_TRY(ensure_exact(c, c->keys0, sizeof(uint32_t) * cap));
+  GS_TRY(ensure_exact(c, c->keys1, sizeof(uint32_t) * cap));
   GS_TRY(ensure_exact(c, c->vals0, sizeof(uint32_t) * cap));
   GS_TRY(ensure_exact(c, c->vals1, sizeof(uint32_t) * cap));
+  GS_TRY(ensure_exact(c, c->dkeys0, sizeof(uint32_t) * pc));
+  GS_TRY(ensure_exact(c, c->dkeys1, sizeof(uint32_t) * pc));
+  GS_TRY(ensure_exact(c, c->dvals0, sizeof(uint32_t) * pc));
+  GS_TRY(ensure_exact(c, c->dvals1, sizeof(uint32_t) * pc));
   GS_TRY(ensure_exact(c, c->ranges, sizeof(uint2) * bins));
   GS_TRY(ensure_exact(c, c->hist, sizeof(uint32_t) * (size_t)B * 8 * 256));
   GS_TRY(ensure_exact(c, c->hist_scan, sizeof(uint32_t) * (size_t)B * 8 * 256));
-  GS_TRY(ensure_exact(c, c->lookback, sort_lookback_bytes(cap, c->sort_items, B) * npass));
-  GS_TRY(ensure_exact(c, c->counters, sizeof(uint32_t) * 8));
+  GS_TRY(ensure_exact(c, c->dhist, sizeof(uint32_t) * (size_t)B * 8 * 256));
+  GS_TRY(ensure_exact(c, c->dhist_scan, sizeof(uint32_t) * (size_t)B * 8 * 256));
+  GS_TRY(ensure_exact(c, c->lookback, sort_lookback_bytes(cap, c->sort_items, B) * tpass));
+  GS_TRY(ensure_exact(c, c->dlookback, sort_lookback_bytes(pc, c->sort_items, B) * kDepthPasses));
+  GS_TRY(ensure_exact(c, c->elookback, emit_lookback_bytes(pc, B)));
+  GS_TRY(ensure_exact(c, c->counters, sizeof(uint32_t) * kSortCounters));
   GS_TRY(ensure_exact(c, c->sorted_slots, 2 * sizeof(void*)));
   GS_TRY(ensure_exact(c, c->tfinal, sizeof(float) * pixels));
   GS_TRY(ensure_exact(c, c->nlast, sizeof(uint32_t) * pixels));
@@ -380,7 +426,9 @@ void gs_destroy(gs_ctx* c) {
                     &c->pair_stats, &c->cells, &c->vismask, &c->ssim_table, &c->ssim_partials, &c->ssim_sums,
                     &c->init_pts, &c->init_scales, &c->knn_part, &c->knn_table, &c->ord_keys0, &c->ord_keys1,
                     &c->ord_vals0, &c->ord_vals1, &c->ord_total, &c->ord_hist, &c->ord_hist_scan, &c->ord_lookback,
-                    &c->ord_counters, &c->ord_views, &c->tile_order};
+                    &c->ord_counters, &c->ord_views, &c->tile_order, &c->vis_sums, &c->vis_offsets, &c->dtotal,
+                    &c->dkeys0, &c->dkeys1, &c->dvals0, &c->dvals1, &c->dhist, &c->dhist_scan, &c->dlookback,
+                    &c->elookback};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -443,6 +491,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   GS_TRY(ensure(c, c->rec3, sizeof(int4) * B * stride));
   GS_TRY(ensure(c, c->tiles, sizeof(uint2) * B * stride));
   GS_TRY(ensure(c, c->block_sums, sizeof(uint32_t) * B * nb));
+  GS_TRY(ensure(c, c->vis_sums, sizeof(uint32_t) * B * nb));
   GS_TRY(ensure(c, c->vismask, sizeof(uint64_t) * stride));
   GS_CUDA(c, cudaMemsetAsync(c->vismask.p, 0, sizeof(uint64_t) * stride, c->stream));
   if (c->capturing) {
@@ -463,6 +512,7 @@ gs_status gs_project(gs_ctx* c, const gs_params* params, const gs_camera* cams, 
   a.rec3 = P<int4>(c->rec3);
   a.tiles = P<uint2>(c->tiles);
   a.block_sums = P<uint32_t>(c->block_sums);
+  a.vis_sums = P<uint32_t>(c->vis_sums);
   a.vismask = P<uint64_t>(c->vismask);
   {
     LaunchScope ls(c, "project_fwd");
@@ -489,19 +539,17 @@ gs_status gs_bin_sort(gs_ctx* c) {
   c->sorted = c->rastered = c->cells_ready = false;
   const int B = c->B;
   GS_TRY(ensure(c, c->block_offsets, sizeof(uint32_t) * B * c->nblocks));
-  // device words: total (u64) | view totals (u64 x 64) | seg (u32 x 65) | part_off (u32 x 65) | ctrl (u32 x 16)
-  //               | single-digit flags (u32 x 64 x 8)
-  GS_TRY(ensure(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
-                                 sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
-  uint64_t* total = P<uint64_t>(c->total);
-  uint64_t* view_total = total + 1;
-  uint32_t* seg = reinterpret_cast<uint32_t*>(view_total + kMaxViews);
-  uint32_t* part_off = seg + kMaxViews + 1;
-  uint32_t* ctrl = part_off + kMaxViews + 1;
+  GS_TRY(ensure(c, c->vis_offsets, sizeof(uint32_t) * B * c->nblocks));
+  GS_TRY(ensure(c, c->total, sort_words_bytes()));
+  GS_TRY(ensure(c, c->dtotal, sort_words_bytes()));
+  const SortWords iw = sort_words(c->total);   // instances (tile sort)
+  const SortWords dw = sort_words(c->dtotal);  // visible pairs (depth sort)
   {
-    LaunchScope ls(c, "scan_block_sums", 2);
-    launch_scan_block_sums(P<uint32_t>(c->block_sums), c->nblocks, B, P<uint32_t>(c->block_offsets), view_total,
-                           seg, total, c->stream);
+    LaunchScope ls(c, "scan_block_sums", 4);
+    launch_scan_block_sums(P<uint32_t>(c->block_sums), c->nblocks, B, P<uint32_t>(c->block_offsets),
+                           iw.view_total, iw.seg, iw.total, c->stream);
+    launch_scan_block_sums(P<uint32_t>(c->vis_sums), c->nblocks, B, P<uint32_t>(c->vis_offsets), dw.view_total,
+                           dw.seg, dw.total, c->stream);
   }
   GS_CHECK_LAUNCH(c);
   // capacity: the exact count (grow-on-demand contexts read it, one stream
@@ -518,84 +566,163 @@ gs_status gs_bin_sort(gs_ctx* c) {
     c->instances = cap;
   }
   if (cap >= ((int64_t)1 << 30) - 1) return fail(c, GS_ECAPACITY, "%lld instances exceed 2^30", (long long)cap);
-  GS_TRY(ensure(c, c->keys0, sizeof(uint64_t) * cap));
-  GS_TRY(ensure(c, c->keys1, sizeof(uint64_t) * cap));
+  const int64_t pc = (int64_t)B * c->n;  // visible pairs at most
+  if (pc >= ((int64_t)1 << 32) - 1) return fail(c, GS_ECAPACITY, "%lld (view, Gaussian) pairs exceed 2^32", (long long)pc);
+  GS_TRY(ensure(c, c->keys0, sizeof(uint32_t) * cap));
+  GS_TRY(ensure(c, c->keys1, sizeof(uint32_t) * cap));
   GS_TRY(ensure(c, c->vals0, sizeof(uint32_t) * cap));
   GS_TRY(ensure(c, c->vals1, sizeof(uint32_t) * cap));
+  GS_TRY(ensure(c, c->dkeys0, sizeof(uint32_t) * pc));
+  GS_TRY(ensure(c, c->dkeys1, sizeof(uint32_t) * pc));
+  GS_TRY(ensure(c, c->dvals0, sizeof(uint32_t) * pc));
+  GS_TRY(ensure(c, c->dvals1, sizeof(uint32_t) * pc));
   GS_TRY(ensure(c, c->ranges, sizeof(uint2) * c->bins));
-  // each view is sorted on its own: the 32 depth bits and the bits of the
+  // each view is sorted on its own: the tile sort on the bits of the
   // largest tile index inside a view
   int64_t most_tiles = 1;
   for (int v = 0; v < B; v++) most_tiles = std::max<int64_t>(most_tiles, (int64_t)c->views_h[v].gw * c->views_h[v].gh);
-  int tile_bits = 0;
-  while (((int64_t)1 << tile_bits) < most_tiles) tile_bits++;
-  const int npass = (32 + tile_bits + 7) / 8;
-  c->sort_passes = npass;
+  const int tpass = tile_passes(most_tiles);
+  c->sort_passes = tpass;
   const size_t lb = sort_lookback_bytes(cap, c->sort_items, B);
+  const size_t dlb = sort_lookback_bytes(pc, c->sort_items, B);
+  const size_t elb = emit_lookback_bytes(pc, B);
   GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * (size_t)B * 8 * 256));
   GS_TRY(ensure(c, c->hist_scan, sizeof(uint32_t) * (size_t)B * 8 * 256));
-  GS_TRY(ensure(c, c->lookback, lb * npass));
-  GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
+  GS_TRY(ensure(c, c->dhist, sizeof(uint32_t) * (size_t)B * 8 * 256));
+  GS_TRY(ensure(c, c->dhist_scan, sizeof(uint32_t) * (size_t)B * 8 * 256));
+  GS_TRY(ensure(c, c->lookback, lb * tpass));
+  GS_TRY(ensure(c, c->dlookback, dlb * kDepthPasses));
+  GS_TRY(ensure(c, c->elookback, elb));
+  GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * kSortCounters));
   GS_TRY(ensure(c, c->sorted_slots, 2 * sizeof(void*)));
   // contribution masks: every tile's region padded to whole batches of 32
   if (!c->forward_only) GS_TRY(ensure(c, c->cells, sizeof(uint32_t) * (cap + 32 * c->bins)));
+  uint32_t* counters = P<uint32_t>(c->counters);
+  GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * kSortCounters, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->dhist.p, 0, sizeof(uint32_t) * (size_t)B * kDepthPasses * 256, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * (size_t)B * tpass * 256, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->dlookback.p, 0, dlb * kDepthPasses, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->elookback.p, 0, elb, c->stream));
+  GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * tpass, c->stream));
 
-  DuplicateArgs d{};
-  d.n = c->n;
-  d.stride = c->stride;
-  d.views = P<ViewRec>(c->views);
-  d.B = c->B;
-  d.rec3 = P<int4>(c->rec3);
-  d.tiles = P<uint2>(c->tiles);
-  d.block_offsets = P<uint32_t>(c->block_offsets);
-  d.seg = seg;
-  d.keys = P<uint64_t>(c->keys0);
-  d.vals = P<uint32_t>(c->vals0);
-  d.capacity = cap;
-  d.status = c->status_d;
+  // 1. visible pairs -> (depth bits, Gaussian), view by view in Gaussian order
+  CompactArgs ca{};
+  ca.n = c->n;
+  ca.stride = c->stride;
+  ca.B = B;
+  ca.tiles = P<uint2>(c->tiles);
+  ca.vis_offsets = P<uint32_t>(c->vis_offsets);
+  ca.vseg = dw.seg;
+  ca.dkeys = P<uint32_t>(c->dkeys0);
+  ca.dvals = P<uint32_t>(c->dvals0);
   {
-    LaunchScope ls(c, "duplicate");
-    launch_duplicate(d, c->stream);
+    LaunchScope ls(c, "compact");
+    launch_compact(ca, c->stream);
   }
   GS_CHECK_LAUNCH(c);
 
+  // 2. stable sort of each view's pairs by depth
+  SortArgs ds{};
+  ds.keys[0] = c->dkeys0.p;
+  ds.keys[1] = c->dkeys1.p;
+  ds.vals[0] = P<uint32_t>(c->dvals0);
+  ds.vals[1] = P<uint32_t>(c->dvals1);
+  ds.key_bytes = 4;
+  ds.view_shift = 0;
+  ds.views = nullptr;
+  ds.count = dw.total;
+  ds.capacity = pc;
+  ds.bins = 0;
+  ds.B = B;
+  ds.seg = dw.seg;
+  ds.part_off = dw.part_off;
+  ds.hist = P<uint32_t>(c->dhist);
+  ds.hist_scan = P<uint32_t>(c->dhist_scan);
+  ds.ctrl = dw.ctrl;
+  ds.single = dw.single;
+  ds.lookback = P<uint32_t>(c->dlookback);
+  ds.lookback_stride = dlb / sizeof(uint32_t);
+  ds.counters = counters + 8;
+  ds.npass = kDepthPasses;
+  ds.wait_rounds = c->sort_wait;
+  ds.status = c->status_d;
+  {
+    LaunchScope ls(c, "depth_histogram", 3);
+    launch_digit_histogram(ds, pc, c->sort_items, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+  for (int p = 0; p < kDepthPasses; p++) {
+    LaunchScope ls(c, "depth_pass");
+    launch_onesweep_pass(ds, p, c->sort_items, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+
+  // 3. one instance per touched tile, in depth order; tile digit counts
+  EmitArgs ea{};
+  ea.B = B;
+  ea.n = c->n;
+  ea.stride = c->stride;
+  ea.views = P<ViewRec>(c->views);
+  ea.rec3 = P<int4>(c->rec3);
+  ea.dvals[0] = P<uint32_t>(c->dvals0);
+  ea.dvals[1] = P<uint32_t>(c->dvals1);
+  ea.dctrl = dw.ctrl;
+  ea.dpass = kDepthPasses;
+  ea.vseg = dw.seg;
+  ea.seg = iw.seg;
+  ea.keys = P<uint32_t>(c->keys0);
+  ea.vals = P<uint32_t>(c->vals0);
+  ea.capacity = cap;
+  ea.lookback = P<uint64_t>(c->elookback);
+  ea.counter = counters + 16;
+  ea.hist = P<uint32_t>(c->hist);
+  ea.tpass = tpass;
+  ea.wait_rounds = c->sort_wait;
+  ea.status = c->status_d;
+  {
+    LaunchScope ls(c, "emit");
+    launch_emit(ea, pc, c->stream);
+  }
+  GS_CHECK_LAUNCH(c);
+
+  // 4. stable sort of each view's instances by tile
   SortArgs sa{};
-  sa.keys[0] = P<uint64_t>(c->keys0);
-  sa.keys[1] = P<uint64_t>(c->keys1);
+  sa.keys[0] = c->keys0.p;
+  sa.keys[1] = c->keys1.p;
   sa.vals[0] = P<uint32_t>(c->vals0);
   sa.vals[1] = P<uint32_t>(c->vals1);
-  sa.count = total;
+  sa.key_bytes = 4;
+  sa.view_shift = 0;
+  sa.views = P<ViewRec>(c->views);
+  sa.count = iw.total;
   sa.capacity = cap;
   sa.bins = c->bins;
   sa.B = B;
-  sa.views = P<ViewRec>(c->views);
-  sa.seg = seg;
-  sa.part_off = part_off;
+  sa.seg = iw.seg;
+  sa.part_off = iw.part_off;
   sa.hist = P<uint32_t>(c->hist);
   sa.hist_scan = P<uint32_t>(c->hist_scan);
-  sa.ctrl = ctrl;
-  sa.single = ctrl + 16;
+  sa.ctrl = iw.ctrl;
+  sa.single = iw.single;
   sa.lookback = P<uint32_t>(c->lookback);
   sa.lookback_stride = lb / sizeof(uint32_t);
-  sa.counters = P<uint32_t>(c->counters);
-  sa.npass = npass;
+  sa.counters = counters;
+  sa.npass = tpass;
   sa.wait_rounds = c->sort_wait;
   sa.status = c->status_d;
-  sa.sorted_keys = reinterpret_cast<const uint64_t**>(c->sorted_slots.p);
+  sa.sorted_keys = reinterpret_cast<const void**>(c->sorted_slots.p);
   sa.sorted_vals = reinterpret_cast<const uint32_t**>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
-  GS_CUDA(c, cudaMemsetAsync(c->hist.p, 0, sizeof(uint32_t) * (size_t)B * npass * 256, c->stream));
-  GS_CUDA(c, cudaMemsetAsync(c->counters.p, 0, sizeof(uint32_t) * 8, c->stream));
-  GS_CUDA(c, cudaMemsetAsync(c->lookback.p, 0, lb * npass, c->stream));
   {
-    LaunchScope ls(c, "digit_histogram", 3);
-    launch_digit_histogram(sa, cap, c->sort_items, c->stream);
+    LaunchScope ls(c, "tile_scan", 2);
+    launch_digit_scan(sa, c->sort_items, c->stream);
   }
   GS_CHECK_LAUNCH(c);
-  for (int p = 0; p < npass; p++) {
-    LaunchScope ls(c, "onesweep_pass");
+  for (int p = 0; p < tpass; p++) {
+    LaunchScope ls(c, "tile_pass");
     launch_onesweep_pass(sa, p, c->sort_items, c->stream);
   }
   GS_CHECK_LAUNCH(c);
+  // 5. per-tile ranges
   GS_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * c->bins, c->stream));
   {
     LaunchScope ls(c, "tile_ranges");
@@ -632,8 +759,10 @@ static gs_status sort_tiles_longest_first(gs_ctx* c) {
   uint32_t* part_off = seg + 2;
   uint32_t* ctrl = part_off + 2;
   SortArgs sa{};
-  sa.keys[0] = P<uint64_t>(c->ord_keys0);
-  sa.keys[1] = P<uint64_t>(c->ord_keys1);
+  sa.keys[0] = c->ord_keys0.p;
+  sa.keys[1] = c->ord_keys1.p;
+  sa.key_bytes = 8;
+  sa.view_shift = 32;
   sa.vals[0] = P<uint32_t>(c->ord_vals0);
   sa.vals[1] = P<uint32_t>(c->ord_vals1);
   sa.count = count;
@@ -659,7 +788,7 @@ static gs_status sort_tiles_longest_first(gs_ctx* c) {
   GS_CUDA(c, cudaMemsetAsync(c->ord_lookback.p, 0, lb, c->stream));
   {
     LaunchScope ls(c, "tile_order", 6);
-    launch_tile_order_keys(P<uint2>(c->ranges), bins, sa.keys[0], sa.vals[0], count, seg, c->stream);
+    launch_tile_order_keys(P<uint2>(c->ranges), bins, P<uint64_t>(c->ord_keys0), sa.vals[0], count, seg, c->stream);
     launch_digit_histogram(sa, bins, items, c->stream);
     launch_onesweep_pass(sa, 0, items, c->stream);
     launch_tile_order_finish(ctrl, 1, sa.vals[0], sa.vals[1], bins, P<uint32_t>(c->tile_order), c->stream);
@@ -884,8 +1013,13 @@ gs_status gs_get_buffer(gs_ctx* c, int32_t which, void** ptr, int64_t* count) {
     case GS_BUF_VISMASK: if (!c->projected) return GS_ESTATE; *ptr = c->vismask.p; *count = c->n; break;
     case GS_BUF_SORT_CTRL:
       if (!c->sorted) return GS_ESTATE;
-      *ptr = reinterpret_cast<uint32_t*>(P<uint64_t>(c->total) + 1 + kMaxViews) + 2 * (kMaxViews + 1);
+      *ptr = sort_words(c->total).ctrl;
       *count = c->sort_passes + 1;
+      break;
+    case GS_BUF_DEPTH_CTRL:
+      if (!c->sorted) return GS_ESTATE;
+      *ptr = sort_words(c->dtotal).ctrl;
+      *count = kDepthPasses + 1;
       break;
     default: return fail(c, GS_EINVAL, "unknown buffer %d", which);
   }
@@ -978,8 +1112,7 @@ gs_status gs_image_metrics(gs_ctx* c, const float* images, const float* targets,
 static gs_status sort_pairs(gs_ctx* c, int64_t n, int bits, int* which) {
   const int npass = std::max(1, (bits + 7) / 8);
   GS_TRY(ensure(c, c->views, sizeof(ViewRec)));
-  GS_TRY(ensure(c, c->total, sizeof(uint64_t) * (1 + kMaxViews) +
-                                 sizeof(uint32_t) * (2 * (kMaxViews + 1) + 16 + 8 * kMaxViews)));
+  GS_TRY(ensure(c, c->total, sort_words_bytes()));
   const size_t lb = sort_lookback_bytes(n, c->sort_items, 1);
   GS_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
   GS_TRY(ensure(c, c->hist_scan, sizeof(uint32_t) * 8 * 256));
@@ -995,8 +1128,10 @@ static gs_status sort_pairs(gs_ctx* c, int64_t n, int bits, int* which) {
   GS_CUDA(c, cudaMemcpyAsync(total, &cnt, sizeof(cnt), cudaMemcpyHostToDevice, c->stream));
   GS_CUDA(c, cudaMemcpyAsync(seg, segs, sizeof(segs), cudaMemcpyHostToDevice, c->stream));
   SortArgs sa{};
-  sa.keys[0] = P<uint64_t>(c->keys0);
-  sa.keys[1] = P<uint64_t>(c->keys1);
+  sa.keys[0] = c->keys0.p;
+  sa.keys[1] = c->keys1.p;
+  sa.key_bytes = 8;
+  sa.view_shift = 32;
   sa.vals[0] = P<uint32_t>(c->vals0);
   sa.vals[1] = P<uint32_t>(c->vals1);
   sa.count = total;

@@ -19,6 +19,7 @@ struct ProjectArgs {
   int4* rec3;            // (radius, tiles, x0 | x1 << 16, y0 | y1 << 16) per (view, Gaussian)
   uint2* tiles;          // [B][stride]: (tiles touched, bits of the depth)
   uint32_t* block_sums;  // [B][ceil(n / block)] instance counts per view and block
+  uint32_t* vis_sums;    // [B][ceil(n / block)] visible (tiles > 0) Gaussians per view and block
   uint64_t* vismask;     // [stride]: bit v = the Gaussian touches a tile of view v
 };
 
@@ -34,17 +35,36 @@ struct ProjectBwdArgs {
   float* dens_count;  //   and += the number of views where the Gaussian touches a tile
 };
 
-struct DuplicateArgs {
+// Visible (view, Gaussian) pairs -> (depth bits, Gaussian), view by view.
+struct CompactArgs {
+  int64_t n, stride;
+  int B;
+  const uint2* tiles;             // [B][stride] (tiles touched, bits of the depth)
+  const uint32_t* vis_offsets;    // [B][blocks] exclusive scan of each view's visible counts per block
+  const uint32_t* vseg;           // [B + 1] first pair of each view's segment
+  uint32_t* dkeys;                // depth bits
+  uint32_t* dvals;                // Gaussian index
+};
+
+// Depth-sorted visible pairs -> one (bin, Gaussian) instance per touched tile.
+struct EmitArgs {
+  int B;
   int64_t n, stride;
   const ViewRec* views;
-  int B;
-  const int4* rec3;
-  const uint2* tiles;  // (tiles touched, bits of the depth)
-  const uint32_t* block_offsets;  // [B][blocks] exclusive scan of each view's block counts
-  const uint32_t* seg;            // [B + 1] first instance of each view's segment
-  uint64_t* keys;
-  uint32_t* vals;
+  const int4* rec3;               // [B][stride] (radius, tiles, x0 | x1 << 16, y0 | y1 << 16)
+  const uint32_t* dvals[2];       // the depth sort's buffers; dctrl[dpass] bit 0 says which is sorted
+  const uint32_t* dctrl;
+  int dpass;
+  const uint32_t* vseg;           // [B + 1] visible pairs: first of each view
+  const uint32_t* seg;            // [B + 1] instances: first of each view
+  uint32_t* keys;                 // [capacity] bins
+  uint32_t* vals;                 // [capacity] Gaussians
   int64_t capacity;
+  uint64_t* lookback;             // [emit_partitions] status words, zeroed before the launch
+  uint32_t* counter;              // partition ticket, zeroed before the launch
+  uint32_t* hist;                 // [B][tpass][256] tile digit counts (added to; zeroed before)
+  int tpass;
+  int wait_rounds;
   int* status;
 };
 
@@ -91,7 +111,11 @@ void launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t s);
 
 void launch_scan_block_sums(const uint32_t* sums, int64_t nb, int B, uint32_t* offsets, uint64_t* view_total,
                             uint32_t* seg, uint64_t* total, cudaStream_t s);
-void launch_duplicate(const DuplicateArgs& a, cudaStream_t s);
+void launch_compact(const CompactArgs& a, cudaStream_t s);
+// pair_capacity: visible pairs the grid covers (B x stride)
+void launch_emit(const EmitArgs& a, int64_t pair_capacity, cudaStream_t s);
+int64_t emit_partitions(int64_t pairs, int segments);
+size_t emit_lookback_bytes(int64_t pair_capacity, int segments);
 
 // LSD radix sort of (key, value) pairs on key bits [0, 8 npass), ping-pong
 // between keys[0]/vals[0] (input) and keys[1]/vals[1].  Everything that
@@ -99,13 +123,15 @@ void launch_duplicate(const DuplicateArgs& a, cudaStream_t s);
 // sorted) is decided on the device, so the sequence can be captured in a
 // CUDA graph.
 struct SortArgs {
-  uint64_t* keys[2];
+  void* keys[2];             // uint32 or uint64 keys (key_bytes)
   uint32_t* vals[2];
+  int key_bytes;             // 4 or 8
+  int view_shift;            // a segment's key base: views[v].tile_offset << view_shift
   const uint64_t* count;     // device: number of pairs (clamped to capacity)
   int64_t capacity;          // pairs the buffers hold
   int64_t bins;              // valid bin ids are [0, bins)
   int B;                     // views: one segment each
-  const ViewRec* views;      // a view's first bin is subtracted before the digits are taken
+  const ViewRec* views;      // NULL: key base 0 for every segment
   const uint32_t* seg;       // [B + 1] segment offsets
   uint32_t* part_off;        // [B + 1] first partition of each segment
   uint32_t* single;          // [B][8] 1 if the view's keys share one digit in the pass
@@ -118,7 +144,7 @@ struct SortArgs {
   int npass;
   int wait_rounds;  // look-back rounds before giving up (0: give up at once)
   int* status;
-  const uint64_t** sorted_keys;  // device slots: where the sorted list ends up
+  const void** sorted_keys;  // device slots: where the sorted list ends up (tile_ranges)
   const uint32_t** sorted_vals;
 };
 
@@ -132,7 +158,10 @@ void launch_tile_order_finish(const uint32_t* ctrl, int npass, const uint32_t* v
 
 size_t sort_lookback_bytes(int64_t count, int items, int segments);
 int64_t sort_partitions(int64_t count, int items, int segments);
+// digit counts (into a.hist, zeroed before), their scans and the pass control words
 void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, int items, cudaStream_t s);
+// the scans and control words only (a.hist counted elsewhere)
+void launch_digit_scan(const SortArgs& a, int items, cudaStream_t s);
 // items: keys per thread (12, 16, 20 or 24); the grid covers a.capacity
 void launch_onesweep_pass(const SortArgs& a, int pass, int items, cudaStream_t s);
 void launch_tile_ranges(const SortArgs& a, int64_t grid_hint, uint2* ranges, cudaStream_t s);

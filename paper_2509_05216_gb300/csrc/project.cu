@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
   gauss_cov(lsc, quat, gc);  // view-independent: once per Gaussian
   __shared__ float4 s_rec[8][32 * kRecStride];  // 256 threads: 8 warps x 32 records
   __shared__ uint32_t s_bsum[kMaxViews];          // the block's instance count per view
-  for (int i = threadIdx.x; i < a.B; i += blockDim.x) s_bsum[i] = 0;
+  __shared__ uint32_t s_vsum[kMaxViews];          // and its visible Gaussians per view
+  for (int i = threadIdx.x; i < a.B; i += blockDim.x) s_bsum[i] = s_vsum[i] = 0;
   __syncthreads();
   uint64_t vis = 0;  // views where the Gaussian touches a tile
   for (int v = 0; v < a.B; v++) {
@@ -258,13 +259,19 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
       if (g0 + f / kRecStride < a.n) dst[f] = stage[f];
     }
     const uint32_t wt = __reduce_add_sync(0xffffffffu, tiles);
-    if (lane == 0 && wt) atomicAdd(&s_bsum[v], wt);
+    const uint32_t wv = (uint32_t)__popc(__ballot_sync(0xffffffffu, tiles != 0u));
+    if (lane == 0 && wt) {
+      atomicAdd(&s_bsum[v], wt);
+      atomicAdd(&s_vsum[v], wv);
+    }
   }
   if (live) a.vismask[g] = vis;
-  // the block's instance count per view (for the per-view scans)
+  // the block's instance and visible counts per view (for the per-view scans)
   __syncthreads();
-  for (int i = threadIdx.x; i < a.B; i += blockDim.x)
+  for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
     a.block_sums[(int64_t)i * gridDim.x + blockIdx.x] = s_bsum[i];
+    a.vis_sums[(int64_t)i * gridDim.x + blockIdx.x] = s_vsum[i];
+  }
 }
 
 // Backward, colour part: dL/drgb per (view, Gaussian) -> dL/dSH and the

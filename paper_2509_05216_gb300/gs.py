@@ -22,7 +22,7 @@ _NAMES = ["GS_OK", "GS_EINVAL", "GS_ENOMEM", "GS_ECUDA", "GS_ECAPACITY", "GS_ETI
           "GS_EAGAIN", "GS_ESTATE"]
 
 (GS_BUF_REC0, GS_BUF_REC1, GS_BUF_REC2, GS_BUF_KEYS, GS_BUF_VALS, GS_BUF_RANGES, GS_BUF_TFINAL,
- GS_BUF_NLAST, GS_BUF_G2D, GS_BUF_REC3, GS_BUF_SORT_CTRL, GS_BUF_VISMASK) = range(12)
+ GS_BUF_NLAST, GS_BUF_G2D, GS_BUF_REC3, GS_BUF_SORT_CTRL, GS_BUF_VISMASK, GS_BUF_DEPTH_CTRL) = range(13)
 LOG2E = 1.4426950408889634
 
 
@@ -431,9 +431,10 @@ class Context:
         self._check(self.L.gs_get_buffer(self.h, which, ctypes.byref(ptr), ctypes.byref(cnt)), "gs_get_buffer")
         n = cnt.value
         spec = {GS_BUF_REC0: ((n, 4), "<f4"), GS_BUF_REC1: ((n, 4), "<f4"), GS_BUF_REC2: ((n, 4), "<f4"),
-                GS_BUF_KEYS: ((n,), "<i8"), GS_BUF_VALS: ((n,), "<i4"), GS_BUF_RANGES: ((n, 2), "<i4"),
+                GS_BUF_KEYS: ((n,), "<i4"), GS_BUF_VALS: ((n,), "<i4"), GS_BUF_RANGES: ((n, 2), "<i4"),
                 GS_BUF_TFINAL: ((n,), "<f4"), GS_BUF_NLAST: ((n,), "<i4"), GS_BUF_G2D: ((n,), "<f4"), GS_BUF_REC3: ((n, 4), "<i4"),
-                GS_BUF_SORT_CTRL: ((n,), "<i4"), GS_BUF_VISMASK: ((n,), "<i8")}[which]
+                GS_BUF_SORT_CTRL: ((n,), "<i4"), GS_BUF_VISMASK: ((n,), "<i8"),
+                GS_BUF_DEPTH_CTRL: ((n,), "<i4")}[which]
         if n == 0:
             return torch.empty(spec[0], device="cuda:%d" % self.device,
                                dtype={"<f4": torch.float32, "<i8": torch.int64, "<i4": torch.int32}[spec[1]])

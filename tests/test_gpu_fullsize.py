@@ -54,7 +54,7 @@ def test_fullsize_binning_bit_exact_on_two_views(c3):
     r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
     r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
     r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
-    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)
+    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint32)
     gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64)
     gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
     tiles_per_view = (RES // 16) ** 2
@@ -66,7 +66,7 @@ def test_fullsize_binning_bit_exact_on_two_views(c3):
         lo, hi = v * tiles_per_view, (v + 1) * tiles_per_view
         starts = gr[lo:hi, 0][gr[lo:hi, 1] > gr[lo:hi, 0]]
         first = int(starts.min())
-        assert np.array_equal(gk[first:first + keys.size], keys)
+        assert np.array_equal(gk[first:first + keys.size], (keys >> np.uint64(32)).astype(np.uint32))
         assert np.array_equal(gv[first:first + keys.size], vals)
         exp_r = np.where(ranges[:, 1:] > ranges[:, :1], ranges + first, 0)
         assert np.array_equal(gr[lo:hi], exp_r)

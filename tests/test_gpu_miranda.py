@@ -94,8 +94,8 @@ def test_c4_binning_bit_exact_on_one_view(c4):
     keys = keys + (np.uint64(v * tiles) << np.uint64(32))
     gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)[v * tiles:(v + 1) * tiles]
     first = int(gr[gr[:, 1] > gr[:, 0], 0].min())
-    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)[first:first + keys.size]
-    assert np.array_equal(gk, keys)
+    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint32)[first:first + keys.size]
+    assert np.array_equal(gk, (keys >> np.uint64(32)).astype(np.uint32))
     del gk
     gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy()[first:first + vals.size].astype(np.int64)
     assert np.array_equal(gv, vals)

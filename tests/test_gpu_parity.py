@@ -172,7 +172,7 @@ def test_binning_is_bit_exact(ctx, name):
     r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
     r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
     keys, vals, ranges, per_view = expected_binning(r0, r2, r3, cams, n, stride)
-    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)
+    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint32)
     gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64)
     gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
     inst, bins, _ = ctx.gs_get_counts()
@@ -181,7 +181,9 @@ def test_binning_is_bit_exact(ctx, name):
     for v in range(len(cams)):
         t = r3[v * stride: v * stride + n, 1].astype(np.int64)
         assert int(t.sum()) == int(per_view[v])
-    assert np.array_equal(gk, keys)
+    # the bins of the sorted (bin, depth) keys; within a bin the Gaussians in
+    # (depth, index) order
+    assert np.array_equal(gk, (keys >> np.uint64(32)).astype(np.uint32))
     assert np.array_equal(gv, vals)
     assert np.array_equal(gr, ranges)
     # the packed tile rect of every touching (view, Gaussian) pair
@@ -192,18 +194,27 @@ def test_binning_is_bit_exact(ctx, name):
         px, py = r3[sl, 2].astype(np.int64), r3[sl, 3].astype(np.int64)
         assert np.array_equal((px & 0xFFFF)[on], x0[on]) and np.array_equal((px >> 16)[on], x1[on])
         assert np.array_equal((py & 0xFFFF)[on], y0[on]) and np.array_equal((py >> 16)[on], y1[on])
-    # the sort ran only the passes whose digit varies in some view (the
-    # depth exponent byte is one digit for these scenes and is skipped)
+    # both sorts ran only the passes whose digit varies in some view
     ctrl = ctx.gs_get_buffer(gs.GS_BUF_SORT_CTRL).cpu().numpy().astype(np.int64)
     npass = ctrl.size - 1
-    # each view's segment is sorted on key - (view's first bin << 32)
+    # the instances of each view are sorted on bin - view's first bin
     offs = np.cumsum([0] + [((c["width"] + 15) // 16) * ((c["height"] + 15) // 16) for c in cams])
-    view = np.searchsorted(offs, (keys >> np.uint64(32)).astype(np.int64), side="right") - 1
-    local = keys - (offs[view].astype(np.uint64) << np.uint64(32))
+    b = (keys >> np.uint64(32)).astype(np.int64)
+    view = np.searchsorted(offs, b, side="right") - 1
+    local = b - offs[view]
+    assert (1 << (8 * npass)) >= max(offs[1:] - offs[:-1]) > (1 << (8 * (npass - 1)))
     for p in range(npass):
-        dg = (local >> np.uint64(8 * p)) & np.uint64(255)
+        dg = (local >> (8 * p)) & 255
         one = all(np.unique(dg[view == v]).size <= 1 for v in range(len(cams)))
         assert bool(ctrl[p] & 2) == one
+    # the visible Gaussians of each view are sorted on their depth bits
+    dctrl = ctx.gs_get_buffer(gs.GS_BUF_DEPTH_CTRL).cpu().numpy().astype(np.int64)
+    assert dctrl.size == 5
+    dbits = [np.ascontiguousarray(r2[v * stride:v * stride + n, 3]).view(np.uint32)[r3[v * stride:v * stride + n, 1] > 0]
+             for v in range(len(cams))]
+    for p in range(4):
+        one = all(np.unique((d >> (8 * p)) & 255).size <= 1 for d in dbits)
+        assert bool(dctrl[p] & 2) == one
 
 
 def test_binning_with_empty_and_uneven_views(ctx):
@@ -220,10 +231,10 @@ def test_binning_with_empty_and_uneven_views(ctx):
     r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
     keys, vals, ranges, per_view = expected_binning(r0, r2, r3, cams, n, stride)
     assert per_view[0] == per_view[2] == per_view[5] == 0 and per_view[1] > 0 and per_view[3] > 0
-    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)
+    gk = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint32)
     gv = ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64)
     gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
-    assert np.array_equal(gk, keys)
+    assert np.array_equal(gk, (keys >> np.uint64(32)).astype(np.uint32))
     assert np.array_equal(gv, vals)
     assert np.array_equal(gr, ranges)
 
@@ -425,8 +436,8 @@ def test_options_reject_bad_values(ctx):
 
 @pytest.mark.parametrize("items", [12, 20, 24])
 def test_sort_partition_sizes_give_the_same_binning(ctx, items):
-    """Every radix-sort partition size sorts to the same keys, values and
-    ranges (bit-exact against the CPU recomputation)."""
+    """Every radix-sort partition size (both sorts) gives the same bins,
+    values and ranges (bit-exact against the CPU recomputation)."""
     scene, cams = SCENES["random_deg3_mixed"]()
     ctx.gs_set_option(gs.GS_OPT_SORT_ITEMS, items)
     try:
@@ -436,7 +447,8 @@ def test_sort_partition_sizes_give_the_same_binning(ctx, items):
         r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
         r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
         keys, vals, ranges, _ = expected_binning(r0, r2, r3, cams, n, stride)
-        assert np.array_equal(ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64), keys)
+        assert np.array_equal(ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint32),
+                              (keys >> np.uint64(32)).astype(np.uint32))
         assert np.array_equal(ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64), vals)
         assert np.array_equal(ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64), ranges)
     finally:

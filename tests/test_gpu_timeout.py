@@ -1,13 +1,14 @@
-"""The bounded wait of the radix sort's look-back (GPU only): with the wait
-limit at 0 every partition that has to look back gives up at once (the
-blocks return; nothing hangs), the next gs_sync reports GS_ETIMEOUT and
-clears the status, and the same context then sorts correctly with the
-default limit."""
+"""The bounded waits of the binning's look-backs (GPU only: the depth sort,
+the emission and the tile sort): with the wait limit at 0 every partition
+that has to look back gives up at once (the blocks return; nothing hangs),
+the next gs_sync reports GS_ETIMEOUT and clears the status, and the same
+context then bins correctly with the default limit."""
 import numpy as np
 import pytest
 import torch
 
 from paper_2509_05216_gb300 import gs, inputs
+from tests.gpu_helpers import expected_binning
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +39,14 @@ def test_sort_wait_limit_reports_timeout_and_the_context_recovers():
         ctx.gs_project(p, scene["n"], scene["deg"], cams)
         ctx.gs_bin_sort()
         ctx.gs_sync()
-        keys = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint64)[:inst]
+        keys = ctx.gs_get_buffer(gs.GS_BUF_KEYS).cpu().numpy().view(np.uint32)
         assert keys.size == inst and np.all(keys[1:] >= keys[:-1])
+        stride = scene["params"].shape[1]
+        r0 = ctx.gs_get_buffer(gs.GS_BUF_REC0).cpu().numpy()
+        r2 = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
+        r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
+        ek, ev, er, _ = expected_binning(r0, r2, r3, cams, scene["n"], stride)
+        assert np.array_equal(keys, (ek >> np.uint64(32)).astype(np.uint32))
+        assert np.array_equal(ctx.gs_get_buffer(gs.GS_BUF_VALS).cpu().numpy().astype(np.int64), ev)
     finally:
         ctx.close()
