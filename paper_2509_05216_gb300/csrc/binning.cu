@@ -169,6 +169,47 @@ __device__ __forceinline__ int segment_of(const uint32_t* off, int B, uint64_t i
   return lo;
 }
 
+// Partition order of the passes of a sort: ticket t takes partition lp of
+// view v, the tickets going round the views (every view's partition 0, then
+// every view's partition 1, ...; views out of partitions are passed over).
+// The partitions in flight then spread over the views, so a partition's
+// look-back -- which stops at its view's first partition -- meets a
+// published prefix a few partitions back instead of walking past every
+// partition in flight.  Within a view the partitions still take increasing
+// tickets, which is all the look-back needs to make progress.
+// order[t] = part_off[v] + lp, the partition's status slot.
+__global__ void partition_order_kernel(const uint32_t* __restrict__ part_off, int B, uint32_t* __restrict__ order,
+                                       int64_t slots) {
+  const uint32_t total = part_off[B];
+  uint32_t most = 0;
+  for (int v = 0; v < B; v++) most = max(most, part_off[v + 1] - part_off[v]);
+  for (int64_t ti = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ti < slots && ti < (int64_t)total;
+       ti += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t = (uint32_t)ti;
+    // the largest round lo with c(lo) <= t, c(L) = sum_v min(P_v, L) (the
+    // tickets of rounds 0 .. L - 1); c(most) = total > t
+    uint32_t lo = 0, hi = most;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      uint32_t cm = 0;
+      for (int v = 0; v < B; v++) cm += min(part_off[v + 1] - part_off[v], mid);
+      if (cm <= t) lo = mid; else hi = mid;
+    }
+    uint32_t r = t;
+    for (int v = 0; v < B; v++) r -= min(part_off[v + 1] - part_off[v], lo);
+    // the r-th view, in view order, that still has a partition in round lo
+    for (int v = 0; v < B; v++) {
+      if (part_off[v + 1] - part_off[v] > lo) {
+        if (r == 0) {
+          order[t] = part_off[v] + lo;
+          break;
+        }
+        r--;
+      }
+    }
+  }
+}
+
 // The key base of segment v: its keys' digits are taken from key - base.
 __device__ __forceinline__ uint64_t segment_key_base(const SortArgs& a, int v) {
   return a.views ? (uint64_t)(uint32_t)a.views[v].tile_offset << a.view_shift : 0ull;
@@ -262,7 +303,8 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   const int shift = kRadixBits * pass;
   const uint32_t nparts = a.part_off[a.B];
   if (tid == 0) {
-    const uint32_t part = atomicAdd(a.counters + pass, 1u);
+    const uint32_t t = atomicAdd(a.counters + pass, 1u);
+    const uint32_t part = t < nparts ? (a.part_order ? a.part_order[t] : t) : nparts;  // status slot
     sm.part = part;
     sm.timed_out = 0;
     if (part < nparts) {
@@ -529,6 +571,12 @@ __global__ void sort_control_kernel(SortArgs a, int items) {
 void launch_digit_scan(const SortArgs& a, int items, cudaStream_t s) {
   digit_scan_kernel<<<a.B, kRadix, 0, s>>>(a);
   sort_control_kernel<<<1, 32, 0, s>>>(a, items);
+  if (a.part_order) {
+    const int64_t slots = sort_partitions(a.capacity, items, a.B);
+    const int64_t blocks = std::min<int64_t>((slots + 255) / 256, (int64_t)sm_count() * 4);
+    partition_order_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a.part_off, a.B, a.part_order,
+                                                                               slots);
+  }
 }
 
 void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, int items, cudaStream_t s) {

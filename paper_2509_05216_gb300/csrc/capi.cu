@@ -82,7 +82,7 @@ struct gs_ctx {
       target_slot, host_tgt0, host_tgt1, pair_stats, cells, vismask, ssim_table, ssim_partials, ssim_sums,
       init_pts, init_scales, knn_part, knn_table, ord_keys0, ord_keys1, ord_vals0, ord_vals1, ord_total, ord_hist,
       ord_hist_scan, ord_lookback, ord_counters, ord_views, tile_order, vis_sums, vis_offsets, dtotal, dkeys0,
-      dkeys1, dvals0, dvals1, dhist, dhist_scan, dlookback, elookback;
+      dkeys1, dvals0, dvals1, dhist, dhist_scan, dlookback, elookback, dorder, torder;
 
   // launch accounting and optional per-kernel event timing
   struct KStat {
@@ -354,6 +354,8 @@ gs_status ctx_reserve(gs_ctx* c, int64_t stride, int B, int64_t bins, int64_t pi
   GS_TRY(ensure_exact(c, c->lookback, sort_lookback_bytes(cap, c->sort_items, B) * tpass));
   GS_TRY(ensure_exact(c, c->dlookback, sort_lookback_bytes(pc, c->sort_items, B) * kDepthPasses));
   GS_TRY(ensure_exact(c, c->elookback, emit_lookback_bytes(pc, B)));
+  GS_TRY(ensure_exact(c, c->torder, sizeof(uint32_t) * sort_partitions(cap, c->sort_items, B)));
+  GS_TRY(ensure_exact(c, c->dorder, sizeof(uint32_t) * sort_partitions(pc, c->sort_items, B)));
   GS_TRY(ensure_exact(c, c->counters, sizeof(uint32_t) * kSortCounters));
   GS_TRY(ensure_exact(c, c->sorted_slots, 2 * sizeof(void*)));
   GS_TRY(ensure_exact(c, c->tfinal, sizeof(float) * pixels));
@@ -428,7 +430,7 @@ void gs_destroy(gs_ctx* c) {
                     &c->ord_vals0, &c->ord_vals1, &c->ord_total, &c->ord_hist, &c->ord_hist_scan, &c->ord_lookback,
                     &c->ord_counters, &c->ord_views, &c->tile_order, &c->vis_sums, &c->vis_offsets, &c->dtotal,
                     &c->dkeys0, &c->dkeys1, &c->dvals0, &c->dvals1, &c->dhist, &c->dhist_scan, &c->dlookback,
-                    &c->elookback};
+                    &c->elookback, &c->dorder, &c->torder};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (const auto& p : c->pending) {
@@ -593,6 +595,8 @@ gs_status gs_bin_sort(gs_ctx* c) {
   GS_TRY(ensure(c, c->lookback, lb * tpass));
   GS_TRY(ensure(c, c->dlookback, dlb * kDepthPasses));
   GS_TRY(ensure(c, c->elookback, elb));
+  GS_TRY(ensure(c, c->torder, sizeof(uint32_t) * sort_partitions(cap, c->sort_items, B)));
+  GS_TRY(ensure(c, c->dorder, sizeof(uint32_t) * sort_partitions(pc, c->sort_items, B)));
   GS_TRY(ensure(c, c->counters, sizeof(uint32_t) * kSortCounters));
   GS_TRY(ensure(c, c->sorted_slots, 2 * sizeof(void*)));
   // contribution masks: every tile's region padded to whole batches of 32
@@ -636,6 +640,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   ds.B = B;
   ds.seg = dw.seg;
   ds.part_off = dw.part_off;
+  ds.part_order = P<uint32_t>(c->dorder);
   ds.hist = P<uint32_t>(c->dhist);
   ds.hist_scan = P<uint32_t>(c->dhist_scan);
   ds.ctrl = dw.ctrl;
@@ -647,7 +652,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   ds.wait_rounds = c->sort_wait;
   ds.status = c->status_d;
   {
-    LaunchScope ls(c, "depth_histogram", 3);
+    LaunchScope ls(c, "depth_histogram", 4);
     launch_digit_histogram(ds, pc, c->sort_items, c->stream);
   }
   GS_CHECK_LAUNCH(c);
@@ -700,6 +705,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   sa.B = B;
   sa.seg = iw.seg;
   sa.part_off = iw.part_off;
+  sa.part_order = P<uint32_t>(c->torder);
   sa.hist = P<uint32_t>(c->hist);
   sa.hist_scan = P<uint32_t>(c->hist_scan);
   sa.ctrl = iw.ctrl;
@@ -713,7 +719,7 @@ gs_status gs_bin_sort(gs_ctx* c) {
   sa.sorted_keys = reinterpret_cast<const void**>(c->sorted_slots.p);
   sa.sorted_vals = reinterpret_cast<const uint32_t**>(P<unsigned char>(c->sorted_slots) + sizeof(void*));
   {
-    LaunchScope ls(c, "tile_scan", 2);
+    LaunchScope ls(c, "tile_scan", 3);
     launch_digit_scan(sa, c->sort_items, c->stream);
   }
   GS_CHECK_LAUNCH(c);

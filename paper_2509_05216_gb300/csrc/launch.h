@@ -134,6 +134,8 @@ struct SortArgs {
   const ViewRec* views;      // NULL: key base 0 for every segment
   const uint32_t* seg;       // [B + 1] segment offsets
   uint32_t* part_off;        // [B + 1] first partition of each segment
+  uint32_t* part_order;      // [partitions] status slot of the partition each ticket takes
+                             // (views interleaved; NULL: ticket order)
   uint32_t* single;          // [B][8] 1 if the view's keys share one digit in the pass
   uint32_t* hist;            // [B][npass][256] digit counts
   uint32_t* hist_scan;       // [B][npass][256] exclusive digit offsets within the segment
@@ -160,7 +162,7 @@ size_t sort_lookback_bytes(int64_t count, int items, int segments);
 int64_t sort_partitions(int64_t count, int items, int segments);
 // digit counts (into a.hist, zeroed before), their scans and the pass control words
 void launch_digit_histogram(const SortArgs& a, int64_t grid_hint, int items, cudaStream_t s);
-// the scans and control words only (a.hist counted elsewhere)
+// the scans, control words and partition order only (a.hist counted elsewhere)
 void launch_digit_scan(const SortArgs& a, int items, cudaStream_t s);
 // items: keys per thread (12, 16, 20 or 24); the grid covers a.capacity
 void launch_onesweep_pass(const SortArgs& a, int pass, int items, cudaStream_t s);
