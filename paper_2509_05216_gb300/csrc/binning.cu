@@ -274,9 +274,12 @@ constexpr uint32_t kCtrlParity = 1u, kCtrlTrivial = 2u;
 template <typename KeyT, int ITEMS>
 struct SortSmem {
   static constexpr int kTile = kSortThreads * ITEMS;
-  uint32_t warp_hist[kSortWarps][kRadix];  // per-warp digit counts -> offsets
-  uint32_t digit_start[kRadix];            // exclusive scan of the tile's digit counts
-  uint32_t global_base[kRadix];            // global destination of the digit's first key
+  // per-warp digit counts -> position of the warp's first key of the digit
+  // in the partition-sorted order
+  uint32_t warp_hist[kSortWarps][kRadix];
+  // global destination of the digit's first key minus its position in the
+  // partition-sorted order (the scatter adds the position)
+  uint32_t global_base[kRadix];
   uint32_t wtot[kSortWarps];
   uint32_t part, seg, seg_lo, seg_hi, first_part;
   uint64_t key_base;
@@ -374,7 +377,8 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
   }
   volatile uint32_t* lb = lookback;
   lb[(int64_t)part * kRadix + d] = (lp0 == 0 ? kFlagPrefix : kFlagAggregate) | tile_count;
-  // digit starts inside the partition (block exclusive scan over the 256 digits)
+  // digit starts inside the partition (block exclusive scan over the 256
+  // digits), folded into the warp offsets and the global bases
   {
     uint32_t inc = tile_count;
 #pragma unroll
@@ -386,7 +390,11 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     __syncthreads();
     uint32_t wpre = 0;
     for (int w = 0; w < wid; w++) wpre += sm.wtot[w];
-    sm.digit_start[d] = wpre + inc - tile_count;
+    const uint32_t digit_start = wpre + inc - tile_count;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) sm.warp_hist[w][d] += digit_start;
+    // (thread d owns entry d; the digit's destination is added after the look-back)
+    sm.global_base[d] = 0u - digit_start;
   }
   __syncthreads();
   // keys -> partition-sorted positions in shared memory (before the
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     uint32_t lpos = 0xffffu;
     if (ok) {
       const uint32_t dd = (word[i] >> wsh) & (kRadix - 1);
-      lpos = sm.digit_start[dd] + sm.warp_hist[wid][dd] + r;
+      lpos = sm.warp_hist[wid][dd] + r;
       sm.buf[lpos] = kWords == 1 ? (KeyT)(word[i] + wsub) : kin[base + wl + 32 * i];
     }
     if (i & 1) rk[i >> 1] = (rk[i >> 1] & 0xffffu) | (lpos << 16); else rk[i >> 1] = (rk[i >> 1] & 0xffff0000u) | lpos;
@@ -447,7 +455,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     if (failed) sm.timed_out = 1;
     lb[(int64_t)part * kRadix + d] = failed ? kFlagFailed : (kFlagPrefix | ((excl + tile_count) & kValueMask));
   }
-  sm.global_base[d] = sm.seg_lo + hist_pass[d] + excl;
+  sm.global_base[d] += sm.seg_lo + hist_pass[d] + excl;
   __syncthreads();
   if (sm.timed_out) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
@@ -464,7 +472,7 @@ __global__ void __launch_bounds__(kSortThreads, MIN_BLOCKS) onesweep_pass_kernel
     if (q < n_here) {
       const KeyT k = sm.buf[q];
       const uint32_t dd = (uint32_t)((KeyT)(k - kb) >> shift) & (kRadix - 1);
-      dst[t] = sm.global_base[dd] + ((uint32_t)q - sm.digit_start[dd]);
+      dst[t] = sm.global_base[dd] + (uint32_t)q;
       if (dst[t] < hi) kout[dst[t]] = k;
     }
   }
