@@ -81,6 +81,20 @@ __device__ __forceinline__ float splat_power(float A, float B, float C, float dx
   return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
 }
 
+// One Adam step of one scalar (torch.optim.Adam with bias correction):
+// m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, p -= lr' m / (sqrt(v) /
+// sqrt(1 - b2^t) + eps) with lr' = lr / (1 - b1^t).  Every rounding is
+// spelled out, so the stand-alone Adam kernel and the projection backward's
+// fused update give the same bits.
+struct AdamStep {
+  float b1, b2, c1, c2, eps, isb2;  // c1 = 1 - b1, c2 = 1 - b2, isb2 = 1 / sqrt(1 - b2^t)
+};
+__device__ __forceinline__ void adam_scalar(float& p, float& m, float& v, float g, float lr, const AdamStep& s) {
+  m = __fmaf_rn(s.b1, m, __fmul_rn(s.c1, g));
+  v = __fmaf_rn(s.b2, v, __fmul_rn(__fmul_rn(s.c2, g), g));
+  p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, m), __fmaf_rn(__fsqrt_rn(v), s.isb2, s.eps)));
+}
+
 // Tile rect of a splat: x in [floor((mx - r)/16), floor((mx + r + 15)/16)),
 // likewise y, clamped to the view's tile grid.  Shared by the projection
 // (tile counts) and the duplication (instances), so both see the same rect.

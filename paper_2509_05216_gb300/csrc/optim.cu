@@ -86,13 +86,18 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   if (threadIdx.x < 64) lr_s[threadIdx.x] = a.consts[threadIdx.x];
   if (threadIdx.x == 0) isb2_s = a.consts[64];
   __syncthreads();
-  const float inv_sqrt_bc2 = isb2_s;
+  AdamStep st;
+  st.b1 = a.beta1;
+  st.b2 = a.beta2;
+  st.c1 = 1.f - a.beta1;
+  st.c2 = 1.f - a.beta2;
+  st.eps = a.eps;
+  st.isb2 = isb2_s;
   const int64_t cols = a.stride / 4;
   float4* p4 = reinterpret_cast<float4*>(a.p);
   const float4* g4 = reinterpret_cast<const float4*>(a.g);
   float4* m4 = reinterpret_cast<float4*>(a.m);
   float4* v4 = reinterpret_cast<float4*>(a.v);
-  const float b1 = a.beta1, b2 = a.beta2, c1 = 1.f - a.beta1, c2 = 1.f - a.beta2;
   for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
        col += (int64_t)gridDim.x * blockDim.x) {
     bool on[4] = {true, true, true, true};
@@ -111,10 +116,8 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
       const float4 g = g4[i];
       const float4 m0 = m4[i], v0 = v4[i], p0 = p4[i];
       float4 m = m0, v = v0, p = p0;
-#define ADAM_LANE(f, k)                                               \
-  m.f = fmaf(b1, m.f, c1 * g.f);                                      \
-  v.f = fmaf(b2, v.f, c2 * g.f * g.f);                                \
-  p.f -= lr * m.f / fmaf(sqrtf(v.f), inv_sqrt_bc2, a.eps);            \
+#define ADAM_LANE(f, k)                \
+  adam_scalar(p.f, m.f, v.f, g.f, lr, st); \
   if (!on[k]) { m.f = m0.f; v.f = v0.f; p.f = p0.f; }
       ADAM_LANE(x, 0) ADAM_LANE(y, 1) ADAM_LANE(z, 2) ADAM_LANE(w, 3)
 #undef ADAM_LANE
