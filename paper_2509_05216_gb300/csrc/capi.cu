@@ -44,6 +44,11 @@ struct gs_ctx {
   cudaStream_t graph_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t staged_ev = nullptr;  // the graph's staging copies have run
+  // a captured step clears the 2D-gradient records on a side branch that
+  // runs beside the forward compositing (fork and join events)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  bool g2d_cleared = false;  // the next gs_raster_bwd finds the records zeroed
   int graph_B = 0;
   std::vector<int> graph_res;        // W, H per view of the captured batch
   gs_adam_hp graph_hp{};
@@ -445,6 +450,9 @@ void gs_destroy(gs_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
   if (c->staged_ev) cudaEventDestroy(c->staged_ev);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
   if (c->copy_stream) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamDestroy(c->copy_stream);
@@ -891,7 +899,8 @@ gs_status gs_raster_bwd(gs_ctx* c, const gs_params* params, const float* dL_dima
   set_device(c);
   const size_t g2d_bytes = sizeof(float) * (kG2dGeo + kG2dCol) * c->B * c->stride;
   GS_TRY(ensure(c, c->g2d, g2d_bytes));
-  GS_CUDA(c, cudaMemsetAsync(c->g2d.p, 0, g2d_bytes, c->stream));
+  if (!c->g2d_cleared) GS_CUDA(c, cudaMemsetAsync(c->g2d.p, 0, g2d_bytes, c->stream));
+  c->g2d_cleared = false;
   RasterArgs r = raster_args(c);
   r.dimage = dL_dimages;
   r.g2d = P<float>(c->g2d);
@@ -1510,6 +1519,11 @@ gs_status gs_train_graph_capture(gs_ctx* c, gs_params* p, gs_params* g, gs_param
   GS_TRY(gs_sync(c));
   // 2. capture on a private stream
   if (!c->graph_stream) GS_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+  if (!c->side_stream) GS_CUDA(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+  if (!c->fork_ev) GS_CUDA(c, cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+  if (!c->join_ev) GS_CUDA(c, cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+  const size_t g2d_bytes = sizeof(float) * (kG2dGeo + kG2dCol) * (size_t)B * c->stride;
+  if (c->g2d.cap < g2d_bytes) return fail(c, GS_ESTATE, "2D-gradient records not sized by the warm-up pass");
   if (c->gexec) {
     GS_CUDA(c, cudaGraphExecDestroy(c->gexec));
     c->gexec = nullptr;
@@ -1535,8 +1549,18 @@ gs_status gs_train_graph_capture(gs_ctx* c, gs_params* p, gs_params* g, gs_param
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->staged_ev, c->stream, cudaEventRecordExternal);
     if (e == cudaSuccess) st = gs_project(c, p, cams, B);
     if (e == cudaSuccess && st == GS_OK) st = gs_bin_sort(c);
+    // the 2D-gradient records are cleared on a side branch beside the
+    // forward compositing (compute-bound, little DRAM traffic), joined
+    // before the backward adds into them
+    if (e == cudaSuccess && st == GS_OK) e = cudaEventRecord(c->fork_ev, c->stream);
+    if (e == cudaSuccess && st == GS_OK) e = cudaStreamWaitEvent(c->side_stream, c->fork_ev, 0);
+    if (e == cudaSuccess && st == GS_OK) e = cudaMemsetAsync(c->g2d.p, 0, g2d_bytes, c->side_stream);
+    if (e == cudaSuccess && st == GS_OK) e = cudaEventRecord(c->join_ev, c->side_stream);
     if (e == cudaSuccess && st == GS_OK) st = gs_raster_fwd_l1(c, images, targets, loss, dL_dimages);
+    if (e == cudaSuccess && st == GS_OK) e = cudaStreamWaitEvent(c->stream, c->join_ev, 0);
+    if (e == cudaSuccess && st == GS_OK) c->g2d_cleared = true;
     if (e == cudaSuccess && st == GS_OK) st = gs_raster_bwd(c, p, dL_dimages, g);
+    c->g2d_cleared = false;
     if (e == cudaSuccess && st == GS_OK) st = gs_adam(c, p, g, m, v, hp, 1);
     const cudaError_t e2 = cudaStreamEndCapture(c->graph_stream, &graph);
     if (e == cudaSuccess) e = e2;
