@@ -570,6 +570,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     __syncwarp();
     for (int it = 0; G::NG > 1 ? it < iters : mask != 0u; it++) {
       const bool act = mask != 0u;
+      // (an idle group evaluates slot 0, which every batch stages: b0 < n)
       const int j = act ? __ffs(mask) - 1 : 0;
       mask &= mask - 1u;
       const float4 q0 = s0[w][j];
@@ -760,10 +761,14 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 8 : 1) raster_bw
     uint32_t mask = G::NG > 1 ? __shfl_sync(0xffffffffu, cm, geo.grp) : any;
     int iters = 32;
     if constexpr (G::NG > 1) iters = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mask));
+    // a group that has run out of entries evaluates a staged one with no
+    // effect: a slot this batch did not stage holds stale shared memory,
+    // whose infinities would turn the zero-weighted updates into NaN
+    const int j_idle = 31 - __clz(any);
     __syncwarp();
     for (int it = 0; G::NG > 1 ? it < iters : mask != 0u; it++) {  // back to front
       const bool act = mask != 0u;
-      const int j = act ? 31 - __clz(mask) : 0;
+      const int j = act ? 31 - __clz(mask) : j_idle;
       mask = act ? mask ^ (1u << j) : 0u;
       const float4 q0 = s0[w][j];
       const float4 q2 = s2[w][j];
