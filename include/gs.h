@@ -178,9 +178,14 @@ gs_status gs_get_option(gs_ctx* ctx, int32_t option, int64_t* value);
  * each Gaussian: t = W mu + tau, cull if depth <= znear, Sigma = R S S^T R^T,
  * Sigma' = J W Sigma W^T J^T + 0.3 I (J with image-plane slopes clamped to
  * 1.3x the half field of view), conic = Sigma'^-1, radius
- * ceil(3 sqrt(lambda_max)), tile rect, opacity sigma(o) and view-dependent
- * colour max(0, SH(d) + 0.5).  Results stay in the context for the next
- * steps.  1 <= B <= max_views; cameras may differ in resolution.
+ * ceil(3 sqrt(lambda_max)), the tile rect of that radius, opacity sigma(o)
+ * and view-dependent colour max(0, SH(d) + 0.5).  The tiles that receive the
+ * Gaussian are those of the rect that the box around its alpha >= 1/255
+ * ellipse (half-extents hx, hy of GS_BUF_REC2, the box the compositing
+ * passes cull with) reaches: a tile the box misses holds no pixel where the
+ * Gaussian could contribute, so leaving it out changes no pixel.  Results
+ * stay in the context for the next steps.  1 <= B <= max_views; cameras may
+ * differ in resolution.
  * Errors: GS_EINVAL (null pointers, n <= 0, sh_degree outside 0..3, bad
  * stride/alignment, width/height <= 0), GS_ENOMEM, GS_ECUDA. */
 gs_status gs_project(gs_ctx* ctx, const gs_params* params, const gs_camera* cams, int32_t B);
@@ -505,14 +510,16 @@ typedef enum {
   GS_BUF_NLAST = 7,  /* uint32 [pixels]: 1 + list position of the last contributor */
   GS_BUF_G2D = 8,    /* float [B][N][8] records dL/d(mu_x, mu_y, A, B), dL/d(C, opacity), 0, 0,
                         then [B][N][4] records dL/d(r, g, b), 0 */
-  GS_BUF_REC3 = 9,   /* int4 [B][N]: radius, tiles touched (0: culled), tile rect
-                        x0 | x1 << 16 and y0 | y1 << 16 (half-open) */
+  GS_BUF_REC3 = 9,   /* int4 [B][N]: radius (0: the radius' rect misses the
+                        view), tiles that receive the Gaussian (0: none), and
+                        their rect x0 | x1 << 16, y0 | y1 << 16 (half-open): the
+                        radius' rect cut to the tiles the alpha box reaches */
   GS_BUF_SORT_CTRL = 10, /* uint32 [npass + 1]: control word of each pass of the
                         instances' sort by bin; bit 1 set = pass skipped (its
                         digit is the same for every key of each view), bit 0 =
                         source buffer */
-  GS_BUF_VISMASK = 11, /* uint64 [N]: bit v = the Gaussian touches a tile of view v
-                        of the last projected batch */
+  GS_BUF_VISMASK = 11, /* uint64 [N]: bit v = the Gaussian's radius rect meets view
+                        v of the last projected batch */
   GS_BUF_DEPTH_CTRL = 12 /* uint32 [5]: control words of the 4 passes of the visible
                         Gaussians' sort by depth bits, as GS_BUF_SORT_CTRL */
 } gs_buffer;

@@ -110,4 +110,19 @@ __device__ __forceinline__ bool tile_rect(const ViewRec& V, float mx, float my, 
   return x1 > x0 && y1 > y0;
 }
 
+// Tiles of one axis that the box [m - h, m + h] reaches with a pixel:
+// [t0, t1), clamped to [0, g).  Tile t spans pixels 16 t .. 16 t + 15; it is
+// reached iff 16 t <= m + h and 16 t + 15 >= m - h, with m + h and m - h the
+// FP32 sums the compositing kernels' box test forms, so a tile outside the
+// range fails that test at every pixel of it.  h < 0 (a splat that never
+// reaches alpha >= 1/255) gives an empty range.
+__device__ __forceinline__ void box_tiles(float m, float h, int g, int& t0, int& t1) {
+  const float lo = __fsub_rn(m, h), hi = __fadd_rn(m, h);
+  const float f = floorf(__fmul_rn(lo, 0.0625f));
+  const float first = lo <= __fadd_rn(__fmul_rn(16.f, f), 15.f) ? f : __fadd_rn(f, 1.f);
+  const float last = __fadd_rn(floorf(__fmul_rn(hi, 0.0625f)), 1.f);
+  t0 = (int)fminf((float)g, fmaxf(0.f, first));
+  t1 = (int)fminf((float)g, fmaxf(0.f, last));
+}
+
 }  // namespace gs

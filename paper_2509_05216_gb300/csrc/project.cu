@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
     const ViewRec& V = a.views[v];
     const int64_t o = (int64_t)v * a.stride + g;
     uint32_t tiles = 0;
+    bool touched = false;  // the 3-sigma rect meets the view
     int radius = 0;
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0;  // tile rect (half-open)
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
           const float mx = fmaf(V.fx, st.tx / st.tz, V.cx);
           const float my = fmaf(V.fy, st.ty / st.tz, V.cy);
           if (radius > 0 && tile_rect(V, mx, my, radius, x0, x1, y0, y1)) {
-            tiles = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+            touched = true;
             // colour
             float dx = mean[0] - V.campos[0], dy = mean[1] - V.campos[1], dz = mean[2] - V.campos[2];
             const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -232,15 +233,30 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
             r1 = make_float4(-0.5f * kLog2e * C, opacity, rgb[0], rgb[1]);
             blue = rgb[2];
             ex = make_float2(hx, hy);
+            // instances only in the rect's tiles that the alpha >= 1/255 box
+            // reaches: the others hold no pixel where the Gaussian passes the
+            // compositing kernels' box test, so no pixel changes without them
+            int bx0, bx1, by0, by1;
+            box_tiles(mx, hx, V.gw, bx0, bx1);
+            box_tiles(my, hy, V.gh, by0, by1);
+            x0 = max(x0, bx0);
+            x1 = min(x1, bx1);
+            y0 = max(y0, by0);
+            y1 = min(y1, by1);
+            if (x1 > x0 && y1 > y0) {
+              tiles = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+            } else {
+              x0 = x1 = y0 = y1 = 0;
+            }
           } else {
             radius = 0;
             x0 = x1 = y0 = y1 = 0;
           }
         }
       }
-      a.rec3[o] = make_int4(tiles ? radius : 0, (int)tiles, x0 | (x1 << 16), y0 | (y1 << 16));
+      a.rec3[o] = make_int4(touched ? radius : 0, (int)tiles, x0 | (x1 << 16), y0 | (y1 << 16));
       a.tiles[o] = make_uint2(tiles, __float_as_uint(depth));
-      vis |= tiles ? 1ull << v : 0ull;
+      vis |= touched ? 1ull << v : 0ull;
     }
     // the warp's 32 records (48 bytes each) go out through shared memory as
     // 96 coalesced 16-byte stores instead of 3 x 32 stores at a 48-byte stride

@@ -35,10 +35,37 @@ def cpu_rect(mx, my, r, W, H):
     return x0, x1, y0, y1
 
 
+def cpu_box_tiles(m, h, g):
+    """Tiles [t0, t1) of one axis that the box [m - h, m + h] reaches with a
+    pixel (tile t spans pixels 16 t .. 16 t + 15), clamped to [0, g): the
+    projection's range, from the same FP32 operations."""
+    f32 = np.float32
+    m = np.asarray(m, f32)
+    h = np.asarray(h, f32)
+    lo = (m - h).astype(f32)
+    hi = (m + h).astype(f32)
+    f = np.floor((lo * f32(0.0625)).astype(f32))
+    first = np.where(lo <= (f * f32(16)).astype(f32) + f32(15), f, (f + f32(1)).astype(f32))
+    last = (np.floor((hi * f32(0.0625)).astype(f32)) + f32(1)).astype(f32)
+    t0 = np.clip(first, 0, g).astype(np.int64)
+    t1 = np.clip(last, 0, g).astype(np.int64)
+    return t0, t1
+
+
+def cpu_cut_rect(mx, my, r, hx, hy, W, H):
+    """The radius' tile rect cut to the tiles the alpha box reaches (empty:
+    x1 <= x0 or y1 <= y0)."""
+    gw, gh = (W + 15) // 16, (H + 15) // 16
+    x0, x1, y0, y1 = cpu_rect(mx, my, r, W, H)
+    bx0, bx1 = cpu_box_tiles(mx, hx, gw)
+    by0, by1 = cpu_box_tiles(my, hy, gh)
+    return np.maximum(x0, bx0), np.minimum(x1, bx1), np.maximum(y0, by0), np.minimum(y1, by1)
+
+
 def expected_binning(rec0, rec2, rec3, cams, n, stride):
     """Keys, values and ranges recomputed on the CPU from the GPU's projection
-    (vectorised: one entry per (view, Gaussian, tile), stable sort by key, so
-    equal keys stay in Gaussian order)."""
+    (vectorised: one entry per (view, Gaussian, tile of the cut rect), stable
+    sort by key, so equal keys stay in Gaussian order)."""
     tile_off, t = [], 0
     for c in cams:
         tile_off.append(t)
@@ -50,9 +77,9 @@ def expected_binning(rec0, rec2, rec3, cams, n, stride):
         mx, my = rec0[sl, 0], rec0[sl, 1]
         rad = rec3[sl, 0].astype(np.int64)
         tiles = rec3[sl, 1].astype(np.int64)
-        x0, x1, y0, y1 = cpu_rect(mx, my, rad, c["width"], c["height"])
-        w = np.where(tiles > 0, x1 - x0, 0)
-        h = np.where(tiles > 0, y1 - y0, 0)
+        x0, x1, y0, y1 = cpu_cut_rect(mx, my, rad, rec2[sl, 1], rec2[sl, 2], c["width"], c["height"])
+        w = np.where(tiles > 0, np.maximum(x1 - x0, 0), 0)
+        h = np.where(tiles > 0, np.maximum(y1 - y0, 0), 0)
         area = w * h
         per_view.append(int(area.sum()))
         g = np.repeat(np.arange(n, dtype=np.int64), area)

@@ -11,7 +11,7 @@ import pytest
 import torch
 
 from paper_2509_05216_gb300 import gs, inputs
-from tests.gpu_helpers import cpu_rect, expected_binning, rel_l2, run_forward, to_dev_images
+from tests.gpu_helpers import cpu_cut_rect, expected_binning, rel_l2, run_forward, to_dev_images
 
 pytestmark = pytest.mark.gpu
 
@@ -122,17 +122,27 @@ def test_projection_matches_oracle(ctx, oracle, name):
     r2f = ctx.gs_get_buffer(gs.GS_BUF_REC2).cpu().numpy()
     r2 = r2f.astype(np.float64)
     r3 = ctx.gs_get_buffer(gs.GS_BUF_REC3).cpu().numpy()
+    vm = ctx.gs_get_buffer(gs.GS_BUF_VISMASK).cpu().numpy().view(np.uint64)
     for v, cam in enumerate(cams):
         sl = slice(v * stride, v * stride + n)
         pr = oracle.project(scene, cam)
         vis = (pr["flags"] & oracle.G_VISIBLE) != 0
-        tiles = r3[sl, 1]
+        touched = ((vm[:n] >> np.uint64(v)) & np.uint64(1)) != 0
         margin = (pr["flags"] & oracle.G_MARG_RECT) != 0
-        # visibility and radius agree except on marginal rects
-        bad = ((tiles > 0) != vis) & ~margin
+        # visibility (the radius' rect meets the view) and radius agree
+        # except on marginal rects
+        bad = (touched != vis) & ~margin
         assert not bad.any(), ("visibility differs", np.nonzero(bad)[0][:8], pr["ext"][bad][:8])
+        assert np.all(r3[sl, 0][~touched] == 0)
+        # instances: the radius' rect cut to the tiles the alpha box reaches,
+        # never more than the oracle's rect holds
+        x0, x1, y0, y1 = cpu_cut_rect(r0[sl, 0].astype(np.float32), r0[sl, 1].astype(np.float32),
+                                      r3[sl, 0].astype(np.int64), r2f[sl, 1], r2f[sl, 2], cam["width"], cam["height"])
+        cut = np.where(touched, np.maximum(x1 - x0, 0) * np.maximum(y1 - y0, 0), 0)
+        assert np.array_equal(r3[sl, 1].astype(np.int64), cut)
+        assert np.all(cut[~margin] <= pr["tiles"][~margin])
         rad = r3[sl, 0]
-        both = vis & (tiles > 0)
+        both = vis & touched
         # the radius ceil itself may flip where 3 sqrt(lambda) is within FP32
         # reach of an integer (the rect usually does not change then)
         ext = pr["ext"]
@@ -177,7 +187,7 @@ def test_binning_is_bit_exact(ctx, name):
     gr = ctx.gs_get_buffer(gs.GS_BUF_RANGES).cpu().numpy().astype(np.int64)
     inst, bins, _ = ctx.gs_get_counts()
     assert inst == keys.size == per_view.sum()
-    # per-(view, Gaussian) tile counts equal the rect areas
+    # per-(view, Gaussian) tile counts equal the cut rects' areas
     for v in range(len(cams)):
         t = r3[v * stride: v * stride + n, 1].astype(np.int64)
         assert int(t.sum()) == int(per_view[v])
@@ -186,10 +196,11 @@ def test_binning_is_bit_exact(ctx, name):
     assert np.array_equal(gk, (keys >> np.uint64(32)).astype(np.uint32))
     assert np.array_equal(gv, vals)
     assert np.array_equal(gr, ranges)
-    # the packed tile rect of every touching (view, Gaussian) pair
+    # the packed (cut) tile rect of every (view, Gaussian) pair with tiles
     for v, c in enumerate(cams):
         sl = slice(v * stride, v * stride + n)
-        x0, x1, y0, y1 = cpu_rect(r0[sl, 0], r0[sl, 1], r3[sl, 0].astype(np.int64), c["width"], c["height"])
+        x0, x1, y0, y1 = cpu_cut_rect(r0[sl, 0], r0[sl, 1], r3[sl, 0].astype(np.int64), r2[sl, 1], r2[sl, 2],
+                                      c["width"], c["height"])
         on = r3[sl, 1] > 0
         px, py = r3[sl, 2].astype(np.int64), r3[sl, 3].astype(np.int64)
         assert np.array_equal((px & 0xFFFF)[on], x0[on]) and np.array_equal((px >> 16)[on], x1[on])

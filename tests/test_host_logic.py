@@ -126,10 +126,13 @@ def test_compositing_work_counts_contributing_pairs_at_full_cost():
 
 def test_cpu_binning_reference_equals_brute_force():
     """The vectorised CPU binning that the GPU parity tests compare against,
-    checked against a plain loop over (view, Gaussian, tile) and a sort of
-    (key, Gaussian) pairs on small random inputs (empty rects, rects clipped
-    at the image border, equal depths)."""
-    from tests.gpu_helpers import cpu_rect, expected_binning
+    checked against a plain loop over (view, Gaussian, tile) -- keeping a
+    tile of the radius' rect if the alpha box reaches one of its pixels,
+    tested tile by tile -- and a sort of (key, Gaussian) pairs on small
+    random inputs (empty rects, rects clipped at the image border, boxes
+    narrower and wider than the rect, a box that reaches nothing, equal
+    depths)."""
+    from tests.gpu_helpers import cpu_cut_rect, cpu_rect, expected_binning
     rng = np.random.default_rng(5)
     cams = [inputs.pinhole(np.eye(4), 70, 45), inputs.pinhole(np.eye(4), 33, 80)]
     n, stride = 40, 48
@@ -142,9 +145,13 @@ def test_cpu_binning_reference_equals_brute_force():
         rec0[sl, 0] = rng.uniform(-20, c["width"] + 20, n)
         rec0[sl, 1] = rng.uniform(-20, c["height"] + 20, n)
         rad = rng.integers(0, 30, n)
-        x0, x1, y0, y1 = cpu_rect(rec0[sl, 0], rec0[sl, 1], rad, c["width"], c["height"])
-        tiles = (x1 - x0) * (y1 - y0)
-        rec3[sl, 0] = np.where(tiles > 0, rad, 0)
+        rec2[sl, 1] = rng.uniform(0.0, 45.0, n)
+        rec2[sl, 2] = rng.uniform(0.0, 45.0, n)
+        rec2[sl.start, 1] = -3.0e38  # reaches no pixel
+        x0, x1, y0, y1 = cpu_cut_rect(rec0[sl, 0], rec0[sl, 1], rad, rec2[sl, 1], rec2[sl, 2], c["width"],
+                                      c["height"])
+        tiles = np.maximum(x1 - x0, 0) * np.maximum(y1 - y0, 0)
+        rec3[sl, 0] = rad
         rec3[sl, 1] = tiles
         rec2[sl, 3] = rng.choice(np.float32([1.5, 2.25, 3.0, 7.0]), n)  # many equal depths
     keys, vals, ranges, per_view = expected_binning(rec0, rec2, rec3, cams, n, stride)
@@ -162,8 +169,14 @@ def test_cpu_binning_reference_equals_brute_force():
                                                           rec3[o:o + 1, 0].astype(np.int64),
                                                           c["width"], c["height"]))
             d = int(np.float32(rec2[o, 3]).view(np.uint32))
+            f32 = np.float32
+            mx, my, hx, hy = f32(rec0[o, 0]), f32(rec0[o, 1]), f32(rec2[o, 1]), f32(rec2[o, 2])
             for ty in range(y0, y1):
                 for tx in range(x0, x1):
+                    # a pixel of the tile inside the box (the compositing's FP32 sums)
+                    if not (f32(16 * tx) <= mx + hx and f32(16 * tx + 15) >= mx - hx and
+                            f32(16 * ty) <= my + hy and f32(16 * ty + 15) >= my - hy):
+                        continue
                     pairs.append((((tile_off + ty * gw + tx) << 32) | d, g))
                     count += 1
         ref_per_view.append(count)
