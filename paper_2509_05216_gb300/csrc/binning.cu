@@ -608,10 +608,11 @@ constexpr uint64_t kEmitPrefix = 2ull << 62;
 constexpr uint64_t kEmitFailed = 3ull << 62;
 constexpr uint64_t kEmitValue = (1ull << 62) - 1;
 constexpr int kEmitThreads = 256;
-constexpr int kEmitItems = 8;  // visible pairs per thread
+constexpr int kEmitItems = 16;  // visible pairs per thread
 constexpr int kEmitWarps = kEmitThreads / 32;
 constexpr int kEmitTile = kEmitThreads * kEmitItems;
-static_assert(kEmitWarps * kEmitItems == 64, "the chunk scan takes two chunks per lane");
+constexpr int kEmitChunkLane = kEmitWarps * kEmitItems / 32;  // chunks per lane in the block's chunk scan
+static_assert(kEmitWarps * kEmitItems % 32 == 0, "the chunk scan takes whole chunks per lane");
 
 int64_t emit_partitions(int64_t pairs, int segments) { return (pairs + kEmitTile - 1) / kEmitTile + segments; }
 
@@ -627,11 +628,9 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 // rect comes from its (view, Gaussian) entry.  The block scans the chunks'
 // instance counts, warp 0 finds the instances of the view's earlier
 // partitions by decoupled look-back (32 statuses per round, bounded waits),
-// and every warp expands its chunks cooperatively: lane j writes output
-// position base + 32 i + j of round i, (tile, Gaussian) of the pair that
-// owns it, tiles of a rect in row-major order.  The tile digits of the
-// following sort are counted on the way (shared memory, one flush per
-// block).
+// and each lane writes its pair's (tile, Gaussian) instances, tiles of a
+// rect in row-major order.  The tile digits of the following sort are
+// counted on the way (shared memory, one flush per block).
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   __shared__ uint32_t s_part[kMaxViews + 1];
   __shared__ uint32_t s_chunk[kEmitWarps * kEmitItems];
@@ -701,17 +700,25 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   }
   __syncthreads();
   if (wid == 0) {
-    // exclusive scan of the block's chunk counts (kEmitWarps x kEmitItems = 64: two per lane)
-    const uint32_t c0 = s_chunk[2 * lane], c1 = s_chunk[2 * lane + 1];
-    const uint32_t t = c0 + c1;
+    // exclusive scan of the block's chunk counts (kEmitChunkLane consecutive chunks per lane)
+    uint32_t cc[kEmitChunkLane], t = 0;
+#pragma unroll
+    for (int i = 0; i < kEmitChunkLane; i++) {
+      cc[i] = s_chunk[kEmitChunkLane * lane + i];
+      t += cc[i];
+    }
     uint32_t inc = t;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
       if (lane >= off) inc += y;
     }
-    s_chunk[2 * lane] = inc - t;
-    s_chunk[2 * lane + 1] = inc - t + c0;
+    uint32_t run = inc - t;
+#pragma unroll
+    for (int i = 0; i < kEmitChunkLane; i++) {
+      s_chunk[kEmitChunkLane * lane + i] = run;
+      run += cc[i];
+    }
     const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
     volatile uint64_t* lb = a.lookback;
     if (lane == 0) lb[part] = (lp == 0 ? kEmitPrefix : kEmitAggregate) | (uint64_t)total;
@@ -774,38 +781,24 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
       if (lane >= off) inc += y;
     }
-    const uint32_t excl = inc - c;
-    const uint32_t ctot = __shfl_sync(0xffffffffu, inc, 31);
-    const int64_t cb = gbase + s_chunk[wid * kEmitItems + r];
-    const uint32_t x0 = rx[r] & 0xffffu, rw = (rx[r] >> 16) - x0, y0 = ry[r] & 0xffffu;
-    for (uint32_t q0 = 0; q0 < ctot; q0 += 32) {
-      const uint32_t q = q0 + lane;
-      // owner: the last lane whose exclusive offset is <= q
-      int own = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = own + step;
-        const uint32_t ec = __shfl_sync(0xffffffffu, excl, cand & 31);
-        if (cand < 32 && ec <= q) own = cand;
-      }
-      const uint32_t e_own = __shfl_sync(0xffffffffu, excl, own);
-      const uint32_t ox0 = __shfl_sync(0xffffffffu, x0, own);
-      const uint32_t oy0 = __shfl_sync(0xffffffffu, y0, own);
-      const uint32_t orw = __shfl_sync(0xffffffffu, rw, own);
-      const uint32_t og = __shfl_sync(0xffffffffu, gi[r], own);
-      const bool ok = q < ctot;
-      uint32_t t = 0;
-      if (ok) {
-        const uint32_t local = q - e_own;
-        t = (oy0 + local / orw) * gw + ox0 + local % orw;
-        a.keys[cb + q] = toff + t;
-        a.vals[cb + q] = og;
-        atomicAdd(&s_hist[0][t & (kRadix - 1)], 1u);
-      }
-      for (int p = 1; p < tpass; p++) {
-        const uint32_t dg = (t >> (kRadixBits * p)) & (kRadix - 1);
-        const unsigned peers = __match_any_sync(0xffffffffu, ok ? dg : (uint32_t)kRadix);
-        if (ok && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_hist[p][dg], (uint32_t)__popc(peers));
+    // each lane writes its own pair's tiles, row by row, at the pair's
+    // offset in the chunk (pairs average under two tiles: the lanes' short
+    // runs are adjacent, so the stores of one step still fall in a few
+    // sectors, and no owner search or division per instance is needed)
+    int64_t o = gbase + s_chunk[wid * kEmitItems + r] + (inc - c);
+    const uint32_t x0 = rx[r] & 0xffffu, x1 = rx[r] >> 16;
+    uint32_t tx = x0, t = (ry[r] & 0xffffu) * gw + x0;
+    for (uint32_t k = 0; k < c; k++) {
+      a.keys[o] = toff + t;
+      a.vals[o] = gi[r];
+      o++;
+      atomicAdd(&s_hist[0][t & (kRadix - 1)], 1u);
+      for (int p = 1; p < tpass; p++) atomicAdd(&s_hist[p][(t >> (kRadixBits * p)) & (kRadix - 1)], 1u);
+      if (++tx == x1) {  // next row of the rect
+        tx = x0;
+        t += gw - (x1 - x0) + 1;
+      } else {
+        t++;
       }
     }
   }
