@@ -784,21 +784,44 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
     // each lane writes its own pair's tiles, row by row, at the pair's
     // offset in the chunk (pairs average under two tiles: the lanes' short
     // runs are adjacent, so the stores of one step still fall in a few
-    // sectors, and no owner search or division per instance is needed)
-    int64_t o = gbase + s_chunk[wid * kEmitItems + r] + (inc - c);
+    // sectors, and no owner search or division per instance is needed);
+    // a pair of more than 32 tiles is expanded by the whole warp below
+    const int64_t o0 = gbase + s_chunk[wid * kEmitItems + r] + (inc - c);
     const uint32_t x0 = rx[r] & 0xffffu, x1 = rx[r] >> 16;
-    uint32_t tx = x0, t = (ry[r] & 0xffffu) * gw + x0;
-    for (uint32_t k = 0; k < c; k++) {
-      a.keys[o] = toff + t;
-      a.vals[o] = gi[r];
-      o++;
-      atomicAdd(&s_hist[0][t & (kRadix - 1)], 1u);
-      for (int p = 1; p < tpass; p++) atomicAdd(&s_hist[p][(t >> (kRadixBits * p)) & (kRadix - 1)], 1u);
-      if (++tx == x1) {  // next row of the rect
-        tx = x0;
-        t += gw - (x1 - x0) + 1;
-      } else {
-        t++;
+    const uint32_t t0 = (ry[r] & 0xffffu) * gw + x0;
+    const bool big = c > 32u;
+    {
+      int64_t o = o0;
+      uint32_t tx = x0, t = t0;
+      for (uint32_t k = 0; k < (big ? 0u : c); k++) {
+        a.keys[o] = toff + t;
+        a.vals[o] = gi[r];
+        o++;
+        atomicAdd(&s_hist[0][t & (kRadix - 1)], 1u);
+        for (int p = 1; p < tpass; p++) atomicAdd(&s_hist[p][(t >> (kRadixBits * p)) & (kRadix - 1)], 1u);
+        if (++tx == x1) {  // next row of the rect
+          tx = x0;
+          t += gw - (x1 - x0) + 1;
+        } else {
+          t++;
+        }
+      }
+    }
+    for (unsigned bigs = __ballot_sync(0xffffffffu, big); bigs; bigs &= bigs - 1u) {
+      const int src = __ffs(bigs) - 1;
+      const uint32_t bc = __shfl_sync(0xffffffffu, c, src);
+      const int64_t bo = __shfl_sync(0xffffffffu, o0, src);
+      const uint32_t bx0 = __shfl_sync(0xffffffffu, x0, src), bw = __shfl_sync(0xffffffffu, x1, src) - bx0;
+      const uint32_t bt0 = __shfl_sync(0xffffffffu, t0, src), bg = __shfl_sync(0xffffffffu, gi[r], src);
+      for (uint32_t q0 = 0; q0 < bc; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        if (q < bc) {
+          const uint32_t t = bt0 + (q / bw) * gw + q % bw;
+          a.keys[bo + q] = toff + t;
+          a.vals[bo + q] = bg;
+          atomicAdd(&s_hist[0][t & (kRadix - 1)], 1u);
+          for (int p = 1; p < tpass; p++) atomicAdd(&s_hist[p][(t >> (kRadixBits * p)) & (kRadix - 1)], 1u);
+        }
       }
     }
   }
