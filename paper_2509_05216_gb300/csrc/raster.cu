@@ -533,6 +533,12 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
   const bool owner = (lane & 1) == 0 && ((lane / G::GCW) % RB) == 0;
   uint32_t* const cell_base = a.cells ? a.cells + cells_offset(rg.x, geo.bin) : nullptr;
   int b0 = 0;
+  // software pipeline over the batches: the record of batch k + 1 and the
+  // index of batch k + 2 are loaded while batch k is walked
+  uint32_t g_next = lane < n ? vals[rg.x + lane] : 0u;
+  uint32_t g_after = 32 + lane < n ? vals[rg.x + 32 + lane] : 0u;
+  float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0, p2 = p0;
+  if (lane < n) stage_one(a, v, g_next, p0, p1, p2);
   for (; b0 < n; b0 += 32) {
     if (__all_sync(0xffffffffu, done == all_done)) break;
     const int i = b0 + lane;
@@ -543,13 +549,17 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
     for (int sl = 0; sl < NSL; sl++) cm[sl] = 0u;
     uint32_t gbits = 0;
     if (i < n) {
-      float4 r0, r1, r2;
-      stage_one(a, v, vals[rg.x + i], r0, r1, r2);
+      const float4 r0 = p0, r1 = p1, r2 = p2;
       s0[w][lane] = r0;
       s1[w][lane] = r1;
       s2[w][lane] = r2;
       if constexpr (G::NG > 1) gbits = box_group_bits(r0, r1, r2, geo);
       else hit = ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
+    }
+    {
+      const int i1 = i + 32, i2 = i + 64;
+      if (i1 < n) stage_one(a, v, g_after, p0, p1, p2);
+      g_after = i2 < n ? vals[rg.x + i2] : 0u;
     }
     // each lane culls its own record; the warp (each lane group) walks the
     // survivors in order
@@ -737,12 +747,16 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS, PPT == 2 ? 8 : 1) raster_bw
   const int c00 = (((int)geo.wx0 & (kTile - 1)) >> 1) + 8 * (((int)geo.wy0 & (kTile - 1)) >> 2);
   const uint32_t* __restrict__ cell_base =
       a.cells + cells_offset(rg.x, geo.bin) + c00 + lane % NCX + 8 * (lane / NCX);
-  for (int bstart = ((total - 1) >> 5) << 5; bstart >= 0 && total > 0; bstart -= 32) {
+  // the cell masks of the next batch are loaded while a batch is walked
+  const int btop = ((total - 1) >> 5) << 5;
+  uint32_t cm_next = (total > 0 && lane < NCX * NCY) ? cell_base[btop] : 0u;
+  for (int bstart = btop; bstart >= 0 && total > 0; bstart -= 32) {
     const int i = bstart + lane;
     // entries at or past the warp's last contributor change nothing
     const int nb = min(32, total - bstart);
     const uint32_t lim = nb >= 32 ? 0xffffffffu : (1u << nb) - 1u;
-    const uint32_t cm = lane < NCX * NCY ? cell_base[bstart] & lim : 0u;
+    const uint32_t cm = cm_next & lim;
+    cm_next = (bstart >= 32 && lane < NCX * NCY) ? cell_base[bstart - 32] : 0u;
     const uint32_t any = __reduce_or_sync(0xffffffffu, cm);
     // a batch where nothing contributed to the warp's pixels is skipped
     // without loading its records
