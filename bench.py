@@ -578,27 +578,32 @@ def gpu_arm(args):
     # end to end through the host-buffer entry point: every step uploads its
     # targets from pinned host memory (overlapped with the previous step on
     # the library's copy stream) and reads its loss back to pinned memory
-    host_t = [t.cpu().pin_memory() for t in targets[:2]]
+    # the same batches as the device-timed steps, each target batch pinned
+    # once in host memory
+    e2e_k = [(args.warmup + i) % len(order) for i in range(args.e2e_steps)]
+    host_t = {k: targets[k].cpu().pin_memory() for k in sorted(set(e2e_k))}
     loss_h = [torch.empty(1, pin_memory=True) for _ in range(args.e2e_steps)]
     # untimed warm-up launches of this entry point (its copy stream, events
     # and device target buffers are created on first use), as for the
     # device-timed steps
     for i in range(max(2, args.warmup)):
         tr.t += 1
-        gctx.gs_train_graph_launch_host(batch(i % 2)[0], host_t[i % 2], tr.t, loss_h[0])
+        k = e2e_k[i % len(e2e_k)]
+        gctx.gs_train_graph_launch_host(cams[order[k] * B:(order[k] + 1) * B], host_t[k], tr.t, loss_h[0])
     gctx.gs_sync()
     torch.cuda.synchronize(dev)
     t_e0 = time.perf_counter()
     e0.record(stream)
     for i in range(args.e2e_steps):
-        b = i % 2
+        k = e2e_k[i]
         tr.t += 1
-        gctx.gs_train_graph_launch_host(batch(b)[0], host_t[b], tr.t, loss_h[i])
+        gctx.gs_train_graph_launch_host(cams[order[k] * B:(order[k] + 1) * B], host_t[k], tr.t, loss_h[i])
     e1.record(stream)
     gctx.gs_sync()
     torch.cuda.synchronize(dev)
     e2e_wall = time.perf_counter() - t_e0
-    e2e = args.e2e_steps * B * world / max(e0.elapsed_time(e1) / 1000.0, e2e_wall)
+    e2e_dev = e0.elapsed_time(e1) / 1000.0
+    e2e = args.e2e_steps * B * world / max(e2e_dev, e2e_wall)
     assert all(np.isfinite(float(x)) for x in loss_h)
 
     out = {
@@ -609,7 +614,11 @@ def gpu_arm(args):
         "config": config_dict(args, world),
         "plain_1view_views_per_s": round(plain, 3), "batched_over_plain": round(value / plain / world, 3),
         "e2e": {"value": round(e2e, 3), "unit": "views/s", "h2d_bytes_per_step": total * 4,
-                "d2h_bytes_per_step": 4},
+                "d2h_bytes_per_step": 4, "steps": args.e2e_steps,
+                "device_ms_per_step": round(1e3 * e2e_dev / args.e2e_steps, 3),
+                "host_wall_ms_per_step": round(1e3 * e2e_wall / args.e2e_steps, 3),
+                "note": "the device-timed steps' batches; each step's targets uploaded from pinned host memory "
+                        "on a copy stream and its loss read back; the slower of the two clocks counts"},
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof,
         "graph": "each timed step is one CUDA-graph launch of the whole step; per-kernel times and the roofline "
                  "come from the same steps launched call by call (%.3f ms/step)" % (ms_calls / args.steps),
