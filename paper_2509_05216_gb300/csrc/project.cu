@@ -64,6 +64,18 @@ struct ShEval {
   }
 };
 
+// The batch's view records copied into shared memory by the whole block
+// (ends with a block barrier).  The view loops read a record at every step,
+// and there a load that misses L1 sits on the step's dependency chain.
+__device__ __forceinline__ void stage_views(const ViewRec* views, int B, ViewRec* s_views) {
+  static_assert(sizeof(ViewRec) % 4 == 0, "view records are copied as 32-bit words");
+  const int words = B * (int)(sizeof(ViewRec) / 4);
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(views);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(s_views);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
 // View-independent part of the covariance: Sigma = M M^T with
 // M = R(q / |q|) diag(exp(s)), computed once per Gaussian.
 struct GaussCov {
@@ -171,11 +183,12 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
   __shared__ float4 s_rec[8][32 * kRecStride];  // 256 threads: 8 warps x 32 records
   __shared__ uint32_t s_bsum[kMaxViews];          // the block's instance count per view
   __shared__ uint32_t s_vsum[kMaxViews];          // and its visible Gaussians per view
+  __shared__ ViewRec s_views[kMaxViews];
   for (int i = threadIdx.x; i < a.B; i += blockDim.x) s_bsum[i] = s_vsum[i] = 0;
-  __syncthreads();
+  stage_views(a.views, a.B, s_views);
   uint64_t vis = 0;  // views where the Gaussian touches a tile
   for (int v = 0; v < a.B; v++) {
-    const ViewRec& V = a.views[v];
+    const ViewRec& V = s_views[v];
     const int64_t o = (int64_t)v * a.stride + g;
     uint32_t tiles = 0;
     bool touched = false;  // the 3-sigma rect meets the view
@@ -294,64 +307,83 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a) {
 // part of dL/dmean that flows through the view direction.  Writes the SH
 // gradient planes and initialises the mean planes.
 //
-// A block holds 32 Gaussians and three warps, one per colour channel: a
-// thread keeps only its channel's K coefficients and gradients in registers
-// (the channels are independent except through the direction gradient, which
-// is linear in the per-channel weights and is summed over the three warps at
-// the end), so three times as many warps fit on an SM as with one thread per
-// Gaussian, which hides the latency of the per-view chains.
+// One thread per Gaussian takes all three channels: the view direction, the
+// SH basis and the basis gradient are evaluated once per (view, Gaussian)
+// and shared by the channels.  The direction gradient is linear in the
+// per-channel weights gc_c sh_kc, so it is evaluated once on their sum over
+// the unclamped channels.  The colour record of the next visible view but
+// one is loaded while a view is processed.  The thread holds 96 values of
+// its own (coefficients and their gradients): capped at 128 registers (4
+// blocks, 16 warps per SM) it spills a few of them to L1, which measured
+// faster than 160 registers and 12 warps.
 template <int DEG>
-__global__ void __launch_bounds__(96) project_bwd_color_kernel(ProjectBwdArgs a) {
+__global__ void __launch_bounds__(128, 4) project_bwd_color_kernel(ProjectBwdArgs a) {
   constexpr int K = ShEval<DEG>::K;
-  __shared__ float s_gm[3][3][32];
-  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t g = (int64_t)blockIdx.x * 32 + lane;
-  const bool live = g < a.n;
+  // camera centres of the batch's views
+  __shared__ float4 s_cam[kMaxViews];
+  for (int i = threadIdx.x; i < a.B; i += blockDim.x)
+    s_cam[i] = make_float4(a.views[i].campos[0], a.views[i].campos[1], a.views[i].campos[2], 0.f);
+  __syncthreads();
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n) return;
   const float* P = a.params;
   const int64_t S = a.stride;
   // only the views where the Gaussian touches a tile have a nonzero 2D
-  // gradient: the others (and Gaussians invisible in every view) read nothing
-  uint64_t vm = live ? a.vismask[g] : 0ull;
-  float mean[3] = {0.f, 0.f, 0.f}, sh[K], gsh[K];
+  // gradient, and only their records are read; the parameters are loaded
+  // without waiting for the mask (a Gaussian invisible in every view reads
+  // them for nothing, but no load of the prologue waits on another)
+  uint64_t vm = a.vismask[g];
+  float mean[3], sh[3][K], gsh[3][K];
 #pragma unroll
-  for (int k = 0; k < K; k++) {
-    sh[k] = vm ? __ldg(P + (11 + 3 * k + c) * S + g) : 0.f;
-    gsh[k] = 0.f;
-  }
-  if (vm) {
+  for (int k = 0; k < K; k++)
 #pragma unroll
-    for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
-  }
+    for (int c = 0; c < 3; c++) {
+      sh[c][k] = __ldg(P + (11 + 3 * k + c) * S + g);
+      gsh[c][k] = 0.f;
+    }
+#pragma unroll
+  for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
   float gm[3] = {0.f, 0.f, 0.f};
-  // dL/d(channel c) in the colour record of (view v, Gaussian g)
-  const float* gch = a.g2d + kG2dGeo * (int64_t)a.B * S + kG2dCol * g + c;
-  const int64_t vstep = kG2dCol * S;
-  // the next visible view's gradient is loaded while this view is processed
-  int vn = vm ? __ffsll((long long)vm) - 1 : -1;
-  float nxt = vn >= 0 ? __ldg(gch + (int64_t)vn * vstep) : 0.f;
-  while (vn >= 0) {
-    const int v = vn;
-    const float gc_in = nxt;
+  // dL/d(r, g, b) of (view v, Gaussian g): the colour record's first three floats
+  const float4* gcol = reinterpret_cast<const float4*>(a.g2d + kG2dGeo * (int64_t)a.B * S) + g;
+  auto next_view = [&]() {
+    const int v = vm ? __ffsll((long long)vm) - 1 : -1;
     vm &= vm - 1;
-    vn = vm ? __ffsll((long long)vm) - 1 : -1;
-    if (vn >= 0) nxt = __ldg(gch + (int64_t)vn * vstep);
-    if (gc_in == 0.f) continue;
-    const ViewRec& V = a.views[v];
+    return v;
+  };
+  int v0 = next_view(), v1 = next_view();
+  float4 c0 = v0 >= 0 ? __ldg(gcol + (int64_t)v0 * S) : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 c1 = v1 >= 0 ? __ldg(gcol + (int64_t)v1 * S) : make_float4(0.f, 0.f, 0.f, 0.f);
+  while (v0 >= 0) {
+    const int v = v0;
+    const float4 gc = c0;
+    v0 = v1;
+    c0 = c1;
+    v1 = next_view();
+    if (v1 >= 0) c1 = __ldg(gcol + (int64_t)v1 * S);
+    if (gc.x == 0.f && gc.y == 0.f && gc.z == 0.f) continue;
+    const float4 cam = s_cam[v];
     // rgb_c = max(0, 0.5 + sum_k sh_kc Y_k(d)), d = (mu - campos) / |mu - campos|
-    float dx = mean[0] - V.campos[0], dy = mean[1] - V.campos[1], dz = mean[2] - V.campos[2];
+    float dx = mean[0] - cam.x, dy = mean[1] - cam.y, dz = mean[2] - cam.z;
     const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
     dx *= inv; dy *= inv; dz *= inv;
     float Y[K];
     ShEval<DEG>::basis(dx, dy, dz, Y);
-    float acc = 0.5f;
+    const float gin[3] = {gc.x, gc.y, gc.z};
+    float gcc[3];
 #pragma unroll
-    for (int k = 0; k < K; k++) acc = fmaf(sh[k], Y[k], acc);
-    if (acc < 0.f) continue;  // clamped channel: no gradient
+    for (int c = 0; c < 3; c++) {
+      float acc = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; k++) acc = fmaf(sh[c][k], Y[k], acc);
+      gcc[c] = acc < 0.f ? 0.f : gin[c];  // a clamped channel has no gradient
+    }
     float wk[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
-      gsh[k] = fmaf(gc_in, Y[k], gsh[k]);
-      wk[k] = gc_in * sh[k];
+#pragma unroll
+      for (int c = 0; c < 3; c++) gsh[c][k] = fmaf(gcc[c], Y[k], gsh[c][k]);
+      wk[k] = fmaf(gcc[2], sh[2][k], fmaf(gcc[1], sh[1][k], gcc[0] * sh[0][k]));
     }
     float gdx, gdy, gdz;
     ShEval<DEG>::grad(dx, dy, dz, wk, gdx, gdy, gdz);
@@ -361,35 +393,26 @@ __global__ void __launch_bounds__(96) project_bwd_color_kernel(ProjectBwdArgs a)
     gm[2] += (gdz - dz * dd) * inv;
   }
   float* G = a.grads;
-  if (live) {
 #pragma unroll
-    for (int k = 0; k < K; k++) G[(11 + 3 * k + c) * S + g] = gsh[k];
-  }
+  for (int k = 0; k < K; k++)
 #pragma unroll
-  for (int i = 0; i < 3; i++) s_gm[c][i][lane] = gm[i];
-  __syncthreads();
-  if (c == 0 && live) {
+    for (int c = 0; c < 3; c++) G[(11 + 3 * k + c) * S + g] = gsh[c][k];
 #pragma unroll
-    for (int i = 0; i < 3; i++) G[i * S + g] = s_gm[0][i][lane] + s_gm[1][i][lane] + s_gm[2][i][lane];
-  }
+  for (int i = 0; i < 3; i++) G[i * S + g] = gm[i];
 }
 
 // Backward, geometry part: dL/d(mu2D, conic, opacity) per (view, Gaussian)
 // -> dL/d(mean, log-scale, quaternion, opacity logit); adds to the mean
 // planes written by the colour part.
 __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a) {
+  __shared__ ViewRec s_views[kMaxViews];
+  stage_views(a.views, a.B, s_views);
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.n) return;
   const float* P = a.params;
   const int64_t S = a.stride;
   uint64_t vm = a.vismask[g];
   float* G = a.grads;
-  if (!vm) {  // no tile in any view: every gradient of this Gaussian is zero
-    // (the mean planes were written by the colour part)
-#pragma unroll
-    for (int i = 3; i < 11; i++) G[i * S + g] = 0.f;
-    return;
-  }
   float mean[3], lsc[3], quat[4];
 #pragma unroll
   for (int i = 0; i < 3; i++) mean[i] = __ldg(P + i * S + g);
@@ -397,7 +420,13 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
   for (int i = 0; i < 3; i++) lsc[i] = __ldg(P + (3 + i) * S + g);
 #pragma unroll
   for (int i = 0; i < 4; i++) quat[i] = __ldg(P + (6 + i) * S + g);
-  const float op = __ldg(P + 10 * S + g);
+  const float op = __ldg(P + 10 * S + g);  // (loaded before the mask is known, as above)
+  if (!vm) {  // no tile in any view: every gradient of this Gaussian is zero
+    // (the mean planes were written by the colour part)
+#pragma unroll
+    for (int i = 3; i < 11; i++) G[i * S + g] = 0.f;
+    return;
+  }
   const float opacity = 1.f / (1.f + expf(-op));
 
   GaussCov gc;
@@ -429,13 +458,13 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a)
 #pragma unroll
     for (int q = 0; q < 6; q++) cur[q] = nxt[q];
     if (a.dens_grad) {
-      const ViewRec& Vd = a.views[v];
+      const ViewRec& Vd = s_views[v];
       const float nx = gmx * 0.5f * (float)Vd.W, ny = gmy * 0.5f * (float)Vd.H;
       dens_g += sqrtf(fmaf(nx, nx, ny * ny));
       dens_c += 1.f;
     }
     if (gmx == 0.f && gmy == 0.f && gA == 0.f && gB == 0.f && gC == 0.f && gsig == 0.f) continue;
-    const ViewRec& V = a.views[v];
+    const ViewRec& V = s_views[v];
     const float depth = depth_key(V, mean[0], mean[1], mean[2]);
     if (!(depth > V.znear)) continue;
     ProjState st;
@@ -548,15 +577,14 @@ void launch_project_fwd(const ProjectArgs& a, int deg, cudaStream_t s) {
 int project_fwd_block() { return 256; }
 
 void launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t s) {
-  const unsigned cblocks = (unsigned)((a.n + 31) / 32);  // 32 Gaussians x 3 channels
-  switch (deg) {
-    case 0: project_bwd_color_kernel<0><<<cblocks, 96, 0, s>>>(a); break;
-    case 1: project_bwd_color_kernel<1><<<cblocks, 96, 0, s>>>(a); break;
-    case 2: project_bwd_color_kernel<2><<<cblocks, 96, 0, s>>>(a); break;
-    default: project_bwd_color_kernel<3><<<cblocks, 96, 0, s>>>(a); break;
-  }
   const int threads = 128;
   const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
+  switch (deg) {
+    case 0: project_bwd_color_kernel<0><<<blocks, threads, 0, s>>>(a); break;
+    case 1: project_bwd_color_kernel<1><<<blocks, threads, 0, s>>>(a); break;
+    case 2: project_bwd_color_kernel<2><<<blocks, threads, 0, s>>>(a); break;
+    default: project_bwd_color_kernel<3><<<blocks, threads, 0, s>>>(a); break;
+  }
   project_bwd_geom_kernel<<<blocks, threads, 0, s>>>(a);
 }
 
