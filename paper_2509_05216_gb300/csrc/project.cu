@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(128, 4) project_bwd_color_kernel(ProjectBwdArg
 // Backward, geometry part: dL/d(mu2D, conic, opacity) per (view, Gaussian)
 // -> dL/d(mean, log-scale, quaternion, opacity logit); adds to the mean
 // planes written by the colour part.
-__global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a) {
+__global__ void __launch_bounds__(128, 5) project_bwd_geom_kernel(ProjectBwdArgs a) {
   __shared__ ViewRec s_views[kMaxViews];
   stage_views(a.views, a.B, s_views);
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
