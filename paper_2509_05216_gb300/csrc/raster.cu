@@ -15,9 +15,10 @@
 // time, one per lane; each lane tests its record's alpha >= 1/255 ellipse
 // (with a rounding margin) against the warp's pixel rectangle, and the warp
 // walks only the survivors (a ballot mask); with 2 pixels per thread the
-// warp's lanes form groups that each walk the survivors whose box reaches
-// their own sub-rectangle (see LaneGroups).  This removes only pairs that
-// the per-pixel test would skip, so the result is unchanged.
+// warp's lanes form groups that each walk the records whose alpha >= 1/255
+// box reaches their own sub-rectangle (see LaneGroups; no ellipse test).
+// This removes only pairs that the per-pixel test would skip, so the result
+// is unchanged.
 #include "gs_internal.cuh"
 #include "launch.h"
 
@@ -109,15 +110,13 @@ __device__ __forceinline__ bool ellipse_hits(const float4& r0, const float4& r1,
   return ellipse_rect(ellipse_terms(r0, r1), r0, r2, x0, x1, y0, y1);
 }
 
-// The same test against the NG lane-group rectangles of a warp (bit g of
-// the result: group g), sharing the per-record terms.
-// Lane-group survivors: the exact test against the warp's rectangle, then
-// the alpha >= 1/255 box against each group's rectangle (bit g: group g).
-// The box is looser than the ellipse but costs four compares per group.
+// Lane-group survivors: the alpha >= 1/255 box against each group's
+// rectangle (bit g: group g).  The box is looser than the ellipse but costs
+// four compares per group; the exact ellipse test against the warp's
+// rectangle on top of it cost the forward more (its per-record terms) than
+// the walk steps it saved.
 template <class Geom>
-__device__ __forceinline__ uint32_t box_group_bits(const float4& r0, const float4& r1, const float4& r2,
-                                                   const Geom& geo) {
-  if (!ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1)) return 0u;
+__device__ __forceinline__ uint32_t box_group_bits(const float4& r0, const float4& r2, const Geom& geo) {
   uint32_t bits = 0;
 #pragma unroll
   for (int g = 0; g < Geom::NG; g++) {
@@ -553,7 +552,7 @@ __global__ void __launch_bounds__(Geo<PPT>::THREADS) raster_fwd_kernel(RasterArg
       s0[w][lane] = r0;
       s1[w][lane] = r1;
       s2[w][lane] = r2;
-      if constexpr (G::NG > 1) gbits = box_group_bits(r0, r1, r2, geo);
+      if constexpr (G::NG > 1) gbits = box_group_bits(r0, r2, geo);
       else hit = ellipse_hits(r0, r1, r2, geo.wx0, geo.wx1, geo.wy0, geo.wy1);
     }
     {
