@@ -418,12 +418,11 @@ struct Shape<8> {  // 1 warp per tile, 4 tiles per block
 // Lane groups: the warp's lanes form NG = 32 / GW groups, each owning a
 // GCW x GRH sub-rectangle of the warp's pixels and walking only the
 // Gaussians whose box reaches it (the warp iterates max over groups; a lane
-// whose group has run out takes no-op steps).  With 2 pixels per thread the
-// forward uses 4 groups of 4 x 4 pixels and the backward, whose work per
-// survivor is larger, 8 groups of 2 x 4.
+// whose group has run out takes no-op steps).  With 2 pixels per thread
+// both kernels use 8 groups of 2 x 4 pixels (one contribution cell each).
 template <int PPT>
 struct LaneGroups {
-  static constexpr int FWD = PPT == 2 ? 8 : 32;
+  static constexpr int FWD = PPT == 2 ? 4 : 32;
   static constexpr int BWD = PPT == 2 ? 4 : 32;
 };
 
